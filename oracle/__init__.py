@@ -1,0 +1,205 @@
+"""Plain FP64 CPU oracle of the EXCMG / 25-point biharmonic solver.
+
+TEST INFRASTRUCTURE ONLY.  Only ``tests/``, ``__graft_entry__.smoke()`` and the
+CPU-baseline leg of ``bench.py`` may import this package.  The product path
+(the CUDA library and its Python binding) never touches it.
+
+The arithmetic lives in ``excmg_oracle.c`` (plain C, compiled with
+``-ffp-contract=off``); this module only builds it and marshals numpy arrays
+through ctypes.  Array conventions: node arrays of shape (N+1, N+1, N+1) in
+(z, y, x) order, i.e. x fastest in memory; g2 as shape (6, N+1, N+1) with faces
+x=0, x=1, y=0, y=1, z=0, z=1 and the two in-face axes (a, b) in x<y<z order
+stored as [face, b, a].
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+import subprocess
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+_SRC = os.path.join(_HERE, "excmg_oracle.c")
+_LIB = os.path.join(_HERE, "liboracle.so")
+_lib = None
+
+_D = ctypes.POINTER(ctypes.c_double)
+_I = ctypes.POINTER(ctypes.c_int)
+
+
+def build(force: bool = False) -> str:
+    """Compile the oracle into ``oracle/liboracle.so`` (gcc, FP64, no FMA contraction)."""
+    if force or not os.path.exists(_LIB) or os.path.getmtime(_LIB) < os.path.getmtime(_SRC):
+        tmp = _LIB + f".tmp{os.getpid()}"
+        subprocess.check_call(
+            ["gcc", "-O2", "-std=c11", "-fPIC", "-shared", "-ffp-contract=off",
+             "-o", tmp, _SRC, "-lm"])
+        os.replace(tmp, _LIB)
+    return _LIB
+
+
+def _load():
+    global _lib
+    if _lib is None:
+        build()
+        lib = ctypes.CDLL(_LIB)
+        lib.orc_stencil_apply.argtypes = [ctypes.c_int, ctypes.c_int, ctypes.c_int, _D, _D]
+        lib.orc_assemble_rhs.argtypes = [ctypes.c_int, ctypes.c_int, _D, _D, _D, _D]
+        lib.orc_inject_nodes.argtypes = [ctypes.c_int, ctypes.c_int, _D, _D]
+        lib.orc_inject_faces.argtypes = [ctypes.c_int, ctypes.c_int, _D, _D]
+        lib.orc_assemble_dense.argtypes = [ctypes.c_int, ctypes.c_int, _D]
+        lib.orc_dsolve.argtypes = [ctypes.c_int, ctypes.c_int, _D, _D]
+        lib.orc_residual_norm.argtypes = [ctypes.c_int, ctypes.c_int, _D, _D]
+        lib.orc_residual_norm.restype = ctypes.c_double
+        lib.orc_interior_norm2.argtypes = [ctypes.c_int, _D]
+        lib.orc_interior_norm2.restype = ctypes.c_double
+        lib.orc_bicg.argtypes = [ctypes.c_int, ctypes.c_int, _D, _D, ctypes.c_double,
+                                 ctypes.c_double, ctypes.c_int, _I, _D]
+        lib.orc_exp_finite.argtypes = [ctypes.c_int, _D, _D, _D]
+        lib.orc_exp_true.argtypes = [ctypes.c_int, _D, _D, _D]
+        lib.orc_excmg.argtypes = [ctypes.c_int, ctypes.c_int, ctypes.c_int, _D, _D, _D,
+                                  ctypes.c_double, ctypes.c_int, ctypes.c_int, ctypes.c_int,
+                                  _D, _D, _D]
+        lib.orc_error_norms.argtypes = [ctypes.c_int, _D, _D, _D]
+        lib.orc_error_norms.restype = None
+        _lib = lib
+    return _lib
+
+
+class OracleError(RuntimeError):
+    pass
+
+
+def _p(a: np.ndarray):
+    return a.ctypes.data_as(_D)
+
+
+def _node(a, N):
+    a = np.ascontiguousarray(a, dtype=np.float64)
+    if a.shape != (N + 1, N + 1, N + 1):
+        raise ValueError(f"expected node array of shape {(N + 1,) * 3}, got {a.shape}")
+    return a
+
+
+def _faces(a, N):
+    a = np.ascontiguousarray(a, dtype=np.float64)
+    if a.shape != (6, N + 1, N + 1):
+        raise ValueError(f"expected faces of shape {(6, N + 1, N + 1)}, got {a.shape}")
+    return a
+
+
+def _check(rc, what):
+    if rc != 0:
+        raise OracleError(f"{what} failed with status {rc}")
+
+
+def stencil_apply(N: int, bc_kind: int, u, transpose: bool = False) -> np.ndarray:
+    """y = A_h u (or A_h^T u); only the interior of u is read, y's boundary is 0."""
+    u = _node(u, N)
+    y = np.empty_like(u)
+    _check(_load().orc_stencil_apply(N, bc_kind, int(bool(transpose)), _p(u), _p(y)), "stencil_apply")
+    return y
+
+
+def assemble_rhs(N: int, bc_kind: int, f, g1, g2) -> np.ndarray:
+    f, g1, g2 = _node(f, N), _node(g1, N), _faces(g2, N)
+    fh = np.empty_like(f)
+    _check(_load().orc_assemble_rhs(N, bc_kind, _p(f), _p(g1), _p(g2), _p(fh)), "assemble_rhs")
+    return fh
+
+
+def inject_nodes(Nf: int, stride: int, src) -> np.ndarray:
+    src = _node(src, Nf)
+    Nc = Nf // stride
+    dst = np.empty((Nc + 1,) * 3)
+    _check(_load().orc_inject_nodes(Nf, stride, _p(src), _p(dst)), "inject_nodes")
+    return dst
+
+
+def inject_faces(Nf: int, stride: int, src) -> np.ndarray:
+    src = _faces(src, Nf)
+    Nc = Nf // stride
+    dst = np.empty((6, Nc + 1, Nc + 1))
+    _check(_load().orc_inject_faces(Nf, stride, _p(src), _p(dst)), "inject_faces")
+    return dst
+
+
+def assemble_dense(N: int, bc_kind: int) -> np.ndarray:
+    n = (N - 1) ** 3
+    A = np.empty((n, n))
+    _check(_load().orc_assemble_dense(N, bc_kind, _p(A)), "assemble_dense")
+    return A
+
+
+def dsolve(N: int, bc_kind: int, fh, u_boundary) -> np.ndarray:
+    """Direct solve; returns a node array with u_boundary's boundary and the solution inside."""
+    fh = _node(fh, N)
+    u = _node(u_boundary, N).copy()
+    _check(_load().orc_dsolve(N, bc_kind, _p(fh), _p(u)), "dsolve")
+    return u
+
+
+def residual_norm(N: int, bc_kind: int, fh, u) -> float:
+    fh, u = _node(fh, N), _node(u, N)
+    return float(_load().orc_residual_norm(N, bc_kind, _p(fh), _p(u)))
+
+
+def interior_norm2(N: int, a) -> float:
+    a = _node(a, N)
+    return float(_load().orc_interior_norm2(N, _p(a)))
+
+
+def bicg(N: int, bc_kind: int, b, x0, tol: float, bnorm: float | None = None, max_iter: int = 10**6):
+    """Alg. 2 with M = I and r*_0 = r_0.  Returns (x, iterations, relres, status)."""
+    b = _node(b, N)
+    x = _node(x0, N).copy()
+    if bnorm is None:
+        bnorm = interior_norm2(N, b)
+    it = ctypes.c_int(0)
+    rr = ctypes.c_double(0.0)
+    rc = _load().orc_bicg(N, bc_kind, _p(b), _p(x), float(tol), float(bnorm), int(max_iter),
+                          ctypes.byref(it), ctypes.byref(rr))
+    return x, it.value, rr.value, rc
+
+
+def exp_finite(Nf: int, u1, u0) -> np.ndarray:
+    """Steps 1-5 at every fine node (boundary nodes included)."""
+    u1, u0 = _node(u1, Nf // 2), _node(u0, Nf // 4)
+    w = np.empty((Nf + 1,) * 3)
+    _check(_load().orc_exp_finite(Nf, _p(u1), _p(u0), _p(w)), "exp_finite")
+    return w
+
+
+def exp_true(Nf: int, uh, u2h) -> np.ndarray:
+    uh, u2h = _node(uh, Nf), _node(u2h, Nf // 2)
+    ut = np.empty_like(uh)
+    _check(_load().orc_exp_true(Nf, _p(uh), _p(u2h), _p(ut)), "exp_true")
+    return ut
+
+
+def excmg(n_finest: int, n_coarsest: int, bc_kind: int, f, g1, g2, tol: float,
+          tol_mode: str = "uniform", max_iter: int = 100000, max_total: int = 1000000):
+    """Alg. 1.  Returns (u_h, u_tilde, stats) with stats[l] = (iters, relres, calls, stagnated)."""
+    f, g1, g2 = _node(f, n_finest), _node(g1, n_finest), _faces(g2, n_finest)
+    uh = np.empty_like(f)
+    ut = np.empty_like(f)
+    nl = 0
+    n = n_coarsest
+    while n < n_finest:
+        n *= 2
+        nl += 1
+    stats = np.zeros((nl + 1, 4))
+    mode = {"paper": 0, "uniform": 1}[tol_mode]
+    rc = _load().orc_excmg(n_finest, n_coarsest, bc_kind, _p(f), _p(g1), _p(g2), float(tol), mode,
+                           int(max_iter), int(max_total), _p(uh), _p(ut), _p(stats))
+    _check(rc, "excmg")
+    return uh, ut, stats
+
+
+def error_norms(N: int, a, b):
+    """(root-mean-square over all nodes, max) norms of a - b, as in Tables 1-5."""
+    a, b = _node(a, N), _node(b, N)
+    out = np.zeros(2)
+    _load().orc_error_norms(N, _p(a), _p(b), _p(out))
+    return float(out[0]), float(out[1])
