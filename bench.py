@@ -1,0 +1,323 @@
+"""Benchmark of the EXCMG solve on GB300.
+
+Workload (default): the plain FP64 EXCMG solve on the 512^3-interval grid
+(511^3 = 133,432,831 unknowns), coarsest grid 8^3 (7 nested levels, 8^3 and
+16^3 solved directly), manufactured u = exp(x+y+z), f = 9u, Bi-CG relative
+residual tolerance 1e-10 on every level.  One step = two solves: first-kind
+and second-kind boundary data.  Inputs are synthetic closed forms; every
+input array is larger than the 129 MB L2, so no flush is needed.
+
+Printed: one JSON line (rank 0).  ``value`` = seconds per solve with the
+inputs resident in HBM; ``e2e`` = the same through the C ABI with pinned host
+buffers, host->device copies of f, g1, g2 and the device->host copy of the
+solution inside the timed region.  ``roofline`` is the operator kernel on the
+finest grid, timed live (CUDA events around each of its launches inside
+Bi-CG).  ``cpu_baseline`` times the CPU oracle on a bounded sample.
+
+Multi-GPU: the solve does not shard here; ``--gpus N`` under torchrun runs N
+independent replicas (weak scaling, no collective on the data path).
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+METRIC = "EXCMG solve s @512³ FP64 vs FP32+refine; stencil HBM GB/s % peak; p99 latency"
+# Work of one solve in work units (one Bi-CG iteration on the finest grid, as
+# the paper counts cost), per boundary kind, for the default workload; used
+# only by the CPU-oracle legs to scale a timed sample to a whole solve when
+# the GPU counts are not at hand.
+WU_DEFAULT = {1: 44.1, 2: 20.1}
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=3)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
+    ap.add_argument("--n", type=int, default=512)
+    ap.add_argument("--nc", type=int, default=8)
+    ap.add_argument("--tol", type=float, default=1e-10)
+    ap.add_argument("--stencil", choices=["exact", "fp64"], default="exact")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-e2e", action="store_true")
+    return ap.parse_args()
+
+
+def dist_env():
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return rank, world, local
+
+
+# ------------------------------------------------------------------ clocks
+class ClockSampler:
+    """nvidia-smi samples of SM clock and throttle reasons while running."""
+
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index: int):
+        self.gpu = gpu_index
+        self.proc = None
+
+    def __enter__(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.gpu), f"--query-gpu={self.FIELDS}", "--format=csv,noheader,nounits",
+                 "-lms", "200"], stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+        except OSError:
+            self.proc = None
+        return self
+
+    def __exit__(self, *exc):
+        self.lines = []
+        if self.proc is not None:
+            self.proc.terminate()
+            try:
+                out, _ = self.proc.communicate(timeout=5)
+            except subprocess.TimeoutExpired:
+                self.proc.kill()
+                out, _ = self.proc.communicate()
+            self.lines = [l for l in out.splitlines() if l.strip()]
+        return False
+
+    def summary(self):
+        sm, mx, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for l in getattr(self, "lines", []):
+            parts = [p.strip() for p in l.split(",")]
+            if len(parts) < 9:
+                continue
+            try:
+                sm.append(float(parts[1]))
+                mx.append(float(parts[2]))
+            except ValueError:
+                continue
+            for nm, v in zip(names, parts[5:9]):
+                if v.lower() == "active":
+                    reasons.add(nm)
+        if not sm:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["unsampled"]}
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": max(mx), "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+# ------------------------------------------------------------- CPU oracle
+def oracle_sample(n: int, nc: int, bc_kinds, wu: dict):
+    """Time the CPU oracle on a bounded sample of the workload: Bi-CG
+    iterations on the 256^3 level of the same problem (one more iteration in
+    the second call than in the first; the difference is one iteration), then
+    scale to one solve: seconds per iteration x (512/256)^3 x the solve's work
+    units.  Single-threaded C."""
+    import oracle
+    from paper_1901_05118_gb300 import problems
+
+    prob = problems.exp_sum()
+    ns = n // 2
+    t_it = []
+    for bc in bc_kinds:
+        f, g1, g2 = prob.data(ns, bc)
+        fh = oracle.assemble_rhs(ns, bc, f, g1, g2)
+        x0 = g1.copy()
+        t0 = time.perf_counter()
+        oracle.bicg(ns, bc, fh, x0, 0.0, max_iter=1)
+        t1 = time.perf_counter()
+        oracle.bicg(ns, bc, fh, x0, 0.0, max_iter=2)
+        t2 = time.perf_counter()
+        t_it.append(max((t2 - t1) - (t1 - t0), 1e-9))
+    scale = ((n - 1) / (ns - 1)) ** 3
+    per_solve = [t * scale * wu[bc] for t, bc in zip(t_it, bc_kinds)]
+    return sum(per_solve) / len(per_solve), {
+        "kind": "oracle", "cores": 1,
+        "sample": (f"single-threaded C oracle: one Bi-CG iteration on the {ns}^3 level of the same problem, "
+                   f"per boundary kind ({', '.join(f'{t:.2f} s' for t in t_it)}), scaled by "
+                   f"((N-1)/({ns}-1))^3 to {n}^3 and by the solve's work units "
+                   f"({', '.join(f'{wu[b]:.1f}' for b in bc_kinds)} finest-grid iterations)")}
+
+
+def run_reference(args):
+    rank, world, local = dist_env()
+    if rank != 0:
+        return
+    bcs = (1, 2)
+    times = []
+    info = None
+    for s in range(args.warmup + args.steps):
+        t0 = time.perf_counter()
+        v, info = oracle_sample(args.n, args.nc, bcs, WU_DEFAULT)
+        if s >= args.warmup:
+            times.append(v)
+    value = statistics.mean(times)
+    info["value"] = value
+    line = {"impl": "reference", "metric": METRIC, "value": value, "unit": "s", "n_gpus": args.gpus,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": 2 * value * 1e3,
+            "higher_is_better": False, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+            "data": "synthetic", "config": config(args),
+            "cpu_baseline": info, "e2e": {"value": value, "unit": "s", "h2d_bytes_per_step": 0,
+                                          "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+def config(args):
+    return {"workload": (f"EXCMG FP64, {args.n}^3 intervals ({args.n - 1}^3 unknowns), coarsest {args.nc}^3, "
+                         f"u=exp(x+y+z), first- and second-kind data, Bi-CG tol {args.tol:g} per level"),
+            "n_finest": args.n, "n_coarsest": args.nc, "levels": int(np.log2(args.n // args.nc)) + 1,
+            "solves_per_step": 2, "tol": args.tol, "stencil": args.stencil,
+            "l2_flush": "inputs larger than L2 (each node array 1.08 GB)", "parallelism": "replicas"}
+
+
+# --------------------------------------------------------------- GPU arm
+def run_ours(args):
+    import torch
+    import torch.distributed as dist
+
+    rank, world, local = dist_env()
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    if world > 1:
+        dist.init_process_group("nccl", device_id=dev)
+
+    from paper_1901_05118_gb300 import binding as B, problems
+
+    n, nc = args.n, args.nc
+    prob = problems.exp_sum()
+    bcs = (1, 2)
+    host = {}
+    f = prob.rhs(n)
+    g1 = prob.exact(n)
+    host["f"] = torch.from_numpy(f).pin_memory()
+    host["g1"] = torch.from_numpy(g1).pin_memory()
+    for bc in bcs:
+        host[f"g2_{bc}"] = torch.from_numpy(prob.boundary_g2(n, bc)).pin_memory()
+    del f, g1
+    d = {k: v.to(dev, non_blocking=False) for k, v in host.items()}
+    u_out = torch.empty((n + 1,) * 3, dtype=torch.float64, device=dev)
+    u_host = torch.empty((n + 1,) * 3, dtype=torch.float64).pin_memory()
+    ctx = B.Context(dev)
+    ctx.set_stencil(args.stencil)
+    stream = torch.cuda.current_stream(dev)
+
+    def solve(bc, stats=False):
+        return B.excmg_solve(n, nc, bc, d["f"], d["g1"], d[f"g2_{bc}"], args.tol, u_out, ctx=ctx,
+                             return_stats=stats)
+
+    def barrier():
+        if world > 1:
+            dist.barrier()
+        torch.cuda.synchronize(dev)
+
+    # warm-up (also builds the DSOLVE inverses held by the context)
+    for _ in range(args.warmup):
+        for bc in bcs:
+            solve(bc)
+    stats = {bc: solve(bc, stats=True)[1] for bc in bcs}
+
+    # ---- device-resident timing
+    ctx.profile(True)
+    launches0 = B.launch_count()
+    barrier()
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    with ClockSampler(local) as clk:
+        e0.record(stream)
+        for _ in range(args.steps):
+            for bc in bcs:
+                solve(bc)
+        e1.record(stream)
+        barrier()
+    ms_total = e0.elapsed_time(e1)
+    launches = B.launch_count() - launches0
+    st_ms, st_cnt = ctx.profile_read(n)
+    ctx.profile(False)
+    ms_step = ms_total / args.steps
+    if world > 1:
+        t = torch.tensor([ms_step], device=dev)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        ms_step = float(t.item())
+    value = ms_step / 1e3 / (len(bcs) * world)   # seconds per solve, whole job
+
+    # ---- end to end through the C ABI, host buffers
+    e2e = None
+    if not args.no_e2e:
+        h2d = sum(host[k].numel() * 8 for k in ("f", "g1")) + host["g2_1"].numel() * 8
+        d2h = u_host.numel() * 8
+        barrier()
+        e2 = torch.cuda.Event(enable_timing=True)
+        e3 = torch.cuda.Event(enable_timing=True)
+        e2.record(stream)
+        for _ in range(args.steps):
+            for bc in bcs:
+                d["f"].copy_(host["f"], non_blocking=True)
+                d["g1"].copy_(host["g1"], non_blocking=True)
+                d[f"g2_{bc}"].copy_(host[f"g2_{bc}"], non_blocking=True)
+                solve(bc)
+                u_host.copy_(u_out, non_blocking=True)
+        e3.record(stream)
+        barrier()
+        ms_e2e = e2.elapsed_time(e3) / args.steps
+        if world > 1:
+            t = torch.tensor([ms_e2e], device=dev)
+            dist.all_reduce(t, op=dist.ReduceOp.MAX)
+            ms_e2e = float(t.item())
+        e2e = {"value": ms_e2e / 1e3 / (len(bcs) * world), "unit": "s",
+               "h2d_bytes_per_step": h2d * len(bcs), "d2h_bytes_per_step": d2h * len(bcs)}
+
+    # ---- roofline of the operator kernel on the finest grid
+    peaks = {}
+    try:
+        peaks = json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))
+    except (OSError, ValueError):
+        pass
+    hbm_peak = float(peaks.get("hbm_gbs", 6800.0))
+    bytes_per_launch = 16.0 * (n - 1) ** 3          # read u + write y, 8 B each per unknown
+    avg_ms = st_ms / st_cnt if st_cnt else float("nan")
+    achieved = bytes_per_launch / (avg_ms * 1e-3) / 1e9 if st_cnt else None
+    roofline = {"kernel": f"stencil_{args.stencil} (A p and A^T p* on the {n}^3 grid)", "bound": "hbm",
+                "achieved": achieved, "peak": hbm_peak, "unit": "GB/s",
+                "frac": (achieved / hbm_peak) if achieved else None, "traffic": None,
+                "launches": st_cnt, "avg_ms": avg_ms, "peak_source": "MEASURED_PEAKS.json hbm_gbs (of measured)"}
+
+    wu = {bc: sum(s["iters"] * (s["n"] / n) ** 3 for s in stats[bc] if s["iters"]) for bc in bcs}
+    line = {"metric": METRIC, "value": value, "unit": "s", "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": ms_step, "higher_is_better": False, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f64", "data": "synthetic", "config": config(args),
+            "e2e": e2e, "gpu_launches": launches, "roofline": roofline, "clocks": clk.summary(),
+            "levels": {str(bc): [{"n": s["n"], "iters": s["iters"], "ms": round(s["ms"], 3),
+                                  "relres": s["relres"]} for s in stats[bc]] for bc in bcs},
+            "work_units": {str(bc): round(w, 2) for bc, w in wu.items()}}
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        cpu_value, info = oracle_sample(n, nc, bcs, wu)
+        info["value"] = cpu_value
+        info["unit"] = "s"
+        line["cpu_baseline"] = info
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+    if world > 1:
+        dist.destroy_process_group()
+
+
+def main():
+    args = parse()
+    if args.impl == "reference":
+        run_reference(args)
+    else:
+        run_ours(args)
+
+
+if __name__ == "__main__":
+    main()

@@ -1,0 +1,194 @@
+/*
+ * excmg.h -- C ABI of the GB300 (sm_103a) EXCMG solver for the 3D biharmonic
+ * equation  Laplacian^2 u = f  on (0,1)^3  with Dirichlet data of the first kind
+ * (u = g1, du/dn = g2) or the second kind (u = g1, d2u/dn2 = g2), discretised
+ * by the 25-point scheme and solved by extrapolation cascadic multigrid with
+ * Bi-CG on every grid (Pan, He & Ni, arXiv 1901.05118).
+ *
+ * Data layout (every grid function):
+ *   N intervals per axis, h = 1/N, nodes i,j,k = 0..N.  A node array holds
+ *   (N+1)^3 doubles, x fastest:  idx = (k*(N+1) + j)*(N+1) + i.
+ *   The unknowns of a grid are its interior nodes 1..N-1 on every axis.
+ *   g2 holds 6 faces of (N+1)^2 doubles, faces ordered x=0, x=1, y=0, y=1,
+ *   z=0, z=1; inside a face the two remaining axes (a,b) in x<y<z order give
+ *   the index b*(N+1)+a.  For bc_kind = 1, g2 is the OUTWARD normal
+ *   derivative du/dn; for bc_kind = 2 it is d2u/dn2.
+ *
+ * Ownership: every array pointer passed in is a DEVICE pointer (CUDA global
+ * memory, e.g. a torch tensor's data_ptr()) owned by the caller; the library
+ * never frees or keeps it beyond the call.  The library allocates its own
+ * workspace (cudaMalloc) inside a context and frees it in excmg_ctx_destroy.
+ *
+ * Streams: a context is bound to one CUDA stream.  Calls enqueue work on
+ * that stream and return after the results are complete on it (the solver
+ * reads a few scalars back to steer its loops); the caller's inputs must be
+ * ready on that stream.  Calls without a context use a per-device default
+ * context on the legacy default stream (stream 0).
+ *
+ * Errors: every call returns an excmg_status; nothing throws across the ABI.
+ * excmg_last_error() gives a message for the last failing call on a context
+ * (or on the default context when given NULL).  A CUDA error makes the call
+ * return EXCMG_ERR_CUDA.
+ */
+#ifndef EXCMG_H
+#define EXCMG_H
+
+#include <stddef.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+    EXCMG_OK = 0,
+    EXCMG_ERR_ARG = -1,        /* invalid argument (size, bc_kind, null pointer, tolerance) */
+    EXCMG_ERR_OOM = -2,        /* device allocation failed                                   */
+    EXCMG_ERR_BREAKDOWN = -3,  /* Bi-CG breakdown: (r*,r) or (p*,Ap) zero or not finite      */
+    EXCMG_ERR_NOCONV = -4,     /* Bi-CG reached its iteration cap above the tolerance        */
+    EXCMG_ERR_NAN = -5,        /* non-finite value in a residual norm                        */
+    EXCMG_ERR_CUDA = -6,       /* a CUDA runtime call or kernel launch failed                */
+    EXCMG_ERR_TIMEOUT = -7,    /* a bounded device-side wait gave up                         */
+    EXCMG_ERR_BUDGET = -9      /* the context's HBM budget is too small for the request      */
+} excmg_status;
+
+typedef struct excmg_ctx excmg_ctx;      /* device, stream, workspace, DSOLVE factor cache */
+typedef struct excmg_level excmg_level;  /* one grid: (context, N, bc_kind)                */
+
+/* Tolerance schedule of Alg. 1: EXCMG_TOL_PAPER uses eps_i = tol * 10^(i-L)
+ * (Alg. 1, line 5); EXCMG_TOL_UNIFORM uses eps_i = tol on every level. */
+enum { EXCMG_TOL_PAPER = 0, EXCMG_TOL_UNIFORM = 1 };
+
+typedef struct {
+    double tol;          /* relative residual tolerance eps of Alg. 1 (> 0)                  */
+    int tol_mode;        /* EXCMG_TOL_PAPER or EXCMG_TOL_UNIFORM                              */
+    int max_iter;        /* cap on the iterations of one Bi-CG call (WHILE body, Alg. 1 l.8)  */
+    int max_total;       /* cap on the Bi-CG iterations of one level                          */
+    int check_every;     /* iterations enqueued between two host checks of convergence (>= 1) */
+} excmg_params;
+
+#define EXCMG_MAX_LEVELS 16
+
+typedef struct {
+    int levels;                          /* number of grids, coarsest first            */
+    int n[EXCMG_MAX_LEVELS];             /* intervals per axis of each grid            */
+    int iters[EXCMG_MAX_LEVELS];         /* Bi-CG iterations (0 on DSOLVE levels)      */
+    int calls[EXCMG_MAX_LEVELS];         /* Bi-CG calls of the WHILE loop              */
+    int stagnated[EXCMG_MAX_LEVELS];     /* 1 if the loop ended on the stagnation rule */
+    double relres[EXCMG_MAX_LEVELS];     /* final true relative residual ||f-Au||/||f|| */
+    double ms[EXCMG_MAX_LEVELS];         /* device time spent on the level (ms)        */
+} excmg_stats;
+
+/* ---------------------------------------------------------------- contexts */
+
+/* Create a context on the current device, bound to `cuda_stream` (a
+ * cudaStream_t; NULL = legacy default stream).  hbm_budget_bytes caps the
+ * workspace the context may hold (0 = no cap); requests beyond it fail with
+ * EXCMG_ERR_BUDGET. */
+int excmg_ctx_create(void *cuda_stream, size_t hbm_budget_bytes, excmg_ctx **out);
+int excmg_ctx_destroy(excmg_ctx *ctx);
+/* Bytes of device workspace the context holds right now. */
+size_t excmg_ctx_bytes(const excmg_ctx *ctx);
+
+/* Arithmetic of the 25-point operator (eq. (method1)) on this context:
+ * EXCMG_STENCIL_EXACT (default): each input plane of a thread block is put
+ *   on one power-of-two scale as 64-bit integers, the 25 integer-weighted
+ *   taps are summed exactly and the result is rounded once to double (error
+ *   below 3.2e-14 of the largest input magnitude the block reads);
+ * EXCMG_STENCIL_FP64: the taps are summed in double precision.
+ * Both give results within 1e-13 relative of each other on the same input. */
+enum { EXCMG_STENCIL_EXACT = 0, EXCMG_STENCIL_FP64 = 1 };
+int excmg_ctx_set_stencil(excmg_ctx *ctx, int variant);
+const char *excmg_last_error(const excmg_ctx *ctx);
+
+/* Instrumentation.  excmg_launch_count: kernel launches the library has
+ * made in this process (all contexts).  excmg_ctx_profile(ctx, 1) makes the
+ * context time every operator launch inside Bi-CG with CUDA events on its
+ * stream (and clears earlier records); excmg_ctx_profile_read returns, for
+ * grids with n intervals, the summed device time (ms) and the number of
+ * operator launches timed since. */
+long long excmg_launch_count(void);
+int excmg_ctx_profile(excmg_ctx *ctx, int enable);
+int excmg_ctx_profile_read(const excmg_ctx *ctx, int n, double *ms_total, long long *launches);
+
+/* One grid with N intervals (N >= 4) and the given kind of boundary data.
+ * The level borrows the context (destroy levels before their context). */
+int excmg_level_create(excmg_ctx *ctx, int n, int bc_kind, excmg_level **out);
+int excmg_level_destroy(excmg_level *level);
+
+/* ---------------------------------------------------------- the hot path */
+
+/* y = A_h u  (transpose = 0)  or  y = A_h^T u  (transpose = 1).
+ * A_h is the matrix of eq. (sec): the 25-point scheme of eq. (method1) on the
+ * interior nodes, with the fictitious nodes outside the domain folded onto
+ * their mirror nodes by eq. (reflection2) (first kind: +1 on the diagonal per
+ * near-boundary axis) or eq. (reflection4) (second kind: -1).  Only the
+ * interior entries of u are read (its boundary entries are ignored); the
+ * interior entries of y are written and its boundary entries set to 0.
+ * u and y are node arrays of the level, and must not overlap. */
+int stencil_apply(const excmg_level *level, int transpose, const double *u, double *y);
+
+/* Bi-CG with preconditioner (Alg. 2) in real arithmetic, M = I, shadow
+ * residual r*_0 = r_0, on A_h x = b.  b: node array (interior entries read);
+ * x_inout: node array, initial guess in, iterate out (boundary entries left
+ * unchanged).  Iterates until the recursively updated residual satisfies
+ * ||r_k||_2 <= tol * ||b||_2 or max_iter iterations.  iters_out / relres_out
+ * (may be NULL) receive the iteration count and ||r_k||_2 / ||b||_2.
+ * Returns EXCMG_OK on convergence, EXCMG_ERR_NOCONV at the cap,
+ * EXCMG_ERR_BREAKDOWN on a breakdown. */
+int bicg_solve(const excmg_level *level, const double *b, double *x_inout, double tol,
+               int max_iter, int *iters_out, double *relres_out);
+
+/* EXP_finite (Sec. 4.2.2-4.2.3, Steps 1-5): third-order approximation w_h on
+ * the grid with n_fine intervals (n_fine divisible by 4, >= 8) of the FD
+ * solution, from the FD solutions u_2h (n_fine/2 intervals) and u_4h
+ * (n_fine/4 intervals).  Every node of w_h is written, boundary nodes
+ * included (interpolated values). */
+int extrapolate_interpolate(int n_fine, const double *u_2h, const double *u_4h, double *w_h);
+
+/* EXP_true (Sec. 4.2.1, eqs. (t1), (chenlin); Alg. 1 line 11): extrapolated
+ * solution u_tilde = u_h + (1/3) * multilinear interpolation of (u_h - u_2h)
+ * on the grid with n_fine intervals (even, >= 4).  Every node is written. */
+int midpoint_extrapolate(int n_fine, const double *u_h, const double *u_2h, double *u_tilde);
+
+/* Alg. 1: EXCMG from the coarsest grid n_coarsest to the finest n_finest =
+ * n_coarsest * 2^(L+1), L >= 1 (n_coarsest >= 4).  f, g1: node arrays on the
+ * finest grid (f's interior and g1's boundary entries are read; coarser grids
+ * take every stride-th node); g2: the 6 faces on the finest grid.  The two
+ * coarsest grids are solved directly (DSOLVE), every finer one by
+ * EXP_finite + Bi-CG until ||f_h - A_h u_h||_2 <= tol ||f_h||_2 on every level.
+ * u_out receives u_tilde = EXP_true(u_h, u_2h) on the finest grid. */
+int excmg_solve(int n_finest, int n_coarsest, int bc_kind, const double *f, const double *g1,
+                const double *g2, double tol, double *u_out);
+
+/* Extended form of excmg_solve on an explicit context: parameters as above,
+ * u_h_out (may be NULL) receives the finest FD solution u_h, u_tilde_out
+ * (may be NULL) the extrapolated solution, stats (may be NULL) per-level
+ * counters. */
+int excmg_solve_ex(excmg_ctx *ctx, int n_finest, int n_coarsest, int bc_kind, const double *f,
+                   const double *g1, const double *g2, const excmg_params *params,
+                   double *u_h_out, double *u_tilde_out, excmg_stats *stats);
+
+/* Context forms of the two transfer steps (same semantics, ctx's stream). */
+int extrapolate_interpolate_ex(excmg_ctx *ctx, int n_fine, const double *u_2h, const double *u_4h,
+                               double *w_h);
+int midpoint_extrapolate_ex(excmg_ctx *ctx, int n_fine, const double *u_h, const double *u_2h,
+                            double *u_tilde);
+
+/* Right-hand side f_h of eq. (sec) for a level: h^4 f plus every known
+ * boundary value and ghost datum the 25-point rows touch, moved across
+ * (Sec. 2, the 27 position cases).  f, g1, g2 are given on a finer grid with
+ * n_src = stride * N intervals (stride >= 1); the level takes every
+ * stride-th node.  fh: node array of the level (boundary entries set to 0). */
+int excmg_assemble_rhs(const excmg_level *level, int n_src, const double *f, const double *g1,
+                       const double *g2, double *fh);
+
+/* DSOLVE (Alg. 1, lines 1-2): u = A_h^{-1} fh on the level's interior nodes
+ * (u's boundary entries left unchanged).  The first call on a (N, bc_kind)
+ * factorises A_h (dense Gauss-Jordan inverse, kept in the context); N <= 32. */
+int excmg_dsolve(const excmg_level *level, const double *fh, double *u);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* EXCMG_H */

@@ -1,0 +1,126 @@
+// Host side of Bi-CG (Alg. 2, M = I, r*_0 = r_0): every iteration is a fixed
+// sequence of kernels that read alpha, beta and the stopping flag from the
+// device-resident BicgState, so iterations are enqueued in batches and the
+// host only looks at the state between batches.
+#include <cmath>
+
+#include "excmg_internal.cuh"
+
+namespace excmg {
+
+int interior_norm(excmg_ctx* ctx, int n, const double* a, double* out) {
+    const size_t len = node_count(n);
+    cudaError_t e = launch_dot(a, a, len, ctx->partials, ctx->ticket, ctx->scalar, ctx->stream);
+    note_launches(1);
+    if (e == cudaSuccess)
+        e = cudaMemcpyAsync(ctx->host_scalar, ctx->scalar, sizeof(double), cudaMemcpyDeviceToHost, ctx->stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(ctx->stream);
+    if (e != cudaSuccess) return ctx_cuda(ctx, e, "norm");
+    *out = sqrt(*ctx->host_scalar);
+    return EXCMG_OK;
+}
+
+// Norm of b - A x over the unknowns (boundary entries of the work vector are
+// zero, so a flat norm over all nodes equals it).
+int true_residual_norm(excmg_ctx* ctx, int n, int bc_kind, const double* b, const double* x,
+                       double* out) {
+    const size_t len = node_count(n);
+    int st = EXCMG_OK;
+    double* r = ctx_buffer(ctx, "res", len * sizeof(double), &st);
+    if (st) return st;
+    cudaError_t e = cudaMemsetAsync(r, 0, len * sizeof(double), ctx->stream);
+    if (e == cudaSuccess) e = launch_stencil(x, r, b, n, bc_kind, false, nullptr, ctx->stream, ctx->stencil_variant);
+    if (e != cudaSuccess) return ctx_cuda(ctx, e, "residual");
+    note_launches(1);
+    return interior_norm(ctx, n, r, out);
+}
+
+int bicg_run(excmg_ctx* ctx, int n, int bc_kind, const double* b, double* x, double tol,
+             double bnorm, int max_iter, int check_every, int* iters_out, double* relres_out) {
+    const size_t len = node_count(n);
+    const size_t bytes = len * sizeof(double);
+    int st = EXCMG_OK;
+    double* r = ctx_buffer(ctx, "bicg_r", bytes, &st);
+    double* rs = st ? nullptr : ctx_buffer(ctx, "bicg_rs", bytes, &st);
+    double* p = st ? nullptr : ctx_buffer(ctx, "bicg_p", bytes, &st);
+    double* ps = st ? nullptr : ctx_buffer(ctx, "bicg_ps", bytes, &st);
+    double* q = st ? nullptr : ctx_buffer(ctx, "bicg_q", bytes, &st);
+    double* qs = st ? nullptr : ctx_buffer(ctx, "bicg_qs", bytes, &st);
+    if (st) return st;
+    cudaStream_t s = ctx->stream;
+    if (check_every < 1) check_every = 1;
+
+    BicgState init{};
+    init.bnorm = bnorm;
+    init.tol = tol;
+    init.max_iter = max_iter;
+    *ctx->host_state = init;
+    cudaError_t e = cudaMemcpyAsync(ctx->state, ctx->host_state, sizeof(BicgState), cudaMemcpyHostToDevice, s);
+    // boundary entries of every work vector stay zero: the stencils write
+    // interior entries only
+    if (e == cudaSuccess) e = cudaMemsetAsync(r, 0, bytes, s);
+    if (e == cudaSuccess) e = cudaMemsetAsync(q, 0, bytes, s);
+    if (e == cudaSuccess) e = cudaMemsetAsync(qs, 0, bytes, s);
+    // r_0 = b - A x_0; r*_0 = p_0 = p*_0 = r_0; rho_0
+    if (e == cudaSuccess) e = launch_stencil(x, r, b, n, bc_kind, false, nullptr, s, ctx->stencil_variant);
+    if (e == cudaSuccess) e = launch_bicg_init(r, rs, p, ps, len, ctx->partials, ctx->state, s);
+    if (e != cudaSuccess) return ctx_cuda(ctx, e, "Bi-CG setup");
+
+    const int* done = &ctx->state->done;
+    note_launches(2);   // residual stencil + init (the memsets are not kernels)
+    int batch = 0;
+    int iter_before = 0;
+    for (;;) {
+        e = cudaMemcpyAsync(ctx->host_state, ctx->state, sizeof(BicgState), cudaMemcpyDeviceToHost, s);
+        if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+        if (e != cudaSuccess) return ctx_cuda(ctx, e, "Bi-CG state read");
+        if (ctx->profile && batch > 0) {
+            // credit only the iterations of the last batch that really ran
+            const int ran = ctx->host_state->iter - iter_before;
+            auto& rec = ctx->prof[n];
+            for (int it = 0; it < ran && it < batch; ++it) {
+                float a = 0.f, b2 = 0.f;
+                cudaEventElapsedTime(&a, ctx->prof_events[3 * it], ctx->prof_events[3 * it + 1]);
+                cudaEventElapsedTime(&b2, ctx->prof_events[3 * it + 1], ctx->prof_events[3 * it + 2]);
+                rec.first += (double)a + (double)b2;
+                rec.second += 2;
+            }
+        }
+        if (ctx->host_state->done) break;
+        iter_before = ctx->host_state->iter;
+        batch = check_every;
+        const int left = max_iter - ctx->host_state->iter;
+        if (batch > left) batch = left;
+        if (ctx->profile) {
+            while ((int)ctx->prof_events.size() < 3 * batch) {
+                cudaEvent_t ev;
+                if (cudaEventCreate(&ev) != cudaSuccess) return ctx_cuda(ctx, cudaGetLastError(), "event");
+                ctx->prof_events.push_back(ev);
+            }
+        }
+        for (int it = 0; it < batch && e == cudaSuccess; ++it) {
+            if (ctx->profile) cudaEventRecord(ctx->prof_events[3 * it], s);
+            e = launch_stencil(p, q, nullptr, n, bc_kind, false, done, s, ctx->stencil_variant);  // A p_k
+            if (ctx->profile) cudaEventRecord(ctx->prof_events[3 * it + 1], s);
+            if (e == cudaSuccess)
+                e = launch_stencil(ps, qs, nullptr, n, bc_kind, true, done, s, ctx->stencil_variant);  // A^T p*_k
+            if (ctx->profile) cudaEventRecord(ctx->prof_events[3 * it + 2], s);
+            if (e == cudaSuccess) e = launch_bicg_sigma(ps, q, len, ctx->partials, ctx->state, s);
+            if (e == cudaSuccess)
+                e = launch_bicg_update(x, p, r, q, rs, qs, len, ctx->partials, ctx->state, s);
+            if (e == cudaSuccess) e = launch_bicg_pupdate(p, r, ps, rs, len, ctx->state, s);
+        }
+        note_launches(5LL * batch);
+        if (e != cudaSuccess) return ctx_cuda(ctx, e, "Bi-CG iteration");
+    }
+    const BicgState& h = *ctx->host_state;
+    if (iters_out) *iters_out = h.iter;
+    const double rn = sqrt(h.rr);
+    if (relres_out) *relres_out = bnorm > 0.0 ? rn / bnorm : rn;
+    if (!std::isfinite(h.rr)) return ctx_fail(ctx, EXCMG_ERR_NAN, "Bi-CG residual is not finite");
+    if (h.status == kBreakdown) return ctx_fail(ctx, EXCMG_ERR_BREAKDOWN, "Bi-CG breakdown");
+    if (h.status == kCapped) return EXCMG_ERR_NOCONV;
+    return EXCMG_OK;
+}
+
+}  // namespace excmg

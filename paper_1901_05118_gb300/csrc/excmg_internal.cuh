@@ -1,0 +1,145 @@
+// Internal declarations shared by the CUDA translation units of the library.
+// Nothing here is part of the C ABI (include/excmg.h is).
+#pragma once
+
+#include <cuda_runtime.h>
+
+#include <cstddef>
+#include <cstdint>
+#include <map>
+#include <string>
+#include <utility>
+#include <vector>
+
+#include "excmg.h"
+
+namespace excmg {
+
+// ------------------------------------------------------------------ sizes
+inline size_t node_count(int n) { return (size_t)(n + 1) * (size_t)(n + 1) * (size_t)(n + 1); }
+inline size_t face_count(int n) { return 6 * (size_t)(n + 1) * (size_t)(n + 1); }
+
+// Grid-stride launches of the flat vector kernels use a fixed grid so that
+// their reductions always combine the same partial sums in the same order.
+constexpr int kVecThreads = 256;
+constexpr int kVecBlocks = 152 * 4;     // 4 CTAs on each of GB300's 152 SMs
+constexpr int kMaxPartials = 2 * kVecBlocks;
+
+// Bi-CG state kept on the device so that a whole iteration runs without the
+// host (Alg. 2 with M = I).
+struct BicgState {
+    double rho;        // (r*_k, r_k)
+    double sigma;      // (p*_k, A p_k)
+    double alpha;
+    double beta;
+    double rr;         // (r_k, r_k)
+    double bnorm;      // ||b||_2 of the stopping test
+    double tol;        // relative tolerance of the stopping test
+    double pad0;
+    int iter;
+    int max_iter;
+    int done;          // 1 once converged, capped or broken down
+    int status;        // kRunning / kConverged / kCapped / kBreakdown
+    unsigned int ticket;   // last-block counter of the reductions
+    int pad1[3];
+};
+enum { kRunning = 0, kConverged = 1, kCapped = 2, kBreakdown = 3 };
+
+// ------------------------------------------------------------- kernels
+// Stencil (eq. (method1) + reflections): y = A u, or y = b - A u when b is
+// non-null.  Writes interior entries of y only.  Returns immediately when
+// *skip is non-zero (skip may be null).
+enum { kStencilExact = 0, kStencilFp64 = 1 };
+cudaError_t launch_stencil(const double* u, double* y, const double* b, int n, int bc_kind,
+                           bool transpose, const int* skip, cudaStream_t s, int variant);
+cudaError_t launch_zero_boundary(double* y, int n, cudaStream_t s);
+
+// Vectors (flat over all (n+1)^3 entries; boundary entries of the Bi-CG
+// vectors are zero, so flat sums equal sums over the unknowns).
+cudaError_t launch_dot(const double* a, const double* b, size_t len, double* partials,
+                       unsigned int* ticket, double* out, cudaStream_t s);
+cudaError_t launch_bicg_init(const double* r, double* rs, double* p, double* ps, size_t len,
+                             double* partials, BicgState* st, cudaStream_t s);
+cudaError_t launch_bicg_sigma(const double* ps, const double* q, size_t len, double* partials,
+                              BicgState* st, cudaStream_t s);
+cudaError_t launch_bicg_update(double* x, const double* p, double* r, const double* q, double* rs,
+                               const double* qs, size_t len, double* partials, BicgState* st,
+                               cudaStream_t s);
+cudaError_t launch_bicg_pupdate(double* p, const double* r, double* ps, const double* rs, size_t len,
+                                const BicgState* st, cudaStream_t s);
+
+// Right-hand side and boundary data for a level with n intervals taken at
+// every stride-th node of arrays with n*stride intervals.
+cudaError_t launch_assemble_rhs(double* fh, int n, int bc_kind, const double* f, const double* g1,
+                                const double* g2, int stride, cudaStream_t s);
+cudaError_t launch_set_boundary(double* u, int n, const double* g1, int stride, cudaStream_t s);
+
+// Level transfer.
+cudaError_t launch_exp_finite(double* w, const double* u1, const double* u0, double* W_scratch,
+                              int n_fine, cudaStream_t s);
+cudaError_t launch_exp_true(double* ut, const double* uh, const double* u2h, int n_fine,
+                            cudaStream_t s);
+
+// DSOLVE: dense inverse of A_h (unknowns in lexicographic order, x fastest)
+// and its application.
+cudaError_t launch_dense_assemble(double* A, int n, int bc_kind, cudaStream_t s);
+cudaError_t launch_gauss_jordan_step(double* A, int m, int k, double* rowk, double* colk,
+                                     cudaStream_t s);
+cudaError_t launch_dense_apply(const double* Ainv, const double* fh, double* u, int n,
+                               cudaStream_t s);
+
+}  // namespace excmg
+
+// ------------------------------------------------------------ context
+struct excmg_buffer {
+    void* ptr = nullptr;
+    size_t bytes = 0;
+};
+
+struct excmg_ctx {
+    int device = 0;
+    cudaStream_t stream = nullptr;
+    size_t budget = 0;           // 0 = unlimited
+    size_t bytes = 0;            // currently held
+    std::string last_error;
+    // named, growable workspace buffers
+    std::map<std::string, excmg_buffer> buffers;
+    // DSOLVE inverses keyed by (n, bc_kind)
+    std::map<std::pair<int, int>, excmg_buffer> inverses;
+    // small device scratch for reductions and the Bi-CG state
+    double* partials = nullptr;
+    unsigned int* ticket = nullptr;
+    double* scalar = nullptr;                 // one-off reduction results (8 doubles)
+    excmg::BicgState* state = nullptr;        // device
+    excmg::BicgState* host_state = nullptr;   // pinned host mirror
+    double* host_scalar = nullptr;            // pinned host mirror of `scalar`
+    int stencil_variant = excmg::kStencilExact;
+    // optional timing of the operator launches inside Bi-CG
+    bool profile = false;
+    std::vector<cudaEvent_t> prof_events;
+    std::map<int, std::pair<double, long long>> prof;   // n -> (ms, launches)
+};
+
+struct excmg_level {
+    excmg_ctx* ctx;
+    int n;
+    int bc_kind;
+};
+
+namespace excmg {
+// Process-wide count of kernel launches made by the library (capi.cu).
+void note_launches(long long k);
+// Workspace helpers (capi.cu).
+int ctx_fail(excmg_ctx* ctx, int status, const std::string& msg);
+int ctx_cuda(excmg_ctx* ctx, cudaError_t err, const char* what);
+double* ctx_buffer(excmg_ctx* ctx, const char* name, size_t bytes, int* status);
+// Bi-CG driver (bicg.cu): iterates on the context's stream.
+int bicg_run(excmg_ctx* ctx, int n, int bc_kind, const double* b, double* x, double tol,
+             double bnorm, int max_iter, int check_every, int* iters_out, double* relres_out);
+// ||b - A x||_2 over the unknowns, via the context's workspace (result on host).
+int true_residual_norm(excmg_ctx* ctx, int n, int bc_kind, const double* b, const double* x,
+                       double* out);
+int interior_norm(excmg_ctx* ctx, int n, const double* a, double* out);
+// DSOLVE (dsolve.cu)
+int dsolve_run(excmg_ctx* ctx, int n, int bc_kind, const double* fh, double* u);
+}  // namespace excmg

@@ -1,0 +1,225 @@
+// Vector kernels of Bi-CG (Alg. 2, M = I): the inner products, the iterate
+// and residual updates and the direction updates, with the scalars alpha and
+// beta formed on the device.
+//
+// Reductions are deterministic: a fixed grid (kVecBlocks x kVecThreads)
+// walks the vectors with a grid stride, each CTA reduces its values by a
+// fixed shuffle tree, and the last CTA to finish (atomic ticket) adds the
+// per-CTA partials in CTA order.  The same inputs therefore always give the
+// same bits, independent of scheduling.
+#include "excmg_internal.cuh"
+
+namespace excmg {
+namespace {
+
+__device__ __forceinline__ double warp_sum(double v) {
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
+    return v;
+}
+
+// Sum of v over the CTA (valid in thread 0).
+__device__ __forceinline__ double block_sum(double v, double* sh) {
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+    v = warp_sum(v);
+    if (lane == 0) sh[wid] = v;
+    __syncthreads();
+    double t = 0.0;
+    if (wid == 0) {
+        t = lane < (int)(blockDim.x >> 5) ? sh[lane] : 0.0;
+        t = warp_sum(t);
+    }
+    __syncthreads();
+    return t;
+}
+
+// Publish this CTA's partial sums (count values) and report whether this
+// CTA is the last one to do so.
+__device__ __forceinline__ bool publish_partials(const double* vals, int count, double* partials,
+                                                 unsigned int* ticket, bool* am_last) {
+    if (threadIdx.x == 0) {
+        for (int c = 0; c < count; ++c) partials[c * gridDim.x + blockIdx.x] = vals[c];
+        __threadfence();
+        const unsigned int t = atomicAdd(ticket, 1u);
+        *am_last = (t == gridDim.x - 1);
+    }
+    __syncthreads();
+    return *am_last;
+}
+
+// In the last CTA: the total of component c over all CTAs, in CTA order.
+__device__ __forceinline__ double gather_partials(const double* partials, int c, double* sh) {
+    double v = 0.0;
+    for (int b = threadIdx.x; b < (int)gridDim.x; b += blockDim.x)
+        v += __ldcg(&partials[c * gridDim.x + b]);
+    return block_sum(v, sh);
+}
+
+__global__ void __launch_bounds__(kVecThreads)
+dot_kernel(const double* __restrict__ a, const double* __restrict__ b, size_t len,
+           double* partials, unsigned int* ticket, double* out) {
+    __shared__ double sh[32];
+    __shared__ bool am_last;
+    double v = 0.0;
+    for (size_t t = blockIdx.x * (size_t)blockDim.x + threadIdx.x; t < len;
+         t += (size_t)gridDim.x * blockDim.x)
+        v += a[t] * b[t];
+    double s = block_sum(v, sh);
+    if (publish_partials(&s, 1, partials, ticket, &am_last)) {
+        const double tot = gather_partials(partials, 0, sh);
+        if (threadIdx.x == 0) {
+            *out = tot;
+            *ticket = 0;
+        }
+    }
+}
+
+// r*_0 = r_0, p_0 = r_0, p*_0 = r*_0; rho_0 = (r*_0, r_0), rr = (r_0, r_0).
+__global__ void __launch_bounds__(kVecThreads)
+bicg_init_kernel(const double* __restrict__ r, double* __restrict__ rs, double* __restrict__ p,
+                 double* __restrict__ ps, size_t len, double* partials, BicgState* st) {
+    __shared__ double sh[32];
+    __shared__ bool am_last;
+    double v = 0.0;
+    for (size_t t = blockIdx.x * (size_t)blockDim.x + threadIdx.x; t < len;
+         t += (size_t)gridDim.x * blockDim.x) {
+        const double rv = r[t];
+        rs[t] = rv;
+        p[t] = rv;
+        ps[t] = rv;
+        v += rv * rv;
+    }
+    double s = block_sum(v, sh);
+    if (publish_partials(&s, 1, partials, &st->ticket, &am_last)) {
+        const double tot = gather_partials(partials, 0, sh);
+        if (threadIdx.x == 0) {
+            st->rho = tot;   // (r*_0, r_0) with r*_0 = r_0
+            st->rr = tot;
+            st->iter = 0;
+            st->alpha = st->beta = st->sigma = 0.0;
+            const bool conv = sqrt(tot) <= st->tol * st->bnorm;
+            st->done = (conv || st->max_iter <= 0) ? 1 : 0;
+            st->status = conv ? kConverged : (st->max_iter <= 0 ? kCapped : kRunning);
+            st->ticket = 0;
+        }
+    }
+}
+
+// sigma_k = (p*_k, A p_k); alpha_k = rho_k / sigma_k.
+__global__ void __launch_bounds__(kVecThreads)
+bicg_sigma_kernel(const double* __restrict__ ps, const double* __restrict__ q, size_t len,
+                  double* partials, BicgState* st) {
+    if (st->done) return;
+    __shared__ double sh[32];
+    __shared__ bool am_last;
+    double v = 0.0;
+    for (size_t t = blockIdx.x * (size_t)blockDim.x + threadIdx.x; t < len;
+         t += (size_t)gridDim.x * blockDim.x)
+        v += ps[t] * q[t];
+    double s = block_sum(v, sh);
+    if (publish_partials(&s, 1, partials, &st->ticket, &am_last)) {
+        const double sigma = gather_partials(partials, 0, sh);
+        if (threadIdx.x == 0) {
+            const double rho = st->rho;
+            st->sigma = sigma;
+            if (!(rho != 0.0 && isfinite(rho)) || !(sigma != 0.0 && isfinite(sigma))) {
+                st->status = kBreakdown;
+                st->done = 1;
+            } else {
+                st->alpha = rho / sigma;
+            }
+            st->ticket = 0;
+        }
+    }
+}
+
+// x += alpha p; r -= alpha A p; r* -= alpha A^T p*;
+// rho_{k+1} = (r*, r), beta = rho_{k+1} / rho_k; stopping test on ||r||.
+__global__ void __launch_bounds__(kVecThreads)
+bicg_update_kernel(double* __restrict__ x, const double* __restrict__ p, double* __restrict__ r,
+                   const double* __restrict__ q, double* __restrict__ rs,
+                   const double* __restrict__ qs, size_t len, double* partials, BicgState* st) {
+    if (st->done) return;
+    __shared__ double sh[32];
+    __shared__ bool am_last;
+    const double alpha = st->alpha;
+    double vr = 0.0, vrr = 0.0;
+    for (size_t t = blockIdx.x * (size_t)blockDim.x + threadIdx.x; t < len;
+         t += (size_t)gridDim.x * blockDim.x) {
+        x[t] = x[t] + alpha * p[t];
+        const double rn = r[t] - alpha * q[t];
+        const double rsn = rs[t] - alpha * qs[t];
+        r[t] = rn;
+        rs[t] = rsn;
+        vr += rsn * rn;
+        vrr += rn * rn;
+    }
+    double s[2];
+    s[0] = block_sum(vr, sh);
+    s[1] = block_sum(vrr, sh);
+    if (publish_partials(s, 2, partials, &st->ticket, &am_last)) {
+        const double rho_new = gather_partials(partials, 0, sh);
+        const double rr = gather_partials(partials, 1, sh);
+        if (threadIdx.x == 0) {
+            st->beta = rho_new / st->rho;
+            st->rho = rho_new;
+            st->rr = rr;
+            st->iter += 1;
+            if (sqrt(rr) <= st->tol * st->bnorm) {
+                st->status = kConverged;
+                st->done = 1;
+            } else if (st->iter >= st->max_iter) {
+                st->status = kCapped;
+                st->done = 1;
+            }
+            st->ticket = 0;
+        }
+    }
+}
+
+// p_{k+1} = r_{k+1} + beta p_k; p*_{k+1} = r*_{k+1} + beta p*_k.
+__global__ void __launch_bounds__(kVecThreads)
+bicg_pupdate_kernel(double* __restrict__ p, const double* __restrict__ r, double* __restrict__ ps,
+                    const double* __restrict__ rs, size_t len, const BicgState* st) {
+    if (st->done) return;
+    const double beta = st->beta;
+    for (size_t t = blockIdx.x * (size_t)blockDim.x + threadIdx.x; t < len;
+         t += (size_t)gridDim.x * blockDim.x) {
+        p[t] = r[t] + beta * p[t];
+        ps[t] = rs[t] + beta * ps[t];
+    }
+}
+
+}  // namespace
+
+cudaError_t launch_dot(const double* a, const double* b, size_t len, double* partials,
+                       unsigned int* ticket, double* out, cudaStream_t s) {
+    dot_kernel<<<kVecBlocks, kVecThreads, 0, s>>>(a, b, len, partials, ticket, out);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_bicg_init(const double* r, double* rs, double* p, double* ps, size_t len,
+                             double* partials, BicgState* st, cudaStream_t s) {
+    bicg_init_kernel<<<kVecBlocks, kVecThreads, 0, s>>>(r, rs, p, ps, len, partials, st);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_bicg_sigma(const double* ps, const double* q, size_t len, double* partials,
+                              BicgState* st, cudaStream_t s) {
+    bicg_sigma_kernel<<<kVecBlocks, kVecThreads, 0, s>>>(ps, q, len, partials, st);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_bicg_update(double* x, const double* p, double* r, const double* q, double* rs,
+                               const double* qs, size_t len, double* partials, BicgState* st,
+                               cudaStream_t s) {
+    bicg_update_kernel<<<kVecBlocks, kVecThreads, 0, s>>>(x, p, r, q, rs, qs, len, partials, st);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_bicg_pupdate(double* p, const double* r, double* ps, const double* rs, size_t len,
+                                const BicgState* st, cudaStream_t s) {
+    bicg_pupdate_kernel<<<kVecBlocks, kVecThreads, 0, s>>>(p, r, ps, rs, len, st);
+    return cudaGetLastError();
+}
+
+}  // namespace excmg

@@ -1,0 +1,256 @@
+"""Parity of the CUDA path (through the C ABI) with the CPU oracle.
+
+Tolerances: a single operator application must match within 1e-12 relative
+in the max norm; on smooth inputs (where A u is tiny next to its terms) the
+yardstick is 1e-12 * max |A||u|, i.e. 1e-12 * 144 max|u|.  Transfers are
+evaluated to rounding (1e-13 relative).  Full solves must match within 1e-9
+relative in the max norm.
+"""
+import numpy as np
+import pytest
+
+import oracle
+from paper_1901_05118_gb300 import problems as P
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+if not torch.cuda.is_available():  # pragma: no cover - collected on CPU machines only
+    pytest.skip("needs a CUDA GPU", allow_module_level=True)
+
+from paper_1901_05118_gb300 import binding as B  # noqa: E402
+
+DEV = torch.device("cuda", 0)
+
+
+def dev(a):
+    return torch.from_numpy(np.array(a, dtype=np.float64, order="C")).to(DEV)
+
+
+def host(t):
+    torch.cuda.synchronize()
+    return t.cpu().numpy()
+
+
+def rel_max(a, b):
+    d = np.abs(a - b).max()
+    s = np.abs(b).max()
+    return d / s if s > 0 else d
+
+
+# ------------------------------------------------------------ operator
+VARIANTS = ["exact", "fp64"]
+
+
+def level(n, bc_kind, variant="exact"):
+    ctx = B.Context()
+    ctx.set_stencil(variant)
+    return B.Level(n, bc_kind, ctx)
+
+
+@pytest.mark.parametrize("variant", VARIANTS)
+@pytest.mark.parametrize("n", [4, 5, 8, 33, 64])
+@pytest.mark.parametrize("bc_kind", [1, 2])
+@pytest.mark.parametrize("transpose", [False, True])
+def test_stencil_random(n, bc_kind, transpose, variant):
+    u = P.random_field(n, 100 + n)   # boundary entries non-zero: must be ignored
+    lvl = level(n, bc_kind, variant)
+    y = host(B.stencil_apply(lvl, dev(u), transpose=transpose))
+    ref = oracle.stencil_apply(n, bc_kind, u, transpose=transpose)
+    assert rel_max(y, ref) <= 1e-12
+    mask = np.ones_like(y, dtype=bool)
+    mask[1:-1, 1:-1, 1:-1] = False
+    assert np.all(y[mask] == 0.0)
+
+
+@pytest.mark.parametrize("variant", VARIANTS)
+@pytest.mark.parametrize("n,bc_kind", [(48, 1), (48, 2)])
+def test_stencil_smooth(n, bc_kind, variant):
+    u = P.exp_sum().exact(n)
+    lvl = level(n, bc_kind, variant)
+    y = host(B.stencil_apply(lvl, dev(u)))
+    ref = oracle.stencil_apply(n, bc_kind, u)
+    assert np.abs(y - ref).max() <= 1e-12 * 144 * np.abs(u).max()
+
+
+def test_stencil_full_size_512():
+    """The workload's size (512 intervals: 511^3 unknowns), both kinds, both
+    arithmetic variants, and A^T."""
+    n = 512
+    u = P.random_field(n, 7)
+    du = dev(u)
+    for bc in (1, 2):
+        ref = oracle.stencil_apply(n, bc, u)
+        for variant in VARIANTS:
+            lvl = level(n, bc, variant)
+            y = host(B.stencil_apply(lvl, du))
+            assert rel_max(y, ref) <= 1e-12
+        yt = host(B.stencil_apply(level(n, bc), du, transpose=True))
+        assert rel_max(yt, ref) <= 1e-12
+
+
+def test_stencil_exact_variant_is_order_free():
+    """The integer variant sums exactly, so A u and the mirrored-tap gather
+    A^T u agree bit for bit (A_h is symmetric)."""
+    n = 40
+    u = dev(P.random_field(n, 77))
+    lvl = level(n, 1)
+    assert torch.equal(B.stencil_apply(lvl, u), B.stencil_apply(lvl, u, transpose=True))
+
+
+def test_stencil_wide_dynamic_range():
+    """Inputs spanning 1e-300 .. 1e300 (and zeros) stay within the error
+    bound relative to the largest magnitude each block reads."""
+    n = 24
+    rng = np.random.Generator(np.random.PCG64(5))
+    u = rng.uniform(-1, 1, (n + 1,) * 3) * 10.0 ** rng.integers(-300, 300, (n + 1,) * 3)
+    u[rng.uniform(size=u.shape) < 0.2] = 0.0
+    ref = oracle.stencil_apply(n, 2, u)
+    y = host(B.stencil_apply(level(n, 2), dev(u)))
+    assert np.abs(y - ref).max() <= 1e-13 * np.abs(u).max()
+    tiny = P.random_field(n, 8) * 1e-310   # subnormal inputs
+    ref = oracle.stencil_apply(n, 1, tiny)
+    y = host(B.stencil_apply(level(n, 1), dev(tiny)))
+    assert np.abs(y - ref).max() <= 1e-13 * np.abs(tiny).max() + 1e-323
+
+
+def test_stencil_nonfinite_propagates():
+    n = 16
+    u = P.random_field(n, 9)
+    u[8, 8, 8] = np.nan
+    y = host(B.stencil_apply(level(n, 1), dev(u)))
+    assert np.isnan(y[8, 8, 8])
+
+
+# ----------------------------------------------------- right-hand side
+@pytest.mark.parametrize("n,stride", [(4, 1), (8, 2), (13, 1), (16, 4)])
+@pytest.mark.parametrize("bc_kind", [1, 2])
+def test_assemble_rhs(n, stride, bc_kind):
+    ns = n * stride
+    prob = P.paper_problem2()
+    f, g1, g2 = prob.data(ns, bc_kind)
+    lvl = B.Level(n, bc_kind)
+    fh = host(B.excmg_assemble_rhs(lvl, ns, dev(f), dev(g1), dev(g2)))
+    ref = oracle.assemble_rhs(n, bc_kind, oracle.inject_nodes(ns, stride, f), oracle.inject_nodes(ns, stride, g1),
+                              oracle.inject_faces(ns, stride, g2))
+    assert np.abs(fh - ref).max() <= 1e-13 * max(1.0, np.abs(ref).max())
+
+
+# ---------------------------------------------------------- transfers
+@pytest.mark.parametrize("nf", [8, 16, 40])
+def test_extrapolate_interpolate(nf):
+    u1 = P.random_field(nf // 2, 1 + nf)
+    u0 = P.random_field(nf // 4, 2 + nf)
+    w = host(B.extrapolate_interpolate(nf, dev(u1), dev(u0)))
+    ref = oracle.exp_finite(nf, u1, u0)
+    assert rel_max(w, ref) <= 1e-13
+
+
+@pytest.mark.parametrize("nf", [4, 10, 64])
+def test_midpoint_extrapolate(nf):
+    uh = P.random_field(nf, 3 + nf)
+    u2 = P.random_field(nf // 2, 4 + nf)
+    ut = host(B.midpoint_extrapolate(nf, dev(uh), dev(u2)))
+    ref = oracle.exp_true(nf, uh, u2)
+    assert rel_max(ut, ref) <= 1e-13
+
+
+# ------------------------------------------------------------ DSOLVE
+@pytest.mark.parametrize("n", [4, 8, 16])
+@pytest.mark.parametrize("bc_kind", [1, 2])
+def test_dsolve(n, bc_kind):
+    fh = P.random_field(n, 9)
+    fh[0] = fh[-1] = 0.0
+    lvl = B.Level(n, bc_kind)
+    u = torch.zeros((n + 1,) * 3, dtype=torch.float64, device=DEV)
+    got = host(B.excmg_dsolve(lvl, dev(fh), u))
+    ref = oracle.dsolve(n, bc_kind, fh, np.zeros_like(fh))
+    assert rel_max(got, ref) <= 1e-10
+
+
+# ------------------------------------------------------------- Bi-CG
+@pytest.mark.parametrize("n,bc_kind", [(12, 1), (17, 2)])
+def test_bicg(n, bc_kind):
+    b = P.random_field(n, 31)
+    x0 = P.random_field(n, 32) * 0.1
+    lvl = B.Level(n, bc_kind)
+    x = dev(x0)
+    it, rel, rc = B.bicg_solve(lvl, dev(b), x, 1e-12, 5000)
+    xr, itr, relr, rcr = oracle.bicg(n, bc_kind, b, x0, 1e-12)
+    assert rc == 0 and rcr == 0
+    assert abs(it - itr) <= 2
+    assert rel <= 1e-12
+    assert rel_max(host(x), xr) <= 1e-9
+
+
+# ---------------------------------------------------------- full solve
+@pytest.mark.parametrize("name,bc_kind,variant", [("sin_pi", 1, "exact"), ("exp_sum", 1, "exact"),
+                                                   ("exp_sum", 2, "exact"), ("paper_p4", 1, "exact"),
+                                                   ("sin_pi", 1, "fp64"), ("exp_sum", 2, "fp64")])
+def test_excmg_solve_matches_oracle(name, bc_kind, variant):
+    """The small workload: 4^3 .. 32^3, tol 1e-10 on every level."""
+    n, nc = 32, 4
+    prob = P.by_name(name)
+    f, g1, g2 = prob.data(n, bc_kind)
+    uh = torch.empty((n + 1,) * 3, dtype=torch.float64, device=DEV)
+    ctx = B.Context()
+    ctx.set_stencil(variant)
+    ut, stats = B.excmg_solve(n, nc, bc_kind, dev(f), dev(g1), dev(g2), 1e-10, u_h_out=uh, return_stats=True,
+                              ctx=ctx)
+    ref_h, ref_t, ref_stats = oracle.excmg(n, nc, bc_kind, f, g1, g2, 1e-10)
+    assert rel_max(host(uh), ref_h) <= 1e-9
+    assert rel_max(host(ut), ref_t) <= 1e-9
+    for l, s in enumerate(stats):
+        assert s["relres"] <= 1e-10 or s["stagnated"]
+        # iteration counts are not pinned by the paper; rounding differences
+        # shift them slightly over hundreds of iterations
+        assert abs(s["iters"] - ref_stats[l, 0]) <= max(3, 0.05 * ref_stats[l, 0])
+
+
+def test_excmg_exact_for_triquadratic():
+    prob = P.polynomial([0.5, -0.3, 0.8], [1.0, 0.2, -0.6], [0.1, 0.7, 0.3])
+    n = 32
+    f, g1, g2 = prob.data(n, 1)
+    uh = torch.empty((n + 1,) * 3, dtype=torch.float64, device=DEV)
+    ut, stats = B.excmg_solve(n, 4, 1, dev(f), dev(g1), dev(g2), 1e-12, u_h_out=uh, return_stats=True)
+    ue = prob.exact(n)
+    assert np.abs(host(uh) - ue).max() <= 1e-11
+    assert np.abs(host(ut) - ue).max() <= 1e-11
+    assert all(s["iters"] == 0 for s in stats)
+
+
+def test_excmg_paper_table_rows_64():
+    """Tables 1-2 rows at 32^3 and 64^3 through the GPU path (8^3, 16^3 solved
+    directly as in the paper)."""
+    import json
+    import os
+    gold = json.load(open(os.path.join(os.path.dirname(__file__), "golden", "paper_tables.json")))["problems"]
+    for name in ("paper_p1", "paper_p2"):
+        prob = P.by_name(name)
+        n = 64
+        f, g1, g2 = prob.data(n, 1)
+        uh = torch.empty((n + 1,) * 3, dtype=torch.float64, device=DEV)
+        B.excmg_solve(n, 8, 1, dev(f), dev(g1), dev(g2), 1e-11, u_h_out=uh)
+        e = host(uh) - prob.exact(n)
+        l2 = np.sqrt((e ** 2).mean())
+        linf = np.abs(e).max()
+        assert l2 == pytest.approx(gold[name]["rows"]["64"]["l2"], rel=0.006)
+        assert linf == pytest.approx(gold[name]["rows"]["64"]["linf"], rel=0.006)
+
+
+# ------------------------------------------------------------ errors
+def test_bad_arguments_raise():
+    lvl = B.Level(8, 1)
+    u = torch.zeros(9 ** 3, dtype=torch.float64, device=DEV)
+    with pytest.raises(B.ExcmgError):
+        B.stencil_apply(lvl, u, u)
+    with pytest.raises(ValueError):
+        B.stencil_apply(lvl, torch.zeros(10, dtype=torch.float64, device=DEV))
+    f = torch.zeros((17,) * 3, dtype=torch.float64, device=DEV)
+    g2 = torch.zeros((6, 17, 17), dtype=torch.float64, device=DEV)
+    with pytest.raises(B.ExcmgError):
+        B.excmg_solve(16, 3, 1, f, f, g2, 1e-8)   # coarsest below 4
+    with pytest.raises(B.ExcmgError):
+        B.excmg_solve(16, 8, 1, f, f, g2, 1e-8)   # L = 0
+    with pytest.raises(B.ExcmgError):
+        B.excmg_solve(16, 4, 3, f, f, g2, 1e-8)   # bc_kind
