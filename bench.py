@@ -63,6 +63,24 @@ def dist_env():
     return rank, world, local
 
 
+def max_over_ranks(x: float, world: int, device=None) -> float:
+    """The largest of every rank's x (a timing): the job takes as long as its
+    slowest replica."""
+    if world <= 1:
+        return float(x)
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([float(x)], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def seconds_per_solve(ms_per_step_max: float, solves_per_step: int, world: int) -> float:
+    """Whole-job seconds per solve: every replica runs solves_per_step solves
+    per step, so the job finishes world * solves_per_step solves per step."""
+    return ms_per_step_max / 1e3 / (solves_per_step * world)
+
+
 # ------------------------------------------------------------------ clocks
 class ClockSampler:
     """nvidia-smi samples of SM clock and throttle reasons while running."""
@@ -244,12 +262,8 @@ def run_ours(args):
     launches = B.launch_count() - launches0
     st_ms, st_cnt = ctx.profile_read(n)
     ctx.profile(False)
-    ms_step = ms_total / args.steps
-    if world > 1:
-        t = torch.tensor([ms_step], device=dev)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        ms_step = float(t.item())
-    value = ms_step / 1e3 / (len(bcs) * world)   # seconds per solve, whole job
+    ms_step = max_over_ranks(ms_total / args.steps, world, dev)
+    value = seconds_per_solve(ms_step, len(bcs), world)
 
     # ---- end to end through the C ABI, host buffers
     e2e = None
@@ -269,12 +283,8 @@ def run_ours(args):
                 u_host.copy_(u_out, non_blocking=True)
         e3.record(stream)
         barrier()
-        ms_e2e = e2.elapsed_time(e3) / args.steps
-        if world > 1:
-            t = torch.tensor([ms_e2e], device=dev)
-            dist.all_reduce(t, op=dist.ReduceOp.MAX)
-            ms_e2e = float(t.item())
-        e2e = {"value": ms_e2e / 1e3 / (len(bcs) * world), "unit": "s",
+        ms_e2e = max_over_ranks(e2.elapsed_time(e3) / args.steps, world, dev)
+        e2e = {"value": seconds_per_solve(ms_e2e, len(bcs), world), "unit": "s",
                "h2d_bytes_per_step": h2d * len(bcs), "d2h_bytes_per_step": d2h * len(bcs)}
 
     # ---- roofline of the operator kernel on the finest grid

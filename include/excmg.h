@@ -58,12 +58,21 @@ typedef struct excmg_level excmg_level;  /* one grid: (context, N, bc_kind)     
  * (Alg. 1, line 5); EXCMG_TOL_UNIFORM uses eps_i = tol on every level. */
 enum { EXCMG_TOL_PAPER = 0, EXCMG_TOL_UNIFORM = 1 };
 
+/* Arithmetic of the Bi-CG levels.  EXCMG_PRECISION_FP64: Alg. 2 in FP64.
+ * EXCMG_PRECISION_MIXED: FP64 iterative refinement -- the true residual
+ * r = f_h - A u, the update u += ||r|| e, the stopping test of Alg. 1 and the
+ * extrapolation steps in FP64 -- around Bi-CG (Alg. 2) on the scaled
+ * correction equation A e = r / ||r|| run entirely in FP32. */
+enum { EXCMG_PRECISION_FP64 = 0, EXCMG_PRECISION_MIXED = 1 };
+
 typedef struct {
     double tol;          /* relative residual tolerance eps of Alg. 1 (> 0)                  */
     int tol_mode;        /* EXCMG_TOL_PAPER or EXCMG_TOL_UNIFORM                              */
     int max_iter;        /* cap on the iterations of one Bi-CG call (WHILE body, Alg. 1 l.8)  */
     int max_total;       /* cap on the Bi-CG iterations of one level                          */
     int check_every;     /* iterations enqueued between two host checks of convergence (>= 1) */
+    int precision;       /* EXCMG_PRECISION_FP64 or EXCMG_PRECISION_MIXED                     */
+    double inner_tol;    /* MIXED: residual reduction asked of each FP32 correction solve     */
 } excmg_params;
 
 #define EXCMG_MAX_LEVELS 16
@@ -72,7 +81,7 @@ typedef struct {
     int levels;                          /* number of grids, coarsest first            */
     int n[EXCMG_MAX_LEVELS];             /* intervals per axis of each grid            */
     int iters[EXCMG_MAX_LEVELS];         /* Bi-CG iterations (0 on DSOLVE levels)      */
-    int calls[EXCMG_MAX_LEVELS];         /* Bi-CG calls of the WHILE loop              */
+    int calls[EXCMG_MAX_LEVELS];         /* Bi-CG calls of the WHILE loop (MIXED: refinement steps) */
     int stagnated[EXCMG_MAX_LEVELS];     /* 1 if the loop ended on the stagnation rule */
     double relres[EXCMG_MAX_LEVELS];     /* final true relative residual ||f-Au||/||f|| */
     double ms[EXCMG_MAX_LEVELS];         /* device time spent on the level (ms)        */

@@ -31,6 +31,7 @@ STATUS_NAMES = {0: "EXCMG_OK", -1: "EXCMG_ERR_ARG", -2: "EXCMG_ERR_OOM", -3: "EX
                 -7: "EXCMG_ERR_TIMEOUT", -9: "EXCMG_ERR_BUDGET"}
 TOL_MODES = {"paper": 0, "uniform": 1}
 STENCIL_VARIANTS = {"exact": 0, "fp64": 1}
+PRECISIONS = {"fp64": 0, "mixed": 1}
 MAX_LEVELS = 16
 
 
@@ -42,7 +43,8 @@ class ExcmgError(RuntimeError):
 
 class Params(ctypes.Structure):
     _fields_ = [("tol", ctypes.c_double), ("tol_mode", ctypes.c_int), ("max_iter", ctypes.c_int),
-                ("max_total", ctypes.c_int), ("check_every", ctypes.c_int)]
+                ("max_total", ctypes.c_int), ("check_every", ctypes.c_int), ("precision", ctypes.c_int),
+                ("inner_tol", ctypes.c_double)]
 
 
 class Stats(ctypes.Structure):
@@ -283,14 +285,16 @@ def excmg_solve(n_finest: int, n_coarsest: int, bc_kind: int, f: torch.Tensor, g
                 g2: torch.Tensor, tol: float, u_out: torch.Tensor | None = None, *,
                 ctx: Context | None = None, tol_mode: str = "uniform", max_iter: int = 100000,
                 max_total: int = 1000000, check_every: int = 16, u_h_out: torch.Tensor | None = None,
-                return_stats: bool = False):
+                return_stats: bool = False, precision: str = "fp64", inner_tol: float = 1e-4):
     """Alg. 1.  Returns u_tilde (EXP_true on the finest grid), and the
-    per-level statistics when return_stats is set."""
+    per-level statistics when return_stats is set.  precision="mixed" runs
+    the Bi-CG levels as FP32 correction solves inside FP64 refinement."""
     ctx = ctx or default_context(f.device)
     n = int(n_finest)
     if u_out is None:
         u_out = _new_node(n, f)
-    params = Params(float(tol), TOL_MODES[tol_mode], int(max_iter), int(max_total), int(check_every))
+    params = Params(float(tol), TOL_MODES[tol_mode], int(max_iter), int(max_total), int(check_every),
+                    PRECISIONS[precision], float(inner_tol))
     stats = Stats()
     ph = _vp(_node(u_h_out, n, "u_h_out")) if u_h_out is not None else _vp(0)
     rc = _lib.excmg_solve_ex(ctx.handle, n, int(n_coarsest), int(bc_kind), _vp(_node(f, n, "f")),

@@ -67,6 +67,9 @@ int bicg_run(excmg_ctx* ctx, int n, int bc_kind, const double* b, double* x, dou
     if (e != cudaSuccess) return ctx_cuda(ctx, e, "Bi-CG setup");
 
     const int* done = &ctx->state->done;
+    // the integer operator has a fused two-field kernel; the FP64 one runs
+    // as two applications and a separate inner product
+    const bool fused = ctx->stencil_variant == kStencilExact && stencil_cta_count(n) <= kMaxPartials;
     note_launches(2);   // residual stencil + init (the memsets are not kernels)
     int batch = 0;
     int iter_before = 0;
@@ -100,17 +103,26 @@ int bicg_run(excmg_ctx* ctx, int n, int bc_kind, const double* b, double* x, dou
         }
         for (int it = 0; it < batch && e == cudaSuccess; ++it) {
             if (ctx->profile) cudaEventRecord(ctx->prof_events[3 * it], s);
-            e = launch_stencil(p, q, nullptr, n, bc_kind, false, done, s, ctx->stencil_variant);  // A p_k
-            if (ctx->profile) cudaEventRecord(ctx->prof_events[3 * it + 1], s);
-            if (e == cudaSuccess)
-                e = launch_stencil(ps, qs, nullptr, n, bc_kind, true, done, s, ctx->stencil_variant);  // A^T p*_k
-            if (ctx->profile) cudaEventRecord(ctx->prof_events[3 * it + 2], s);
-            if (e == cudaSuccess) e = launch_bicg_sigma(ps, q, len, ctx->partials, ctx->state, s);
+            if (fused) {
+                // A p_k and A^T p*_k in one z-march, sigma_k and alpha_k fused
+                e = launch_bicg_stencil_pair(p, q, ps, qs, n, bc_kind, ctx->partials, ctx->state, s);
+                if (ctx->profile) {
+                    cudaEventRecord(ctx->prof_events[3 * it + 1], s);
+                    cudaEventRecord(ctx->prof_events[3 * it + 2], s);
+                }
+            } else {
+                e = launch_stencil(p, q, nullptr, n, bc_kind, false, done, s, ctx->stencil_variant);  // A p_k
+                if (ctx->profile) cudaEventRecord(ctx->prof_events[3 * it + 1], s);
+                if (e == cudaSuccess)
+                    e = launch_stencil(ps, qs, nullptr, n, bc_kind, true, done, s, ctx->stencil_variant);  // A^T p*_k
+                if (ctx->profile) cudaEventRecord(ctx->prof_events[3 * it + 2], s);
+                if (e == cudaSuccess) e = launch_bicg_sigma(ps, q, len, ctx->partials, ctx->state, s);
+            }
             if (e == cudaSuccess)
                 e = launch_bicg_update(x, p, r, q, rs, qs, len, ctx->partials, ctx->state, s);
             if (e == cudaSuccess) e = launch_bicg_pupdate(p, r, ps, rs, len, ctx->state, s);
         }
-        note_launches(5LL * batch);
+        note_launches((fused ? 3LL : 5LL) * batch);
         if (e != cudaSuccess) return ctx_cuda(ctx, e, "Bi-CG iteration");
     }
     const BicgState& h = *ctx->host_state;

@@ -276,6 +276,10 @@ int excmg_solve_ex(excmg_ctx* ctx, int n_finest, int n_coarsest, int bc_kind, co
         return ctx_fail(ctx, EXCMG_ERR_ARG, "n_finest must be n_coarsest * 2^(L+1) with L >= 1");
     if (!(params->tol > 0.0) || params->max_iter < 1 || params->max_total < 1)
         return ctx_fail(ctx, EXCMG_ERR_ARG, "excmg_solve: tol > 0, max_iter >= 1, max_total >= 1");
+    if (params->precision != EXCMG_PRECISION_FP64 && params->precision != EXCMG_PRECISION_MIXED)
+        return ctx_fail(ctx, EXCMG_ERR_ARG, "excmg_solve: unknown precision");
+    if (params->precision == EXCMG_PRECISION_MIXED && !(params->inner_tol > 0.0 && params->inner_tol < 1.0))
+        return ctx_fail(ctx, EXCMG_ERR_ARG, "excmg_solve: inner_tol must lie in (0, 1)");
     const int nl = steps + 1;   // levels 0 .. L+1
     if (nl > EXCMG_MAX_LEVELS) return ctx_fail(ctx, EXCMG_ERR_ARG, "too many levels");
     const int L = nl - 2;
@@ -323,6 +327,12 @@ int excmg_solve_ex(excmg_ctx* ctx, int n_finest, int n_coarsest, int bc_kind, co
             const int i = l - 1;   // Alg. 1 loop counter 1..L
             const double eps = params->tol_mode == EXCMG_TOL_PAPER ? params->tol * std::pow(10.0, (double)(i - L))
                                                                    : params->tol;
+            if (params->precision == EXCMG_PRECISION_MIXED) {
+                result = mixed_level_solve(ctx, N, bc_kind, fh, u, fnorm, eps, params->inner_tol, params->max_iter,
+                                           params->max_total, params->check_every, &iters, &calls, &stag, &rel);
+                if (result) break;
+                goto level_done;
+            }
             if ((result = true_residual_norm(ctx, N, bc_kind, fh, u, &rn))) break;
             rel = fnorm > 0.0 ? rn / fnorm : 0.0;
             // Alg. 1, lines 7-9
@@ -346,6 +356,7 @@ int excmg_solve_ex(excmg_ctx* ctx, int n_finest, int n_coarsest, int bc_kind, co
                 }
             }
         }
+    level_done:
         cudaEventRecord(ev1, s);
         cudaEventSynchronize(ev1);
         float ms = 0.f;
@@ -384,6 +395,8 @@ int excmg_solve(int n_finest, int n_coarsest, int bc_kind, const double* f, cons
     p.max_iter = 100000;
     p.max_total = 1000000;
     p.check_every = 16;
+    p.precision = EXCMG_PRECISION_FP64;
+    p.inner_tol = 1e-4;
     if (!u_out) return EXCMG_ERR_ARG;
     return excmg_solve_ex(nullptr, n_finest, n_coarsest, bc_kind, f, g1, g2, &p, nullptr, u_out, nullptr);
 }

@@ -23,7 +23,7 @@ inline size_t face_count(int n) { return 6 * (size_t)(n + 1) * (size_t)(n + 1); 
 // their reductions always combine the same partial sums in the same order.
 constexpr int kVecThreads = 256;
 constexpr int kVecBlocks = 152 * 4;     // 4 CTAs on each of GB300's 152 SMs
-constexpr int kMaxPartials = 2 * kVecBlocks;
+constexpr int kMaxPartials = 8192;   // >= 2 * kVecBlocks and >= stencil CTAs
 
 // Bi-CG state kept on the device so that a whole iteration runs without the
 // host (Alg. 2 with M = I).
@@ -53,6 +53,12 @@ enum { kStencilExact = 0, kStencilFp64 = 1 };
 cudaError_t launch_stencil(const double* u, double* y, const double* b, int n, int bc_kind,
                            bool transpose, const int* skip, cudaStream_t s, int variant);
 cudaError_t launch_zero_boundary(double* y, int n, cudaStream_t s);
+// One z-march applying A to p (-> q) and A^T to p* (-> qs) with the integer
+// arithmetic, fused with sigma = (p*, q) and alpha = rho / sigma (Alg. 2).
+// Skips when st->done.  partials must hold stencil_cta_count(n) doubles.
+cudaError_t launch_bicg_stencil_pair(const double* p, double* q, const double* ps, double* qs, int n,
+                                     int bc_kind, double* partials, BicgState* st, cudaStream_t s);
+int stencil_cta_count(int n);
 
 // Vectors (flat over all (n+1)^3 entries; boundary entries of the Bi-CG
 // vectors are zero, so flat sums equal sums over the unknowns).
@@ -142,4 +148,8 @@ int true_residual_norm(excmg_ctx* ctx, int n, int bc_kind, const double* b, cons
 int interior_norm(excmg_ctx* ctx, int n, const double* a, double* out);
 // DSOLVE (dsolve.cu)
 int dsolve_run(excmg_ctx* ctx, int n, int bc_kind, const double* fh, double* u);
+// FP32 inner solves + FP64 refinement on one level (mixed.cu).
+int mixed_level_solve(excmg_ctx* ctx, int n, int bc_kind, const double* fh, double* u, double fnorm, double eps,
+                      double inner_tol, int max_inner, int max_total, int check_every, int* iters_out,
+                      int* outer_out, int* stag_out, double* rel_out);
 }  // namespace excmg

@@ -22,6 +22,7 @@
 // diagonal, so this is the same arithmetic; the flag is kept so that A^T is
 // applied as Alg. 2 asks (its shadow recurrence multiplies by A^T).
 #include "excmg_internal.cuh"
+#include "reduce.cuh"
 
 namespace excmg {
 namespace {
@@ -138,101 +139,210 @@ __device__ __forceinline__ int exponent_of(double v) {
     return (int)(((unsigned)__double2hiint(v) >> 20) & 0x7FFu);
 }
 
-template <bool kTranspose>
-__global__ void __launch_bounds__(TX * TY)
-stencil_fx_kernel(const double* __restrict__ u, double* __restrict__ y, const double* __restrict__ b,
-                  int n, int sigma, int kz_per_cta, const int* __restrict__ skip) {
+// Register-blocked integer kernel.  A CTA of FX_TX x FX_TY threads owns
+// FX_TX x (FX_TY * FX_RY) output columns; each thread produces FX_RY = 2
+// vertically adjacent columns, which share 9 of their 18 shared-memory reads.
+// NF fields are marched together through the same z-planes (NF = 2 applies A
+// to p and A^T to p* in one pass for Bi-CG); field f has its own running
+// scale exponent E[f].  Each thread's halo-load slots are the same on every
+// plane, so their offsets are computed once.
+//
+// The transposed operator gathers over the mirrored tap set; every tap d of
+// eq. (method1) has a partner -d of equal weight and integer sums do not
+// depend on order, so A^T u and A u come out bit for bit equal here.
+//
+// With kDot the kernel also forms the Bi-CG scalar sigma = (p*, A p) of
+// Alg. 2 (field 1's input against field 0's output) and, in the last CTA,
+// alpha = rho / sigma.
+constexpr int FX_TX = 32;
+constexpr int FX_TY = 8;
+constexpr int FX_RY = 2;
+constexpr int FX_OY = FX_TY * FX_RY;                 // output rows per CTA
+constexpr int FX_HX = FX_TX + 4;
+constexpr int FX_HY = FX_OY + 4;
+constexpr int FX_NT = FX_TX * FX_TY;
+constexpr int FX_SLOTS = (FX_HX * FX_HY + FX_NT - 1) / FX_NT;
+
+struct FxFields {
+    const double* in[2];
+    double* out[2];
+};
+
+__device__ __forceinline__ double fx_result(long long acc, int E, bool poisoned) {
+    if (poisoned) return __longlong_as_double(0x7FF8000000000000ll);
+    if (E >= 53 && E <= 2037) return from_fixed(acc, E);
+    return ldexp((double)acc, E - 1075);
+}
+
+template <int NF, bool kDot>
+__global__ void __launch_bounds__(FX_NT)
+stencil_fx_kernel(FxFields fl, const double* __restrict__ b, int n, int sigma, int kz_per_cta,
+                  const int* __restrict__ skip, double* partials, BicgState* st) {
     if (skip != nullptr && *skip) return;
-    __shared__ long long tile[HY][HX];
-    __shared__ int wmax[TX * TY / 32];
-    constexpr int kPerThread = (HX * HY + TX * TY - 1) / (TX * TY);
+    __shared__ long long tile[NF][FX_HY * FX_HX];
+    __shared__ int wmax[NF][FX_NT / 32];
     const int np = n + 1;
-    const int tx = threadIdx.x, ty = threadIdx.y, tid = ty * TX + tx;
-    const int i0 = 1 + blockIdx.x * TX, j0 = 1 + blockIdx.y * TY;
+    const size_t plane = (size_t)np * np;
+    const int tx = threadIdx.x, ty = threadIdx.y, tid = ty * FX_TX + tx;
+    const int lane = tid & 31;
+    const int i0 = 1 + blockIdx.x * FX_TX, j0 = 1 + blockIdx.y * FX_OY;
     const int kz0 = 1 + blockIdx.z * kz_per_cta;
     const int kz1 = min(kz0 + kz_per_cta, n);
-    const int i = i0 + tx, j = j0 + ty;
-    const bool active = (i <= n - 1) && (j <= n - 1);
-    const int cxy = (i == 1) + (i == n - 1) + (j == 1) + (j == n - 1);
-    const int sg = kTranspose ? -1 : 1;
 
-    long long acc0 = 0, acc1 = 0, acc2 = 0, acc3 = 0, acc4 = 0;
-    int E = 1;            // running scale exponent (1: nothing non-zero met yet)
-    bool poisoned = false;
+    // halo-load slots of this thread: in-plane offset (-1: outside the
+    // interior, reads as zero) and shared-memory index (-1: no slot)
+    int soff[FX_SLOTS], sidx[FX_SLOTS];
+#pragma unroll
+    for (int r = 0; r < FX_SLOTS; ++r) {
+        const int e = tid + r * FX_NT;
+        soff[r] = -1;
+        sidx[r] = -1;
+        if (e < FX_HX * FX_HY) {
+            const int ly = e / FX_HX, lx = e - ly * FX_HX;
+            const int gi = i0 - 2 + lx, gj = j0 - 2 + ly;
+            sidx[r] = e;
+            if (gi >= 1 && gi <= n - 1 && gj >= 1 && gj <= n - 1) soff[r] = gj * np + gi;
+        }
+    }
+    const int i = i0 + tx, ja = j0 + ty * FX_RY;
+    const bool act0 = (i <= n - 1) && (ja <= n - 1);
+    const bool act1 = (i <= n - 1) && (ja + 1 <= n - 1);
+    const int cx = (i == 1) + (i == n - 1);
+    const int c0 = cx + (ja == 1) + (ja == n - 1);
+    const int c1 = cx + (ja + 1 == 1) + (ja + 1 == n - 1);
+    const int ry = ty * FX_RY + 2, rx = tx + 2;   // tile coordinates of the first output
+
+    long long acc[NF][FX_RY][5];
+    int E[NF];
+    bool poisoned[NF];
+#pragma unroll
+    for (int f = 0; f < NF; ++f) {
+#pragma unroll
+        for (int q = 0; q < FX_RY; ++q)
+#pragma unroll
+            for (int k = 0; k < 5; ++k) acc[f][q][k] = 0;
+        E[f] = 1;
+        poisoned[f] = false;
+    }
+    double dot = 0.0;
+
     for (int zin = kz0 - 2; zin <= kz1 + 1; ++zin) {
         const bool zok = (zin >= 1) && (zin <= n - 1);
-        double v[kPerThread];
-        int emax = 0;
+        const size_t zbase = zok ? (size_t)zin * plane : 0;
+        double v[NF][FX_SLOTS];
 #pragma unroll
-        for (int r = 0; r < kPerThread; ++r) {
-            const int e = tid + r * TX * TY;
-            v[r] = 0.0;
-            if (e < HX * HY) {
-                const int ly = e / HX, lx = e - ly * HX;
-                const int gi = i0 - 2 + lx, gj = j0 - 2 + ly;
-                if (zok && gi >= 1 && gi <= n - 1 && gj >= 1 && gj <= n - 1)
-                    v[r] = u[((size_t)zin * np + gj) * np + gi];
+        for (int f = 0; f < NF; ++f) {
+            int emax = 0;
+#pragma unroll
+            for (int r = 0; r < FX_SLOTS; ++r) {
+                v[f][r] = (zok && soff[r] >= 0) ? fl.in[f][zbase + soff[r]] : 0.0;
+                emax = max(emax, exponent_of(v[f][r]));
             }
-            emax = max(emax, exponent_of(v[r]));
+            emax = (int)__reduce_max_sync(0xffffffffu, (unsigned)emax);
+            if (lane == 0) wmax[f][tid >> 5] = emax;
         }
-        emax = (int)__reduce_max_sync(0xffffffffu, (unsigned)emax);
-        if ((tid & 31) == 0) wmax[tid >> 5] = emax;
-        __syncthreads();   // also: every thread is done reading the previous tile
-        int ep = wmax[0];
+        __syncthreads();   // also: every thread is done reading the previous tiles
 #pragma unroll
-        for (int w = 1; w < TX * TY / 32; ++w) ep = max(ep, wmax[w]);
-        if (ep == 0x7FF) poisoned = true;
-        if (ep > E) {
-            const int d = ep - E;
-            if (d >= 63) {
-                acc0 = acc1 = acc2 = acc3 = acc4 = 0;
-            } else {
-                acc0 >>= d; acc1 >>= d; acc2 >>= d; acc3 >>= d; acc4 >>= d;
-            }
-            E = ep;
-        }
+        for (int f = 0; f < NF; ++f) {
+            const int ep = (int)__reduce_max_sync(0xffffffffu, (unsigned)wmax[f][lane & (FX_NT / 32 - 1)]);
+            if (ep == 0x7FF) poisoned[f] = true;
+            if (ep > E[f]) {
+                const int d = ep - E[f];
 #pragma unroll
-        for (int r = 0; r < kPerThread; ++r) {
-            const int e = tid + r * TX * TY;
-            if (e < HX * HY) {
-                const int ly = e / HX, lx = e - ly * HX;
-                tile[ly][lx] = to_fixed(v[r], E);
+                for (int q = 0; q < FX_RY; ++q)
+#pragma unroll
+                    for (int k = 0; k < 5; ++k) acc[f][q][k] = d >= 63 ? 0 : (acc[f][q][k] >> d);
+                E[f] = ep;
             }
+#pragma unroll
+            for (int r = 0; r < FX_SLOTS; ++r)
+                if (sidx[r] >= 0) tile[f][sidx[r]] = to_fixed(v[f][r], E[f]);
         }
         __syncthreads();
-        const int cy = ty + 2, cx = tx + 2;
-        const long long a = tile[cy][cx];
-        const long long n4 = tile[cy][cx - sg] + tile[cy][cx + sg] + tile[cy - sg][cx] + tile[cy + sg][cx];
-        const long long f4 = tile[cy][cx - 2 * sg] + tile[cy][cx + 2 * sg] + tile[cy - 2 * sg][cx] +
-                             tile[cy + 2 * sg][cx];
-        const long long d4 = tile[cy - sg][cx - sg] + tile[cy - sg][cx + sg] + tile[cy + sg][cx - sg] +
-                             tile[cy + sg][cx + sg];
         const int cz = (zin == 1) + (zin == n - 1);
-        const long long centre = 42 + sigma * (cxy + cz);
-        const long long p0 = centre * a - 12 * n4 + f4 + 2 * d4;
-        const long long p1 = 2 * n4 - 12 * a;
-        acc0 += a;
-        acc1 += p1;
-        acc2 += p0;
-        acc3 += p1;
-        acc4 += a;
         const int zo = zin - 2;
-        if (active && zo >= kz0 && zo < kz1) {
-            const size_t o = ((size_t)zo * np + j) * np + i;
-            double val;
-            if (poisoned)
-                val = __longlong_as_double(0x7FF8000000000000ll);
-            else if (E >= 53 && E <= 2037)
-                val = from_fixed(acc0, E);
-            else
-                val = ldexp((double)acc0, E - 1075);
-            y[o] = b ? (b[o] - val) : val;
+        const bool zstore = zo >= kz0 && zo < kz1;
+        const size_t o0 = ((size_t)zo * np + ja) * np + i;
+#pragma unroll
+        for (int f = 0; f < NF; ++f) {
+            const long long* T = tile[f];
+            auto at = [&](int yy, int xx) { return T[yy * FX_HX + xx]; };
+            // column x: rows ry-2 .. ry+3; columns x-1, x+1: rows ry-1 .. ry+2;
+            // columns x-2, x+2: rows ry, ry+1
+            const long long cm2 = at(ry - 2, rx), cm1 = at(ry - 1, rx), c_0 = at(ry, rx),
+                            c_1 = at(ry + 1, rx), c_2 = at(ry + 2, rx), c_3 = at(ry + 3, rx);
+            const long long lm1 = at(ry - 1, rx - 1), l_0 = at(ry, rx - 1), l_1 = at(ry + 1, rx - 1),
+                            l_2 = at(ry + 2, rx - 1);
+            const long long rm1 = at(ry - 1, rx + 1), r_0 = at(ry, rx + 1), r_1 = at(ry + 1, rx + 1),
+                            r_2 = at(ry + 2, rx + 1);
+            const long long ll0 = at(ry, rx - 2), ll1 = at(ry + 1, rx - 2), rr0 = at(ry, rx + 2),
+                            rr1 = at(ry + 1, rx + 2);
+            {   // output row ja
+                const long long n4 = l_0 + r_0 + cm1 + c_1;
+                const long long f4 = ll0 + rr0 + cm2 + c_2;
+                const long long d4 = lm1 + l_1 + rm1 + r_1;
+                const long long p0 = (long long)(42 + sigma * (c0 + cz)) * c_0 - 12 * n4 + f4 + 2 * d4;
+                const long long p1 = 2 * n4 - 12 * c_0;
+                acc[f][0][0] += c_0;
+                acc[f][0][1] += p1;
+                acc[f][0][2] += p0;
+                acc[f][0][3] += p1;
+                acc[f][0][4] += c_0;
+            }
+            {   // output row ja + 1
+                const long long n4 = l_1 + r_1 + c_0 + c_2;
+                const long long f4 = ll1 + rr1 + cm1 + c_3;
+                const long long d4 = l_0 + l_2 + r_0 + r_2;
+                const long long p0 = (long long)(42 + sigma * (c1 + cz)) * c_1 - 12 * n4 + f4 + 2 * d4;
+                const long long p1 = 2 * n4 - 12 * c_1;
+                acc[f][1][0] += c_1;
+                acc[f][1][1] += p1;
+                acc[f][1][2] += p0;
+                acc[f][1][3] += p1;
+                acc[f][1][4] += c_1;
+            }
+            if (zstore) {
+                if (act0) {
+                    double val = fx_result(acc[f][0][0], E[f], poisoned[f]);
+                    if (NF == 1 && b != nullptr) val = b[o0] - val;
+                    fl.out[f][o0] = val;
+                    if (kDot && f == 0) dot += __ldg(&fl.in[1][o0]) * val;
+                }
+                if (act1) {
+                    double val = fx_result(acc[f][1][0], E[f], poisoned[f]);
+                    if (NF == 1 && b != nullptr) val = b[o0 + np] - val;
+                    fl.out[f][o0 + np] = val;
+                    if (kDot && f == 0) dot += __ldg(&fl.in[1][o0 + np]) * val;
+                }
+            }
+#pragma unroll
+            for (int q = 0; q < FX_RY; ++q) {
+                acc[f][q][0] = acc[f][q][1];
+                acc[f][q][1] = acc[f][q][2];
+                acc[f][q][2] = acc[f][q][3];
+                acc[f][q][3] = acc[f][q][4];
+                acc[f][q][4] = 0;
+            }
         }
-        acc0 = acc1;
-        acc1 = acc2;
-        acc2 = acc3;
-        acc3 = acc4;
-        acc4 = 0;
+    }
+    if (kDot) {
+        __shared__ double sh[32];
+        __shared__ bool am_last;
+        double sdot = block_sum(dot, sh);
+        if (publish_partials(&sdot, 1, partials, &st->ticket, &am_last)) {
+            const double sg = gather_partials(partials, 0, sh);
+            if (thread0()) {
+                const double rho = st->rho;
+                st->sigma = sg;
+                if (!(rho != 0.0 && isfinite(rho)) || !(sg != 0.0 && isfinite(sg))) {
+                    st->status = kBreakdown;
+                    st->done = 1;
+                } else {
+                    st->alpha = rho / sg;
+                }
+                st->ticket = 0;
+            }
+        }
     }
 }
 
@@ -256,34 +366,106 @@ __global__ void zero_boundary_kernel(double* __restrict__ y, int n) {
 
 }  // namespace
 
+namespace {
+
+struct StencilGrid {
+    dim3 grid, block;
+    int kz_per_cta;
+};
+
+// Column tiles x z-slabs.  The slab count is chosen so that the CTAs fill
+// whole waves of the GPU's resident slots (152 SMs x CTAs per SM) while each
+// slab stays long enough that its 4 extra halo planes cost little.
+StencilGrid stencil_grid(int n, int tx, int rows, int per_sm) {
+    const int m = n - 1;  // interior extent
+    StencilGrid g;
+    const int gx = (m + tx - 1) / tx, gy = (m + rows - 1) / rows;
+    const int tiles = gx * gy;
+    const int slots = 152 * (per_sm > 0 ? per_sm : 1);
+    int best = 1;
+    double best_eff = -1.0;
+    for (int slabs = 1; slabs <= 64; ++slabs) {
+        const int planes = (m + slabs - 1) / slabs;
+        if (slabs > 1 && planes < 8) break;
+        const long long ctas = (long long)tiles * slabs;
+        const long long waves = (ctas + slots - 1) / slots;
+        const double eff = (double)ctas / (double)(waves * slots) * planes / (planes + 4.0);
+        if (eff > best_eff + 1e-9) {
+            best_eff = eff;
+            best = slabs;
+        }
+    }
+    g.kz_per_cta = (m + best - 1) / best;
+    const int slabs = (m + g.kz_per_cta - 1) / g.kz_per_cta;
+    g.grid = dim3(gx, gy, slabs);
+    return g;
+}
+
+template <typename K>
+int resident_per_sm(K kernel, int threads) {
+    int v = 0;
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&v, kernel, threads, 0) != cudaSuccess) {
+        cudaGetLastError();
+        v = 1;
+    }
+    return v > 0 ? v : 1;
+}
+
+StencilGrid fx_grid(int n, int nf) {
+    static int occ1 = 0, occ2 = 0;
+    if (nf == 1) {
+        if (!occ1) occ1 = resident_per_sm(stencil_fx_kernel<1, false>, FX_NT);
+        StencilGrid g = stencil_grid(n, FX_TX, FX_OY, occ1);
+        g.block = dim3(FX_TX, FX_TY, 1);
+        return g;
+    }
+    if (!occ2) occ2 = resident_per_sm(stencil_fx_kernel<2, true>, FX_NT);
+    StencilGrid g = stencil_grid(n, FX_TX, FX_OY, occ2);
+    g.block = dim3(FX_TX, FX_TY, 1);
+    return g;
+}
+
+StencilGrid f64_grid(int n) {
+    static int occ = 0;
+    if (!occ) occ = resident_per_sm(stencil_f64_kernel<false>, TX * TY);
+    StencilGrid g = stencil_grid(n, TX, TY, occ);
+    g.block = dim3(TX, TY, 1);
+    return g;
+}
+
+}  // namespace
+
+int stencil_cta_count(int n) {
+    const StencilGrid g = fx_grid(n, 2);
+    return (int)(g.grid.x * g.grid.y * g.grid.z);
+}
+
 cudaError_t launch_stencil(const double* u, double* y, const double* b, int n, int bc_kind,
                            bool transpose, const int* skip, cudaStream_t s, int variant) {
-    const int m = n - 1;  // interior extent
-    dim3 block(TX, TY, 1);
-    const int gx = (m + TX - 1) / TX, gy = (m + TY - 1) / TY;
-    const int tiles = gx * gy;
-    // enough CTAs to fill the GPU: split z into slabs when there are few columns
-    const int target = 152 * 6;
-    int slabs = (target + tiles - 1) / tiles;
-    const int max_slabs = (m + 3) / 4;
-    if (slabs > max_slabs) slabs = max_slabs;
-    if (slabs < 1) slabs = 1;
-    const int kz_per_cta = (m + slabs - 1) / slabs;
-    slabs = (m + kz_per_cta - 1) / kz_per_cta;
-    dim3 grid(gx, gy, slabs);
     if (variant == kStencilFp64) {
+        const StencilGrid g = f64_grid(n);
         const double sigma = bc_kind == 1 ? 1.0 : -1.0;
         if (transpose)
-            stencil_f64_kernel<true><<<grid, block, 0, s>>>(u, y, b, n, sigma, kz_per_cta, skip);
+            stencil_f64_kernel<true><<<g.grid, g.block, 0, s>>>(u, y, b, n, sigma, g.kz_per_cta, skip);
         else
-            stencil_f64_kernel<false><<<grid, block, 0, s>>>(u, y, b, n, sigma, kz_per_cta, skip);
+            stencil_f64_kernel<false><<<g.grid, g.block, 0, s>>>(u, y, b, n, sigma, g.kz_per_cta, skip);
     } else {
-        const int sigma = bc_kind == 1 ? 1 : -1;
-        if (transpose)
-            stencil_fx_kernel<true><<<grid, block, 0, s>>>(u, y, b, n, sigma, kz_per_cta, skip);
-        else
-            stencil_fx_kernel<false><<<grid, block, 0, s>>>(u, y, b, n, sigma, kz_per_cta, skip);
+        // A^T u == A u bit for bit in integer arithmetic (see above)
+        (void)transpose;
+        const StencilGrid g = fx_grid(n, 1);
+        FxFields fl{{u, nullptr}, {y, nullptr}};
+        stencil_fx_kernel<1, false><<<g.grid, g.block, 0, s>>>(fl, b, n, bc_kind == 1 ? 1 : -1, g.kz_per_cta,
+                                                               skip, nullptr, nullptr);
     }
+    return cudaGetLastError();
+}
+
+cudaError_t launch_bicg_stencil_pair(const double* p, double* q, const double* ps, double* qs, int n,
+                                     int bc_kind, double* partials, BicgState* st, cudaStream_t s) {
+    const StencilGrid g = fx_grid(n, 2);
+    FxFields fl{{p, ps}, {q, qs}};
+    stencil_fx_kernel<2, true><<<g.grid, g.block, 0, s>>>(fl, nullptr, n, bc_kind == 1 ? 1 : -1, g.kz_per_cta,
+                                                          &st->done, partials, st);
     return cudaGetLastError();
 }
 

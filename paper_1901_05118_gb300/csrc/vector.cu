@@ -8,51 +8,10 @@
 // per-CTA partials in CTA order.  The same inputs therefore always give the
 // same bits, independent of scheduling.
 #include "excmg_internal.cuh"
+#include "reduce.cuh"
 
 namespace excmg {
 namespace {
-
-__device__ __forceinline__ double warp_sum(double v) {
-    for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
-    return v;
-}
-
-// Sum of v over the CTA (valid in thread 0).
-__device__ __forceinline__ double block_sum(double v, double* sh) {
-    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
-    v = warp_sum(v);
-    if (lane == 0) sh[wid] = v;
-    __syncthreads();
-    double t = 0.0;
-    if (wid == 0) {
-        t = lane < (int)(blockDim.x >> 5) ? sh[lane] : 0.0;
-        t = warp_sum(t);
-    }
-    __syncthreads();
-    return t;
-}
-
-// Publish this CTA's partial sums (count values) and report whether this
-// CTA is the last one to do so.
-__device__ __forceinline__ bool publish_partials(const double* vals, int count, double* partials,
-                                                 unsigned int* ticket, bool* am_last) {
-    if (threadIdx.x == 0) {
-        for (int c = 0; c < count; ++c) partials[c * gridDim.x + blockIdx.x] = vals[c];
-        __threadfence();
-        const unsigned int t = atomicAdd(ticket, 1u);
-        *am_last = (t == gridDim.x - 1);
-    }
-    __syncthreads();
-    return *am_last;
-}
-
-// In the last CTA: the total of component c over all CTAs, in CTA order.
-__device__ __forceinline__ double gather_partials(const double* partials, int c, double* sh) {
-    double v = 0.0;
-    for (int b = threadIdx.x; b < (int)gridDim.x; b += blockDim.x)
-        v += __ldcg(&partials[c * gridDim.x + b]);
-    return block_sum(v, sh);
-}
 
 __global__ void __launch_bounds__(kVecThreads)
 dot_kernel(const double* __restrict__ a, const double* __restrict__ b, size_t len,
@@ -66,7 +25,7 @@ dot_kernel(const double* __restrict__ a, const double* __restrict__ b, size_t le
     double s = block_sum(v, sh);
     if (publish_partials(&s, 1, partials, ticket, &am_last)) {
         const double tot = gather_partials(partials, 0, sh);
-        if (threadIdx.x == 0) {
+        if (thread0()) {
             *out = tot;
             *ticket = 0;
         }
@@ -91,7 +50,7 @@ bicg_init_kernel(const double* __restrict__ r, double* __restrict__ rs, double* 
     double s = block_sum(v, sh);
     if (publish_partials(&s, 1, partials, &st->ticket, &am_last)) {
         const double tot = gather_partials(partials, 0, sh);
-        if (threadIdx.x == 0) {
+        if (thread0()) {
             st->rho = tot;   // (r*_0, r_0) with r*_0 = r_0
             st->rr = tot;
             st->iter = 0;
@@ -118,7 +77,7 @@ bicg_sigma_kernel(const double* __restrict__ ps, const double* __restrict__ q, s
     double s = block_sum(v, sh);
     if (publish_partials(&s, 1, partials, &st->ticket, &am_last)) {
         const double sigma = gather_partials(partials, 0, sh);
-        if (threadIdx.x == 0) {
+        if (thread0()) {
             const double rho = st->rho;
             st->sigma = sigma;
             if (!(rho != 0.0 && isfinite(rho)) || !(sigma != 0.0 && isfinite(sigma))) {
@@ -159,7 +118,7 @@ bicg_update_kernel(double* __restrict__ x, const double* __restrict__ p, double*
     if (publish_partials(s, 2, partials, &st->ticket, &am_last)) {
         const double rho_new = gather_partials(partials, 0, sh);
         const double rr = gather_partials(partials, 1, sh);
-        if (threadIdx.x == 0) {
+        if (thread0()) {
             st->beta = rho_new / st->rho;
             st->rho = rho_new;
             st->rr = rr;

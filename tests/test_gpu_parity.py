@@ -169,18 +169,33 @@ def test_dsolve(n, bc_kind):
 
 
 # ------------------------------------------------------------- Bi-CG
-@pytest.mark.parametrize("n,bc_kind", [(12, 1), (17, 2)])
-def test_bicg(n, bc_kind):
+@pytest.mark.parametrize("variant", VARIANTS)
+@pytest.mark.parametrize("n,bc_kind", [(12, 1), (17, 2), (40, 1)])
+def test_bicg(n, bc_kind, variant):
     b = P.random_field(n, 31)
     x0 = P.random_field(n, 32) * 0.1
-    lvl = B.Level(n, bc_kind)
+    lvl = level(n, bc_kind, variant)
     x = dev(x0)
     it, rel, rc = B.bicg_solve(lvl, dev(b), x, 1e-12, 5000)
     xr, itr, relr, rcr = oracle.bicg(n, bc_kind, b, x0, 1e-12)
     assert rc == 0 and rcr == 0
-    assert abs(it - itr) <= 2
+    # iteration counts are not pinned (rounding shifts them over hundreds of steps)
+    assert abs(it - itr) <= max(3, 0.05 * itr)
     assert rel <= 1e-12
     assert rel_max(host(x), xr) <= 1e-9
+
+
+def test_bicg_is_deterministic():
+    """The reductions add their partial sums in a fixed order, so two runs
+    on the same input give the same iterate bit for bit."""
+    n = 24
+    b = dev(P.random_field(n, 41))
+    x1 = torch.zeros((n + 1,) * 3, dtype=torch.float64, device=DEV)
+    x2 = torch.zeros_like(x1)
+    lvl = level(n, 1)
+    r1 = B.bicg_solve(lvl, b, x1, 1e-11, 2000)
+    r2 = B.bicg_solve(lvl, b, x2, 1e-11, 2000)
+    assert r1 == r2 and torch.equal(x1, x2)
 
 
 # ---------------------------------------------------------- full solve
@@ -254,3 +269,33 @@ def test_bad_arguments_raise():
         B.excmg_solve(16, 8, 1, f, f, g2, 1e-8)   # L = 0
     with pytest.raises(B.ExcmgError):
         B.excmg_solve(16, 4, 3, f, f, g2, 1e-8)   # bc_kind
+
+
+# ------------------------------------------- FP32 inner + FP64 refinement
+@pytest.mark.parametrize("bc_kind", [1, 2])
+def test_mixed_precision_solve(bc_kind):
+    """FP32 correction solves inside FP64 refinement reach the same FP64
+    residual tolerance on every level, and the result's distance from the
+    oracle's FP64 solution is negligible next to the discretisation error."""
+    n, nc = 32, 4
+    prob = P.sin2pi_plus_poly()
+    f, g1, g2 = prob.data(n, bc_kind)
+    uh = torch.empty((n + 1,) * 3, dtype=torch.float64, device=DEV)
+    ut, stats = B.excmg_solve(n, nc, bc_kind, dev(f), dev(g1), dev(g2), 1e-10, u_h_out=uh,
+                              return_stats=True, precision="mixed", inner_tol=1e-4)
+    ref_h, ref_t, _ = oracle.excmg(n, nc, bc_kind, f, g1, g2, 1e-10)
+    ue = prob.exact(n)
+    disc = np.abs(ref_h - ue).max()
+    assert np.abs(host(uh) - ref_h).max() <= 1e-3 * disc
+    assert np.abs(host(ut) - ref_t).max() <= 1e-3 * disc
+    for s in stats[2:]:
+        assert s["relres"] <= 1e-10 or s["stagnated"]
+        assert s["calls"] >= 1
+
+
+def test_mixed_precision_exact_polynomial():
+    prob = P.polynomial([0.5, -0.3, 0.8], [1.0, 0.2, -0.6], [0.1, 0.7, 0.3])
+    n = 32
+    f, g1, g2 = prob.data(n, 1)
+    ut = B.excmg_solve(n, 4, 1, dev(f), dev(g1), dev(g2), 1e-12, precision="mixed")
+    assert np.abs(host(ut) - prob.exact(n)).max() <= 1e-11
