@@ -53,6 +53,8 @@ def parse():
     ap.add_argument("--stencil", choices=["exact", "fp64"], default="exact")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-mixed", action="store_true", help="skip the FP32-inner / FP64-refinement leg")
+    ap.add_argument("--mixed-steps", type=int, default=2)
     return ap.parse_args()
 
 
@@ -302,6 +304,10 @@ def run_ours(args):
                 "frac": (achieved / hbm_peak) if achieved else None, "traffic": None,
                 "launches": st_cnt, "avg_ms": avg_ms, "peak_source": "MEASURED_PEAKS.json hbm_gbs (of measured)"}
 
+    mixed = None
+    if not args.no_mixed:
+        mixed = precision_leg(args, B, problems, ctx, dev, stream, barrier, world)
+
     wu = {bc: sum(s["iters"] * (s["n"] / n) ** 3 for s in stats[bc] if s["iters"]) for bc in bcs}
     line = {"metric": METRIC, "value": value, "unit": "s", "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": ms_step, "higher_is_better": False, "scaling": "weak",
@@ -309,7 +315,7 @@ def run_ours(args):
             "e2e": e2e, "gpu_launches": launches, "roofline": roofline, "clocks": clk.summary(),
             "levels": {str(bc): [{"n": s["n"], "iters": s["iters"], "ms": round(s["ms"], 3),
                                   "relres": s["relres"]} for s in stats[bc]] for bc in bcs},
-            "work_units": {str(bc): round(w, 2) for bc, w in wu.items()}}
+            "work_units": {str(bc): round(w, 2) for bc, w in wu.items()}, "precision_leg": mixed}
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         cpu_value, info = oracle_sample(n, nc, bcs, wu)
         info["value"] = cpu_value
@@ -319,6 +325,52 @@ def run_ours(args):
         print(json.dumps(line), flush=True)
     if world > 1:
         dist.destroy_process_group()
+
+
+def precision_leg(args, B, problems, ctx, dev, stream, barrier, world):
+    """FP64 versus FP32-inner / FP64-refinement on the same 512^3 problem:
+    u = sin(2 pi x) sin(2 pi y) sin(2 pi z) + x^2 y^2 z^2, both kinds of data,
+    refinement to the same FP64 relative residual tol on every level.
+    Reports seconds per solve of each, the max error of each against the
+    exact solution (the discretisation error) and their distance from each
+    other."""
+    import torch
+
+    n, nc = args.n, args.nc
+    prob = problems.sin2pi_plus_poly()
+    f = torch.from_numpy(prob.rhs(n)).to(dev)
+    ue = torch.from_numpy(prob.exact(n)).to(dev)
+    out = {"workload": (f"{n}^3, coarsest {nc}^3, u = sin(2 pi x)sin(2 pi y)sin(2 pi z) + x^2y^2z^2, "
+                        f"first- and second-kind data, FP64 residual tol {args.tol:g} per level"),
+           "inner_tol": 1e-4}
+    res = {}
+    for prec in ("fp64", "mixed"):
+        times, errs, outs = [], [], {}
+        for bc in (1, 2):
+            g2 = torch.from_numpy(prob.boundary_g2(n, bc)).to(dev)
+            u = torch.empty_like(f)
+            run = lambda: B.excmg_solve(n, nc, bc, f, ue, g2, args.tol, u, ctx=ctx, precision=prec,
+                                        inner_tol=1e-4, return_stats=True)
+            _, st = run()   # warm-up
+            barrier()
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            for _ in range(args.mixed_steps):
+                _, st = run()
+            e1.record(stream)
+            barrier()
+            times.append(e0.elapsed_time(e1) / args.mixed_steps / 1e3)
+            errs.append(float((u - ue).abs().max()))
+            outs[bc] = u.clone()
+            res.setdefault("levels_" + prec, {})[str(bc)] = [(s["n"], s["iters"], s["calls"]) for s in st]
+        res[prec] = (sum(times) / len(times), errs, outs)
+    t64, e64, o64 = res["fp64"]
+    tmx, emx, omx = res["mixed"]
+    out.update({"fp64_s": max_over_ranks(t64, world, dev), "mixed_s": max_over_ranks(tmx, world, dev),
+                "speedup": t64 / tmx, "err_vs_exact_linf_fp64": e64, "err_vs_exact_linf_mixed": emx,
+                "mixed_minus_fp64_linf": [float((omx[bc] - o64[bc]).abs().max()) for bc in (1, 2)],
+                "levels_fp64": res["levels_fp64"], "levels_mixed": res["levels_mixed"]})
+    return out
 
 
 def main():

@@ -3,6 +3,7 @@
     python -m paper_1901_05118_gb300.cases stencil --n 256 --variant exact --reps 3
     python -m paper_1901_05118_gb300.cases bicg --n 256 --iters 4
     python -m paper_1901_05118_gb300.cases solve --n 64 --nc 8
+    python -m paper_1901_05118_gb300.cases issue-rates
 
 Each case allocates a few hundred MB at most (inputs still larger than L2 at
 n = 256) and runs a handful of launches, so a profiler capture ends quickly.
@@ -10,16 +11,24 @@ n = 256) and runs a handful of launches, so a profiler capture ends quickly.
 from __future__ import annotations
 
 import argparse
+import os
+import subprocess
+import sys
 
-import torch
 
-from . import binding as B
-from . import problems
+def issue_rates():
+    """Compile and run issue_rates.cu (FP64 / FP32 / integer issue rates)."""
+    here = os.path.dirname(os.path.abspath(__file__))
+    exe = os.path.join(here, "_build", "issue_rates")
+    os.makedirs(os.path.dirname(exe), exist_ok=True)
+    subprocess.check_call(["nvcc", "-gencode", "arch=compute_103a,code=sm_103a", "-O3", "-o", exe,
+                           os.path.join(here, "issue_rates.cu")])
+    sys.exit(subprocess.call([exe]))
 
 
 def main(argv=None):
     ap = argparse.ArgumentParser()
-    ap.add_argument("case", choices=["stencil", "bicg", "solve"])
+    ap.add_argument("case", choices=["stencil", "bicg", "solve", "issue-rates"])
     ap.add_argument("--n", type=int, default=256)
     ap.add_argument("--nc", type=int, default=8)
     ap.add_argument("--bc", type=int, default=1)
@@ -27,6 +36,13 @@ def main(argv=None):
     ap.add_argument("--reps", type=int, default=3)
     ap.add_argument("--iters", type=int, default=4)
     a = ap.parse_args(argv)
+    if a.case == "issue-rates":
+        issue_rates()
+    import torch
+
+    from . import binding as B
+    from . import problems
+
     dev = torch.device("cuda", 0)
     torch.cuda.set_device(dev)
     ctx = B.Context(dev)

@@ -388,6 +388,7 @@ StencilGrid stencil_grid(int n, int tx, int rows, int per_sm) {
         const int planes = (m + slabs - 1) / slabs;
         if (slabs > 1 && planes < 8) break;
         const long long ctas = (long long)tiles * slabs;
+        if (slabs > 1 && ctas > 4096) break;   // keeps the fused reductions' partials small
         const long long waves = (ctas + slots - 1) / slots;
         const double eff = (double)ctas / (double)(waves * slots) * planes / (planes + 4.0);
         if (eff > best_eff + 1e-9) {
