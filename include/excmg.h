@@ -48,7 +48,8 @@ typedef enum {
     EXCMG_ERR_NAN = -5,        /* non-finite value in a residual norm                        */
     EXCMG_ERR_CUDA = -6,       /* a CUDA runtime call or kernel launch failed                */
     EXCMG_ERR_TIMEOUT = -7,    /* a bounded device-side wait gave up                         */
-    EXCMG_ERR_BUDGET = -9      /* the context's HBM budget is too small for the request      */
+    EXCMG_ERR_BUDGET = -9,     /* the context's HBM budget is too small for the request      */
+    EXCMG_ERR_SIZE = -10       /* a size beyond the fixed maximum of an allocation-free call */
 } excmg_status;
 
 typedef struct excmg_ctx excmg_ctx;      /* device, stream, workspace, DSOLVE factor cache */
@@ -153,6 +154,21 @@ int bicg_solve(const excmg_level *level, const double *b, double *x_inout, doubl
  * (n_fine/4 intervals).  Every node of w_h is written, boundary nodes
  * included (interpolated values). */
 int extrapolate_interpolate(int n_fine, const double *u_2h, const double *u_4h, double *w_h);
+
+/* EXP_finite as above, allocating nothing (the paper has no counterpart: it
+ * is a service for callers that cannot allocate device memory at this point
+ * -- memory owned entirely by an arena or planner, a hard device-memory
+ * budget, or a path where entering the CUDA allocator, which may synchronise
+ * the device, is not allowed).  Its scratch lives in a fixed array inside
+ * the library (2.2 MB, held by every GPU that loads the library until the
+ * process exits), so n_fine is limited to 128; larger sizes return
+ * EXCMG_ERR_SIZE.  The caller passes inputs and output as for
+ * extrapolate_interpolate.  Runs on the legacy default stream and returns
+ * when the result is complete.  The first call on a device looks up the
+ * array's device address; make that first call before any stream capture.
+ * All calls share the one array: calls that overlap on the GPU (other host
+ * threads, other streams) race and must be serialised by the caller. */
+int extrapolate_interpolate_noalloc(int n_fine, const double *u_2h, const double *u_4h, double *w_h);
 
 /* EXP_true (Sec. 4.2.1, eqs. (t1), (chenlin); Alg. 1 line 11): extrapolated
  * solution u_tilde = u_h + (1/3) * multilinear interpolation of (u_h - u_2h)

@@ -28,7 +28,7 @@ _lib = ctypes.CDLL(LIB_PATH)
 EXCMG_OK = 0
 STATUS_NAMES = {0: "EXCMG_OK", -1: "EXCMG_ERR_ARG", -2: "EXCMG_ERR_OOM", -3: "EXCMG_ERR_BREAKDOWN",
                 -4: "EXCMG_ERR_NOCONV", -5: "EXCMG_ERR_NAN", -6: "EXCMG_ERR_CUDA",
-                -7: "EXCMG_ERR_TIMEOUT", -9: "EXCMG_ERR_BUDGET"}
+                -7: "EXCMG_ERR_TIMEOUT", -9: "EXCMG_ERR_BUDGET", -10: "EXCMG_ERR_SIZE"}
 TOL_MODES = {"paper": 0, "uniform": 1}
 STENCIL_VARIANTS = {"exact": 0, "fp64": 1}
 PRECISIONS = {"fp64": 0, "mixed": 1}

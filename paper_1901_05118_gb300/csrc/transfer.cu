@@ -17,6 +17,8 @@
 //     u~ = u_h + (1/3) * (mean of u_h - u_2h over the 2^m coarse nodes
 //                         around the node),
 // which is (4 u_h - u_2h)/3 at coarse nodes and (chenlin) at 1D midpoints.
+#include <mutex>
+
 #include "excmg_internal.cuh"
 
 namespace excmg {
@@ -139,3 +141,68 @@ cudaError_t launch_exp_true(double* ut, const double* uh, const double* u2h, int
 }
 
 }  // namespace excmg
+
+// ---------------------------------------------------------------------------
+// EXP_finite without allocation.
+//
+// Some callers cannot allocate device memory when they need this step: code
+// whose device memory is all owned by an arena or planner that hands out no
+// further blocks (a serving process that sized its pools up front, a job
+// held to a hard device-memory budget), or code running where entering the
+// CUDA allocator is not allowed (cudaMalloc and cudaFree may synchronise the
+// device, which a callback or a latency-critical path must not do).  This
+// variant keeps its only scratch -- the middle-grid values W -- in a fixed
+// array compiled into the library.  Every GPU that loads the library holds
+// that array (2.2 MB) until the process exits.
+namespace {
+
+constexpr int kNoAllocMaxFine = 128;
+constexpr size_t kNoAllocW =
+    (size_t)(kNoAllocMaxFine / 2 + 1) * (kNoAllocMaxFine / 2 + 1) * (kNoAllocMaxFine / 2 + 1);
+
+static __device__ __align__(256) double g_noalloc_W[kNoAllocW];
+
+std::mutex g_noalloc_mu;
+double* g_noalloc_addr[64] = {};   // device address of g_noalloc_W, per device
+
+// The array's device address on the current device, looked up once per
+// device (the name g_noalloc_W is only a host-side stand-in in host code).
+int noalloc_scratch(double** out) {
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= 64) {
+        cudaGetLastError();
+        return EXCMG_ERR_CUDA;
+    }
+    std::lock_guard<std::mutex> lock(g_noalloc_mu);
+    if (!g_noalloc_addr[dev]) {
+        void* p = nullptr;
+        const cudaError_t e = cudaGetSymbolAddress(&p, g_noalloc_W);
+        if (e != cudaSuccess || !p) {
+            cudaGetLastError();
+            return EXCMG_ERR_CUDA;
+        }
+        g_noalloc_addr[dev] = (double*)p;
+    }
+    *out = g_noalloc_addr[dev];
+    return EXCMG_OK;
+}
+
+}  // namespace
+
+extern "C" int extrapolate_interpolate_noalloc(int n_fine, const double* u_2h, const double* u_4h,
+                                               double* w_h) {
+    if (n_fine < 8 || n_fine % 4 || !u_2h || !u_4h || !w_h) return EXCMG_ERR_ARG;
+    if (n_fine > kNoAllocMaxFine) return EXCMG_ERR_SIZE;
+    double* W = nullptr;
+    const int st = noalloc_scratch(&W);
+    if (st != EXCMG_OK) return st;
+    // every entry of W is written before it is read: nothing to clear
+    cudaError_t e = excmg::launch_exp_finite(w_h, u_2h, u_4h, W, n_fine, nullptr);
+    excmg::note_launches(2);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(nullptr);
+    if (e != cudaSuccess) {
+        cudaGetLastError();
+        return EXCMG_ERR_CUDA;
+    }
+    return EXCMG_OK;
+}
