@@ -55,6 +55,10 @@ def parse():
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-mixed", action="store_true", help="skip the FP32-inner / FP64-refinement leg")
     ap.add_argument("--mixed-steps", type=int, default=2)
+    ap.add_argument("--no-batch", action="store_true", help="skip the 64-instance batched leg")
+    ap.add_argument("--no-serve", action="store_true", help="skip the request-stream leg")
+    ap.add_argument("--serve-requests", type=int, default=300)
+    ap.add_argument("--serve-precision", choices=["fp64", "mixed"], default="fp64")
     return ap.parse_args()
 
 
@@ -140,10 +144,10 @@ class ClockSampler:
 # ------------------------------------------------------------- CPU oracle
 def oracle_sample(n: int, nc: int, bc_kinds, wu: dict):
     """Time the CPU oracle on a bounded sample of the workload: Bi-CG
-    iterations on the 256^3 level of the same problem (one more iteration in
-    the second call than in the first; the difference is one iteration), then
-    scale to one solve: seconds per iteration x (512/256)^3 x the solve's work
-    units.  Single-threaded C."""
+    iterations on the 256^3 level of the same problem (three more iterations
+    in the second call than in the first; the difference over three is one
+    iteration), then scale to one solve: seconds per iteration x
+    ((512-1)/(256-1))^3 x the solve's work units.  Single-threaded C."""
     import oracle
     from paper_1901_05118_gb300 import problems
 
@@ -157,15 +161,16 @@ def oracle_sample(n: int, nc: int, bc_kinds, wu: dict):
         t0 = time.perf_counter()
         oracle.bicg(ns, bc, fh, x0, 0.0, max_iter=1)
         t1 = time.perf_counter()
-        oracle.bicg(ns, bc, fh, x0, 0.0, max_iter=2)
+        oracle.bicg(ns, bc, fh, x0, 0.0, max_iter=4)
         t2 = time.perf_counter()
-        t_it.append(max((t2 - t1) - (t1 - t0), 1e-9))
+        t_it.append(max(((t2 - t1) - (t1 - t0)) / 3.0, 1e-9))
     scale = ((n - 1) / (ns - 1)) ** 3
     per_solve = [t * scale * wu[bc] for t, bc in zip(t_it, bc_kinds)]
     return sum(per_solve) / len(per_solve), {
         "kind": "oracle", "cores": 1,
         "sample": (f"single-threaded C oracle: one Bi-CG iteration on the {ns}^3 level of the same problem, "
-                   f"per boundary kind ({', '.join(f'{t:.2f} s' for t in t_it)}), scaled by "
+                   f"per boundary kind ({', '.join(f'{t:.2f} s' for t in t_it)}; difference of 4- and "
+                   f"1-iteration calls over 3), scaled by "
                    f"((N-1)/({ns}-1))^3 to {n}^3 and by the solve's work units "
                    f"({', '.join(f'{wu[b]:.1f}' for b in bc_kinds)} finest-grid iterations)")}
 
@@ -275,19 +280,34 @@ def run_ours(args):
         barrier()
         e2 = torch.cuda.Event(enable_timing=True)
         e3 = torch.cuda.Event(enable_timing=True)
+        marks = []
         e2.record(stream)
         for _ in range(args.steps):
             for bc in bcs:
+                m = [torch.cuda.Event(enable_timing=True) for _ in range(3)]
                 d["f"].copy_(host["f"], non_blocking=True)
                 d["g1"].copy_(host["g1"], non_blocking=True)
                 d[f"g2_{bc}"].copy_(host[f"g2_{bc}"], non_blocking=True)
+                m[0].record(stream)
                 solve(bc)
+                m[1].record(stream)
                 u_host.copy_(u_out, non_blocking=True)
+                m[2].record(stream)
+                marks.append(m)
         e3.record(stream)
         barrier()
+        prev = e2
+        h2d_ms = solve_ms = d2h_ms = 0.0
+        for m in marks:
+            h2d_ms += prev.elapsed_time(m[0])
+            solve_ms += m[0].elapsed_time(m[1])
+            d2h_ms += m[1].elapsed_time(m[2])
+            prev = m[2]
         ms_e2e = max_over_ranks(e2.elapsed_time(e3) / args.steps, world, dev)
+        ns = args.steps * len(bcs)
         e2e = {"value": seconds_per_solve(ms_e2e, len(bcs), world), "unit": "s",
-               "h2d_bytes_per_step": h2d * len(bcs), "d2h_bytes_per_step": d2h * len(bcs)}
+               "h2d_bytes_per_step": h2d * len(bcs), "d2h_bytes_per_step": d2h * len(bcs),
+               "per_solve_ms": {"h2d": h2d_ms / ns, "solve": solve_ms / ns, "d2h": d2h_ms / ns}}
 
     # ---- roofline of the operator kernel on the finest grid
     peaks = {}
@@ -308,6 +328,13 @@ def run_ours(args):
     if not args.no_mixed:
         mixed = precision_leg(args, B, problems, ctx, dev, stream, barrier, world)
 
+    batched = None
+    if not args.no_batch:
+        batched = batched_leg(args, B, problems, ctx, dev)
+    served = None
+    if not args.no_serve:
+        served = serving_leg(args, B, ctx, dev)
+
     wu = {bc: sum(s["iters"] * (s["n"] / n) ** 3 for s in stats[bc] if s["iters"]) for bc in bcs}
     line = {"metric": METRIC, "value": value, "unit": "s", "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": ms_step, "higher_is_better": False, "scaling": "weak",
@@ -315,7 +342,8 @@ def run_ours(args):
             "e2e": e2e, "gpu_launches": launches, "roofline": roofline, "clocks": clk.summary(),
             "levels": {str(bc): [{"n": s["n"], "iters": s["iters"], "ms": round(s["ms"], 3),
                                   "relres": s["relres"]} for s in stats[bc]] for bc in bcs},
-            "work_units": {str(bc): round(w, 2) for bc, w in wu.items()}, "precision_leg": mixed}
+            "work_units": {str(bc): round(w, 2) for bc, w in wu.items()}, "precision_leg": mixed,
+            "batched_leg": batched, "serving_leg": served}
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         cpu_value, info = oracle_sample(n, nc, bcs, wu)
         info["value"] = cpu_value
@@ -342,7 +370,7 @@ def precision_leg(args, B, problems, ctx, dev, stream, barrier, world):
     ue = torch.from_numpy(prob.exact(n)).to(dev)
     out = {"workload": (f"{n}^3, coarsest {nc}^3, u = sin(2 pi x)sin(2 pi y)sin(2 pi z) + x^2y^2z^2, "
                         f"first- and second-kind data, FP64 residual tol {args.tol:g} per level"),
-           "inner_tol": 1e-4}
+           "inner_tol": B.MIXED_INNER_TOL, "inner_cap": B.MIXED_INNER_CAP}
     res = {}
     for prec in ("fp64", "mixed"):
         times, errs, outs = [], [], {}
@@ -350,7 +378,7 @@ def precision_leg(args, B, problems, ctx, dev, stream, barrier, world):
             g2 = torch.from_numpy(prob.boundary_g2(n, bc)).to(dev)
             u = torch.empty_like(f)
             run = lambda: B.excmg_solve(n, nc, bc, f, ue, g2, args.tol, u, ctx=ctx, precision=prec,
-                                        inner_tol=1e-4, return_stats=True)
+                                        return_stats=True, max_total=20000)
             _, st = run()   # warm-up
             barrier()
             e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
@@ -371,6 +399,104 @@ def precision_leg(args, B, problems, ctx, dev, stream, barrier, world):
                 "mixed_minus_fp64_linf": [float((omx[bc] - o64[bc]).abs().max()) for bc in (1, 2)],
                 "levels_fp64": res["levels_fp64"], "levels_mixed": res["levels_mixed"]})
     return out
+
+
+def batched_leg(args, B, problems, ctx, dev):
+    """64 independent solves, finest grids drawn (seeded) from 32..128 with
+    coarsest 8/6/8/6/8, mixed kinds of boundary data, u = four random sines;
+    FP32 correction solves in FP64 refinement, tol 1e-10.  All submitted at
+    once to the batch engine; compared with the same 64 solved one by one."""
+    import torch
+
+    rng = np.random.Generator(np.random.PCG64(0))
+    sizes = [int(v) for v in rng.choice([32, 48, 64, 96, 128], 64)]
+    coarse = {32: 8, 48: 6, 64: 8, 96: 6, 128: 8}
+    kinds = [int(v) for v in rng.integers(1, 3, 64)]
+    tol = 1e-10
+    inputs = [problems.random_sines_torch(2000 + i, sizes[i], kinds[i], dev) for i in range(64)]
+
+    def run_batch(idx, precision):
+        batch = B.Batch(ctx, max_instances=len(idx))
+        outs = {}
+        for i in idx:
+            f, g1, g2 = inputs[i]
+            ident, u = batch.submit(sizes[i], coarse[sizes[i]], kinds[i], f, g1, g2, tol, precision=precision)
+            outs[i] = (ident, u)
+        steps = 0
+        while batch.step() > 0:
+            steps += 1
+        res = {i: (batch.query(ident), u) for i, (ident, u) in outs.items()}
+        launches = batch.launches
+        batch.close()
+        return res, steps + 1, launches
+
+    # warm-up: one instance of every (coarsest, kind) builds the DSOLVE inverses
+    seen, warm = set(), []
+    for i in range(64):
+        key = (coarse[sizes[i]], kinds[i])
+        if key not in seen:
+            seen.add(key)
+            warm.append(i)
+    out = {"workload": "64 instances, n from {32,48,64,96,128} (PCG64 seed 0), coarsest 8/6/8/6/8, kinds mixed, "
+                       "u = 4 random sines, tol 1e-10 per level"}
+    for precision in ("fp64", "mixed"):
+        run_batch(warm, precision)
+        torch.cuda.synchronize(dev)
+        t0 = time.perf_counter()
+        res, steps, launches = run_batch(list(range(64)), precision)
+        torch.cuda.synchronize(dev)
+        t_batch = time.perf_counter() - t0
+        t0 = time.perf_counter()
+        seq = {}
+        for i in range(64):
+            f, g1, g2 = inputs[i]
+            seq[i] = B.excmg_solve(sizes[i], coarse[sizes[i]], kinds[i], f, g1, g2, tol, ctx=ctx, precision=precision)
+        torch.cuda.synchronize(dev)
+        t_seq = time.perf_counter() - t0
+        diff = max(float((res[i][1] - seq[i]).abs().max() / seq[i].abs().max()) for i in range(64))
+        out[precision] = {"batched_s": t_batch, "solves_per_s": 64 / t_batch, "engine_steps": steps,
+                          "launches": launches, "sequential_s": t_seq, "speedup_vs_sequential": t_seq / t_batch,
+                          "max_rel_diff_vs_sequential": diff,
+                          "all_ok": all(res[i][0]["done"] and res[i][0]["status"] == 0 for i in range(64))}
+    return out
+
+
+def serving_leg(args, B, ctx, dev):
+    """Poisson request stream (sizes log-uniform in 32..256 rounded to
+    c*2^k, kinds uniform, random-sine problems, tol 1e-8) through the batch
+    engine at 0.8x its measured capacity; p50 / p99 latency and solves/s."""
+    import torch
+
+    from paper_1901_05118_gb300 import serving as S
+
+    tol = 1e-8
+    prec = {"precision": args.serve_precision}
+    pool = S.InputPool(dev)
+    new_out = lambda n: torch.empty((n + 1,) * 3, dtype=torch.float64, device=dev)
+    # capacity: a closed burst of 64 requests from the same distribution
+    burst = S.make_requests(64, rate=1e9, seed=11)
+    pool.warm(burst)
+    warm, seen = [], set()
+    for r in burst:
+        if (r.nc, r.bc) not in seen:
+            seen.add((r.nc, r.bc))
+            warm.append(r)
+    S.serve(B.Batch(ctx, max_instances=256), warm, pool, tol, new_output=new_out, submit_kwargs=prec)
+    torch.cuda.synchronize(dev)
+    _, cap = S.serve(B.Batch(ctx, max_instances=256), burst, pool, tol, new_output=new_out, submit_kwargs=prec)
+    rate = 0.8 * cap["solves_per_s"]
+    reqs = S.make_requests(args.serve_requests, rate=rate, seed=1)
+    pool.warm(reqs)
+    torch.cuda.synchronize(dev)
+    budget = 64 * (1 << 30)
+    recs, summ = S.serve(B.Batch(ctx, hbm_budget_bytes=budget, max_instances=256), reqs, pool, tol,
+                         new_output=new_out, submit_kwargs=prec)
+    summ.update({"capacity_solves_per_s": cap["solves_per_s"], "rate_per_s": rate, "hbm_budget_bytes": budget,
+                 "precision": args.serve_precision,
+                 "workload": (f"{args.serve_requests} requests, Poisson at 0.8x capacity, n log-uniform in "
+                              "[32, 256] rounded to c*2^k (c = 4..7), kinds uniform, 4 random-sine problems "
+                              "per (n, kind), tol 1e-8")})
+    return summ
 
 
 def main():

@@ -148,6 +148,12 @@ int stencil_apply(const excmg_level *level, int transpose, const double *u, doub
 int bicg_solve(const excmg_level *level, const double *b, double *x_inout, double tol,
                int max_iter, int *iters_out, double *relres_out);
 
+/* bicg_solve with a caller-chosen shadow residual r*_0 (Alg. 2, line 2 leaves
+ * x*_0 and b* free): shadow_r0 is a node array whose interior entries give
+ * r*_0 ((r_0, r*_0) must not vanish); NULL means r*_0 = r_0. */
+int bicg_solve_ex(const excmg_level *level, const double *b, double *x_inout, const double *shadow_r0,
+                  double tol, int max_iter, int *iters_out, double *relres_out);
+
 /* EXP_finite (Sec. 4.2.2-4.2.3, Steps 1-5): third-order approximation w_h on
  * the grid with n_fine intervals (n_fine divisible by 4, >= 8) of the FD
  * solution, from the FD solutions u_2h (n_fine/2 intervals) and u_4h
@@ -211,6 +217,49 @@ int excmg_assemble_rhs(const excmg_level *level, int n_src, const double *f, con
  * (u's boundary entries left unchanged).  The first call on a (N, bc_kind)
  * factorises A_h (dense Gauss-Jordan inverse, kept in the context); N <= 32. */
 int excmg_dsolve(const excmg_level *level, const double *fh, double *u);
+
+/* ------------------------------------------------------ many solves at once */
+
+/* A batch engine runs many independent EXCMG solves (Alg. 1) concurrently on
+ * one context's GPU and stream, each in FP64 (integer operator, FP64 Bi-CG)
+ * or in the mixed-precision form (FP64 refinement around FP32 Bi-CG
+ * correction solves, see EXCMG_PRECISION_MIXED).  Every instance keeps its
+ * level hierarchy resident; the Bi-CG iterations of all instances that need
+ * them run together in one cooperative launch per value type and
+ * excmg_batch_step.  Instances may be submitted at
+ * any time and leave when done, so the batch refills continuously. */
+typedef struct excmg_batch excmg_batch;
+
+/* hbm_budget_bytes caps the device memory all live instances may hold
+ * (0 = no cap); max_instances caps their number (1..1024). */
+int excmg_batch_create(excmg_ctx *ctx, size_t hbm_budget_bytes, int max_instances, excmg_batch **out);
+int excmg_batch_destroy(excmg_batch *batch);
+const char *excmg_batch_last_error(const excmg_batch *batch);
+/* Device memory held by live instances now, and what one instance needs. */
+size_t excmg_batch_bytes(const excmg_batch *batch);
+size_t excmg_batch_instance_bytes(int n_finest, int n_coarsest, int precision);
+
+/* Admit one solve: arguments as for excmg_solve_ex (params->precision picks
+ * FP64 or mixed; max_iter caps one Bi-CG call, inner_tol is used in mixed
+ * mode).  f, g1, g2 and u_out must stay valid until the instance is done;
+ * u_out receives u_tilde.  Returns EXCMG_ERR_BUDGET (nothing admitted) when
+ * the budget or the slot count is full -- submit again after a step. */
+int excmg_batch_submit(excmg_batch *batch, int n_finest, int n_coarsest, int bc_kind, const double *f,
+                       const double *g1, const double *g2, const excmg_params *params, double *u_out,
+                       int *id_out);
+
+/* Advance every live instance (all pending per-instance steps, then one
+ * batched launch of FP32 Bi-CG iterations).  *n_live (may be NULL) receives
+ * the number of instances still running. */
+int excmg_batch_step(excmg_batch *batch, int *n_live);
+
+/* *done = 1 once instance `id` has finished; then *status is its outcome,
+ * stats (may be NULL) its per-level counters and *latency_s (may be NULL)
+ * the wall time from submit to finish. */
+int excmg_batch_query(excmg_batch *batch, int id, int *done, int *status, excmg_stats *stats,
+                      double *latency_s);
+/* Kernel launches made by the batch so far. */
+long long excmg_batch_launches(const excmg_batch *batch);
 
 #ifdef __cplusplus
 }

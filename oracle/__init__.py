@@ -56,6 +56,8 @@ def _load():
         lib.orc_interior_norm2.restype = ctypes.c_double
         lib.orc_bicg.argtypes = [ctypes.c_int, ctypes.c_int, _D, _D, ctypes.c_double,
                                  ctypes.c_double, ctypes.c_int, _I, _D]
+        lib.orc_bicg_shadow.argtypes = [ctypes.c_int, ctypes.c_int, _D, _D, _D, ctypes.c_double,
+                                        ctypes.c_double, ctypes.c_int, _I, _D]
         lib.orc_exp_finite.argtypes = [ctypes.c_int, _D, _D, _D]
         lib.orc_exp_true.argtypes = [ctypes.c_int, _D, _D, _D]
         lib.orc_excmg.argtypes = [ctypes.c_int, ctypes.c_int, ctypes.c_int, _D, _D, _D,
@@ -150,16 +152,23 @@ def interior_norm2(N: int, a) -> float:
     return float(_load().orc_interior_norm2(N, _p(a)))
 
 
-def bicg(N: int, bc_kind: int, b, x0, tol: float, bnorm: float | None = None, max_iter: int = 10**6):
-    """Alg. 2 with M = I and r*_0 = r_0.  Returns (x, iterations, relres, status)."""
+def bicg(N: int, bc_kind: int, b, x0, tol: float, bnorm: float | None = None, max_iter: int = 10**6,
+         shadow=None):
+    """Alg. 2 with M = I; r*_0 = shadow (node array, interior read) or r_0.
+    Returns (x, iterations, relres, status)."""
     b = _node(b, N)
     x = _node(x0, N).copy()
     if bnorm is None:
         bnorm = interior_norm2(N, b)
     it = ctypes.c_int(0)
     rr = ctypes.c_double(0.0)
-    rc = _load().orc_bicg(N, bc_kind, _p(b), _p(x), float(tol), float(bnorm), int(max_iter),
-                          ctypes.byref(it), ctypes.byref(rr))
+    if shadow is None:
+        rc = _load().orc_bicg(N, bc_kind, _p(b), _p(x), float(tol), float(bnorm), int(max_iter),
+                              ctypes.byref(it), ctypes.byref(rr))
+    else:
+        sh = _node(shadow, N)
+        rc = _load().orc_bicg_shadow(N, bc_kind, _p(b), _p(x), _p(sh), float(tol), float(bnorm), int(max_iter),
+                                     ctypes.byref(it), ctypes.byref(rr))
     return x, it.value, rr.value, rc
 
 

@@ -373,8 +373,19 @@ double orc_interior_norm2(int N, const double *a) { return sqrt(idot(N, a, a)); 
  * or on a breakdown (rho or sigma exactly zero / not finite).
  * x: node array; its interior is updated, its boundary left alone.
  * ---------------------------------------------------------------------- */
+int orc_bicg_shadow(int N, int bc_kind, const double *b, double *x, const double *rs0, double tol,
+                    double bnorm, int max_iter, int *iters_out, double *relres_out);
+
 int orc_bicg(int N, int bc_kind, const double *b, double *x, double tol, double bnorm,
              int max_iter, int *iters_out, double *relres_out) {
+    return orc_bicg_shadow(N, bc_kind, b, x, NULL, tol, bnorm, max_iter, iters_out, relres_out);
+}
+
+/* Alg. 2 with a caller-chosen shadow residual r*_0 (line 2 of the algorithm
+ * leaves x*_0 and b* free, i.e. any r*_0 with (r_0, r*_0) != 0); rs0 = NULL
+ * takes r*_0 = r_0. */
+int orc_bicg_shadow(int N, int bc_kind, const double *b, double *x, const double *rs0, double tol,
+                    double bnorm, int max_iter, int *iters_out, double *relres_out) {
     size_t total = (size_t)(N + 1) * (size_t)(N + 1) * (size_t)(N + 1), q;
     double *r, *rs, *p, *ps, *Ap, *Atps;
     double rho, rho_new, sigma, alpha, beta, rnorm;
@@ -395,7 +406,7 @@ int orc_bicg(int N, int bc_kind, const double *b, double *x, double tol, double 
             for (i = 1; i <= N - 1; ++i) {
                 q = nidx(N, i, j, k);
                 r[q] = b[q] - Ap[q];
-                rs[q] = r[q];
+                rs[q] = rs0 ? rs0[q] : r[q];
                 p[q] = r[q];
                 ps[q] = rs[q];
             }

@@ -7,7 +7,7 @@ this package exposes it through a thin ctypes binding with the same names.
 first use of an API name, and raises if the library has not been built.
 """
 _API = ("excmg_solve", "stencil_apply", "bicg_solve", "extrapolate_interpolate", "midpoint_extrapolate",
-        "excmg_assemble_rhs", "excmg_dsolve", "Context", "Level", "ExcmgError", "default_context")
+        "excmg_assemble_rhs", "excmg_dsolve", "Context", "Level", "ExcmgError", "default_context", "Batch")
 
 __all__ = list(_API) + ["problems"]
 

@@ -32,6 +32,8 @@ STATUS_NAMES = {0: "EXCMG_OK", -1: "EXCMG_ERR_ARG", -2: "EXCMG_ERR_OOM", -3: "EX
 TOL_MODES = {"paper": 0, "uniform": 1}
 STENCIL_VARIANTS = {"exact": 0, "fp64": 1}
 PRECISIONS = {"fp64": 0, "mixed": 1}
+MIXED_INNER_CAP = 500      # iterations of one FP32 correction solve
+MIXED_INNER_TOL = 1e-4     # residual reduction asked of one FP32 correction solve
 MAX_LEVELS = 16
 
 
@@ -75,6 +77,7 @@ _lib.excmg_level_create.argtypes = [_vp, _i, _i, ctypes.POINTER(_vp)]
 _lib.excmg_level_destroy.argtypes = [_vp]
 _lib.stencil_apply.argtypes = [_vp, _i, _vp, _vp]
 _lib.bicg_solve.argtypes = [_vp, _vp, _vp, _d, _i, ctypes.POINTER(_i), ctypes.POINTER(_d)]
+_lib.bicg_solve_ex.argtypes = [_vp, _vp, _vp, _vp, _d, _i, ctypes.POINTER(_i), ctypes.POINTER(_d)]
 _lib.extrapolate_interpolate.argtypes = [_i, _vp, _vp, _vp]
 _lib.extrapolate_interpolate_ex.argtypes = [_vp, _i, _vp, _vp, _vp]
 _lib.midpoint_extrapolate.argtypes = [_i, _vp, _vp, _vp]
@@ -85,9 +88,29 @@ _lib.excmg_solve_ex.argtypes = [_vp, _i, _i, _i, _vp, _vp, _vp, ctypes.POINTER(P
 _lib.excmg_assemble_rhs.argtypes = [_vp, _i, _vp, _vp, _vp, _vp]
 _lib.excmg_dsolve.argtypes = [_vp, _vp, _vp]
 
+_lib.excmg_batch_create.argtypes = [_vp, _sz, _i, ctypes.POINTER(_vp)]
+_lib.excmg_batch_destroy.argtypes = [_vp]
+_lib.excmg_batch_last_error.argtypes = [_vp]
+_lib.excmg_batch_last_error.restype = ctypes.c_char_p
+_lib.excmg_batch_bytes.argtypes = [_vp]
+_lib.excmg_batch_bytes.restype = _sz
+_lib.excmg_batch_instance_bytes.argtypes = [_i, _i, _i]
+_lib.excmg_batch_instance_bytes.restype = _sz
+_lib.excmg_batch_submit.argtypes = [_vp, _i, _i, _i, _vp, _vp, _vp, ctypes.POINTER(Params), _vp,
+                                    ctypes.POINTER(_i)]
+_lib.excmg_batch_step.argtypes = [_vp, ctypes.POINTER(_i)]
+_lib.excmg_batch_query.argtypes = [_vp, _i, ctypes.POINTER(_i), ctypes.POINTER(_i), ctypes.POINTER(Stats),
+                                   ctypes.POINTER(_d)]
+_lib.excmg_batch_launches.argtypes = [_vp]
+_lib.excmg_batch_launches.restype = ctypes.c_longlong
+
+for _name in ("excmg_batch_create", "excmg_batch_destroy", "excmg_batch_submit", "excmg_batch_step",
+              "excmg_batch_query"):
+    getattr(_lib, _name).restype = _i
+
 for _name in ("excmg_ctx_create", "excmg_ctx_destroy", "excmg_ctx_set_stencil", "excmg_ctx_profile",
               "excmg_ctx_profile_read", "excmg_level_create", "excmg_level_destroy",
-              "stencil_apply", "bicg_solve", "extrapolate_interpolate", "extrapolate_interpolate_ex",
+              "stencil_apply", "bicg_solve", "bicg_solve_ex", "extrapolate_interpolate", "extrapolate_interpolate_ex",
               "midpoint_extrapolate", "midpoint_extrapolate_ex", "excmg_solve", "excmg_solve_ex",
               "excmg_assemble_rhs", "excmg_dsolve"):
     getattr(_lib, _name).restype = _i
@@ -227,13 +250,19 @@ def stencil_apply(level: Level, u: torch.Tensor, y: torch.Tensor | None = None,
     return y
 
 
-def bicg_solve(level: Level, b: torch.Tensor, x: torch.Tensor, tol: float, max_iter: int = 100000):
-    """Alg. 2 (M = I, r*_0 = r_0) on A_h x = b in place; returns (iters, relres, status)."""
+def bicg_solve(level: Level, b: torch.Tensor, x: torch.Tensor, tol: float, max_iter: int = 100000,
+               shadow: torch.Tensor | None = None):
+    """Alg. 2 (M = I; r*_0 = shadow, or r_0) on A_h x = b in place; returns (iters, relres, status)."""
     n = level.n
     it = ctypes.c_int(0)
     rr = ctypes.c_double(0.0)
-    rc = _lib.bicg_solve(level.handle, _vp(_node(b, n, "b")), _vp(_node(x, n, "x")), float(tol),
-                         int(max_iter), ctypes.byref(it), ctypes.byref(rr))
+    if shadow is None:
+        rc = _lib.bicg_solve(level.handle, _vp(_node(b, n, "b")), _vp(_node(x, n, "x")), float(tol),
+                             int(max_iter), ctypes.byref(it), ctypes.byref(rr))
+    else:
+        rc = _lib.bicg_solve_ex(level.handle, _vp(_node(b, n, "b")), _vp(_node(x, n, "x")),
+                                _vp(_node(shadow, n, "shadow")), float(tol), int(max_iter), ctypes.byref(it),
+                                ctypes.byref(rr))
     if rc not in (EXCMG_OK, -4):
         level.ctx.check(rc, "bicg_solve")
     return it.value, rr.value, rc
@@ -283,9 +312,9 @@ def excmg_dsolve(level: Level, fh: torch.Tensor, u: torch.Tensor) -> torch.Tenso
 
 def excmg_solve(n_finest: int, n_coarsest: int, bc_kind: int, f: torch.Tensor, g1: torch.Tensor,
                 g2: torch.Tensor, tol: float, u_out: torch.Tensor | None = None, *,
-                ctx: Context | None = None, tol_mode: str = "uniform", max_iter: int = 100000,
+                ctx: Context | None = None, tol_mode: str = "uniform", max_iter: int | None = None,
                 max_total: int = 1000000, check_every: int = 16, u_h_out: torch.Tensor | None = None,
-                return_stats: bool = False, precision: str = "fp64", inner_tol: float = 1e-4):
+                return_stats: bool = False, precision: str = "fp64", inner_tol: float = MIXED_INNER_TOL):
     """Alg. 1.  Returns u_tilde (EXP_true on the finest grid), and the
     per-level statistics when return_stats is set.  precision="mixed" runs
     the Bi-CG levels as FP32 correction solves inside FP64 refinement."""
@@ -293,6 +322,11 @@ def excmg_solve(n_finest: int, n_coarsest: int, bc_kind: int, f: torch.Tensor, g
     n = int(n_finest)
     if u_out is None:
         u_out = _new_node(n, f)
+    if max_iter is None:
+        # FP64: one Bi-CG call may run to convergence; mixed: each FP32
+        # correction solve is capped (FP32 recurrences stop paying off after
+        # a few hundred iterations on these operators)
+        max_iter = 100000 if precision == "fp64" else MIXED_INNER_CAP
     params = Params(float(tol), TOL_MODES[tol_mode], int(max_iter), int(max_total), int(check_every),
                     PRECISIONS[precision], float(inner_tol))
     stats = Stats()
@@ -304,3 +338,92 @@ def excmg_solve(n_finest: int, n_coarsest: int, bc_kind: int, f: torch.Tensor, g
     if return_stats:
         return u_out, stats.as_list()
     return u_out
+
+
+# ------------------------------------------------------------ many solves
+class Batch:
+    """Many independent EXCMG solves on one GPU (FP64 refinement around FP32
+    correction solves); see excmg_batch_* in include/excmg.h.  Tensors passed
+    to submit() are kept alive here until their instance is done."""
+
+    def __init__(self, ctx: Context | None = None, hbm_budget_bytes: int = 0, max_instances: int = 64):
+        self.ctx = ctx or default_context()
+        h = _vp()
+        rc = _lib.excmg_batch_create(self.ctx.handle, int(hbm_budget_bytes), int(max_instances), ctypes.byref(h))
+        if rc != EXCMG_OK:
+            raise ExcmgError(rc, "excmg_batch_create failed")
+        self.handle = h
+        self._keep = {}
+
+    def _check(self, rc, what):
+        if rc != EXCMG_OK:
+            msg = _lib.excmg_batch_last_error(self.handle)
+            raise ExcmgError(rc, f"{what}: {msg.decode() if msg else ''}")
+
+    @staticmethod
+    def instance_bytes(n_finest: int, n_coarsest: int, precision: str = "mixed") -> int:
+        return int(_lib.excmg_batch_instance_bytes(int(n_finest), int(n_coarsest), PRECISIONS[precision]))
+
+    @property
+    def bytes(self) -> int:
+        return int(_lib.excmg_batch_bytes(self.handle))
+
+    @property
+    def launches(self) -> int:
+        return int(_lib.excmg_batch_launches(self.handle))
+
+    def submit(self, n_finest: int, n_coarsest: int, bc_kind: int, f: torch.Tensor, g1: torch.Tensor,
+               g2: torch.Tensor, tol: float, u_out: torch.Tensor | None = None, *, tol_mode: str = "uniform",
+               precision: str = "mixed", inner_tol: float = MIXED_INNER_TOL, max_iter: int | None = None,
+               max_total: int = 1000000):
+        """Admit one solve; returns (id, u_out), or None when the budget or the
+        slots are full right now."""
+        n = int(n_finest)
+        if u_out is None:
+            u_out = _new_node(n, f)
+        if max_iter is None:
+            max_iter = 100000 if precision == "fp64" else MIXED_INNER_CAP
+        params = Params(float(tol), TOL_MODES[tol_mode], int(max_iter), int(max_total), 16, PRECISIONS[precision],
+                        float(inner_tol))
+        ident = ctypes.c_int(-1)
+        rc = _lib.excmg_batch_submit(self.handle, n, int(n_coarsest), int(bc_kind), _vp(_node(f, n, "f")),
+                                     _vp(_node(g1, n, "g1")), _vp(_faces(g2, n, "g2")), ctypes.byref(params),
+                                     _vp(_node(u_out, n, "u_out")), ctypes.byref(ident))
+        if rc == -9:
+            return None
+        self._check(rc, "excmg_batch_submit")
+        self._keep[ident.value] = (f, g1, g2, u_out)
+        return ident.value, u_out
+
+    def step(self) -> int:
+        live = ctypes.c_int(0)
+        self._check(_lib.excmg_batch_step(self.handle, ctypes.byref(live)), "excmg_batch_step")
+        return live.value
+
+    def query(self, ident: int):
+        done = ctypes.c_int(0)
+        status = ctypes.c_int(0)
+        stats = Stats()
+        lat = ctypes.c_double(0.0)
+        self._check(_lib.excmg_batch_query(self.handle, int(ident), ctypes.byref(done), ctypes.byref(status),
+                                           ctypes.byref(stats), ctypes.byref(lat)), "excmg_batch_query")
+        if done.value:
+            self._keep.pop(int(ident), None)
+            return {"done": True, "status": status.value, "stats": stats.as_list(), "latency_s": lat.value}
+        return {"done": False}
+
+    def run(self) -> None:
+        """Step until no instance is live."""
+        while self.step() > 0:
+            pass
+
+    def close(self):
+        if getattr(self, "handle", None):
+            _lib.excmg_batch_destroy(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass

@@ -1,0 +1,979 @@
+// Many independent EXCMG solves on one GPU at once.
+//
+// Each instance keeps its whole level hierarchy (Alg. 1) and its FP64/FP32
+// refinement state resident on the device and moves through a small state
+// machine: direct solves of the two coarsest grids, then per Bi-CG level
+// EXP_finite + right-hand side, FP64 residual, FP32 correction solve,
+// FP64 update, until the level's tolerance (or the stagnation rule) is met,
+// and finally EXP_true.  The expensive part -- the FP32 Bi-CG iterations of
+// the correction solves (Alg. 2, M = I, r*_0 = r_0) -- runs for ALL
+// instances that are in that phase in one cooperative launch: CTAs take
+// operator tiles and vector chunks from every instance, instances advance
+// in lock step one iteration per grid-barrier round, and each instance's
+// scalars are formed by the CTA that completes its last tile / chunk.
+// Instances can be submitted at any time (the engine admits them against
+// its device-memory budget) and leave as soon as they are done, so the
+// batch continuously refills: the same engine serves the fixed batch and
+// the request stream.
+#include <algorithm>
+#include <chrono>
+#include <cmath>
+#include <cstring>
+#include <vector>
+
+#include "excmg_internal.cuh"
+#include "march_f32.cuh"
+#include "march_fx.cuh"
+#include "reduce.cuh"
+
+namespace excmg {
+namespace {
+
+constexpr int kChunk = 8192;          // vector entries per chunk of the batched kernel
+constexpr int kBatchMaxInst = 1024;
+
+template <typename T>
+struct BatchInst {     // device table entry, one per instance in the Bi-CG phase
+    int n;
+    int sigma;
+    int gx, gy, kz_per, nunits, unit_begin;
+    int nchunks, chunk_begin;
+    int slot;          // index into the state array
+    long long len;
+    T *x, *r, *rs, *p, *ps, *q, *qs;
+};
+
+// One tile's operator pair (A p, A p* -- A is symmetric) and its share of
+// (p*, A p): FP32 arithmetic for the correction solves, the integer
+// evaluation for FP64 solves.
+__device__ __forceinline__ float march_pair(const BatchInst<float>& in, int bx, int by, int kz0, int kz1) {
+    return f32_march<2, true>(in.p, in.ps, in.q, in.qs, in.n, (float)in.sigma, bx, by, kz0, kz1);
+}
+__device__ __forceinline__ double march_pair(const BatchInst<double>& in, int bx, int by, int kz0, int kz1) {
+    const FxFields fl{{in.p, in.ps}, {in.q, in.qs}};
+    return fx_march<2, true>(fl, nullptr, in.n, in.sigma, bx, by, kz0, kz1);
+}
+
+struct BatchState {    // device, one per slot
+    double rho, rr, alpha, beta, sigma, tol;
+    int iter, max_iter, done, status;
+    unsigned int ticket_a, ticket_b;
+};
+
+struct BatchBarrier {
+    unsigned int* count;
+    unsigned int* gen;
+    int* err;
+};
+
+__device__ bool batch_sync(const BatchBarrier& gb, unsigned int nblocks) {
+    __syncthreads();
+    if (thread0()) {
+        volatile unsigned int* gen = gb.gen;
+        volatile int* err = gb.err;
+        const unsigned int g = *gen;
+        __threadfence();
+        if (atomicAdd(gb.count, 1u) == nblocks - 1u) {
+            atomicExch(gb.count, 0u);
+            __threadfence();
+            atomicAdd(gb.gen, 1u);
+        } else {
+            long long spins = 0;
+            while (*gen == g) {
+                if (*err) break;
+                if (++spins > (1ll << 22)) {
+                    atomicExch(gb.err, 1);
+                    break;
+                }
+                __nanosleep(32);
+            }
+        }
+        __threadfence();
+    }
+    __syncthreads();
+    return *(volatile int*)gb.err == 0;
+}
+
+// Instance owning global index g, given each instance's first index.
+__device__ __forceinline__ int owner(const int* begin, int ninst, int g) {
+    int lo = 0, hi = ninst - 1;
+    while (lo < hi) {
+        const int mid = (lo + hi + 1) >> 1;
+        if (begin[mid] <= g) lo = mid;
+        else hi = mid - 1;
+    }
+    return lo;
+}
+
+// True in every thread of the CTA that took the last ticket of `ticket`.
+__device__ __forceinline__ bool take_last(unsigned int* ticket, unsigned int total, bool* flag) {
+    if (thread0()) {
+        __threadfence();
+        *flag = atomicAdd(ticket, 1u) == total - 1u;
+    }
+    __syncthreads();
+    const bool last = *flag;
+    __syncthreads();
+    return last;
+}
+
+__device__ __forceinline__ double sum_range(const double* v, int begin, int count, int stride, double* sh) {
+    const int tid = threadIdx.x + blockDim.x * threadIdx.y;
+    const int nt = blockDim.x * blockDim.y;
+    double s = 0.0;
+    for (int k = tid; k < count; k += nt) s += __ldcg(&v[(size_t)(begin + k) * stride]);
+    return block_sum(s, sh);
+}
+
+template <typename T>
+__global__ void __launch_bounds__(S_NT)
+batch_bicg_kernel(const BatchInst<T>* __restrict__ inst, const int* __restrict__ unit_begin,
+                    const int* __restrict__ chunk_begin, int ninst, int total_units, int total_chunks,
+                    double* unit_part, double* chunk_part, BatchState* states, int iters, int* active,
+                    BatchBarrier gb) {
+    __shared__ double sh[32];
+    __shared__ T shf[32];
+    __shared__ bool flag;
+    const unsigned int G = gridDim.x;
+    const int tid = threadIdx.x + blockDim.x * threadIdx.y;
+    const int nt = blockDim.x * blockDim.y;
+    bool ok = true;
+    for (int it = 0; it < iters && ok; ++it) {
+        // phase A: q = A p, q* = A p*, per-tile (p*, q); the CTA finishing an
+        // instance's last tile forms sigma and alpha
+        for (int u = blockIdx.x; u < total_units; u += G) {
+            const int i = owner(unit_begin, ninst, u);
+            const BatchInst<T>& in = inst[i];
+            BatchState& st = states[in.slot];
+            if (*(volatile int*)&st.done) continue;
+            const int loc = u - in.unit_begin;
+            const int bx = loc % in.gx, by = (loc / in.gx) % in.gy, bz = loc / (in.gx * in.gy);
+            const int kz0 = 1 + bz * in.kz_per;
+            const T d = march_pair(in, bx, by, kz0, min(kz0 + in.kz_per, in.n));
+            const double ds = (double)block_sum(d, shf);
+            if (thread0()) unit_part[u] = ds;
+            if (take_last(&st.ticket_a, (unsigned)in.nunits, &flag)) {
+                const double sg = sum_range(unit_part, in.unit_begin, in.nunits, 1, sh);
+                if (thread0()) {
+                    st.sigma = sg;
+                    if (!(st.rho != 0.0 && isfinite(st.rho)) || !(sg != 0.0 && isfinite(sg))) {
+                        st.status = kBreakdown;
+                        st.done = 1;
+                        atomicSub(active, 1);
+                    } else {
+                        st.alpha = st.rho / sg;
+                    }
+                    st.ticket_a = 0;
+                }
+            }
+        }
+        if (!(ok = batch_sync(gb, G))) break;
+        // phase B: x += alpha p; r -= alpha q; r* -= alpha q*; per-chunk
+        // (r*, r), (r, r); the CTA finishing the last chunk forms beta and
+        // tests convergence
+        for (int c = blockIdx.x; c < total_chunks; c += G) {
+            const int i = owner(chunk_begin, ninst, c);
+            const BatchInst<T>& in = inst[i];
+            BatchState& st = states[in.slot];
+            if (*(volatile int*)&st.done) continue;
+            const T alpha = (T)st.alpha;
+            const long long t0 = (long long)(c - in.chunk_begin) * kChunk;
+            const long long t1 = min(t0 + kChunk, in.len);
+            T vr = 0, vrr = 0;
+            for (long long t = t0 + tid; t < t1; t += nt) {
+                in.x[t] = in.x[t] + alpha * in.p[t];
+                const T rn = in.r[t] - alpha * in.q[t];
+                const T rsn = in.rs[t] - alpha * in.qs[t];
+                in.r[t] = rn;
+                in.rs[t] = rsn;
+                vr += rsn * rn;
+                vrr += rn * rn;
+            }
+            const double a = (double)block_sum(vr, shf);
+            const double b = (double)block_sum(vrr, shf);
+            if (thread0()) {
+                chunk_part[2 * (size_t)c] = a;
+                chunk_part[2 * (size_t)c + 1] = b;
+            }
+            if (take_last(&st.ticket_b, (unsigned)in.nchunks, &flag)) {
+                const double rho_new = sum_range(chunk_part, in.chunk_begin, in.nchunks, 2, sh);
+                const double rr = sum_range(chunk_part + 1, in.chunk_begin, in.nchunks, 2, sh);
+                if (thread0()) {
+                    st.beta = rho_new / st.rho;
+                    st.rho = rho_new;
+                    st.rr = rr;
+                    st.iter += 1;
+                    if (sqrt(rr) <= st.tol) {
+                        st.status = kConverged;
+                        st.done = 1;
+                        atomicSub(active, 1);
+                    } else if (st.iter >= st.max_iter) {
+                        st.status = kCapped;
+                        st.done = 1;
+                        atomicSub(active, 1);
+                    }
+                    st.ticket_b = 0;
+                }
+            }
+        }
+        if (!(ok = batch_sync(gb, G))) break;
+        // the counter changes only in phases A and B: between this barrier
+        // and the next every CTA reads the same value
+        if (*(volatile int*)active <= 0) break;
+        // phase C: p = r + beta p; p* = r* + beta p*
+        for (int c = blockIdx.x; c < total_chunks; c += G) {
+            const int i = owner(chunk_begin, ninst, c);
+            const BatchInst<T>& in = inst[i];
+            const BatchState& st = states[in.slot];
+            if (*(volatile const int*)&st.done) continue;
+            const T beta = (T)st.beta;
+            const long long t0 = (long long)(c - in.chunk_begin) * kChunk;
+            const long long t1 = min(t0 + kChunk, in.len);
+            for (long long t = t0 + tid; t < t1; t += nt) {
+                in.p[t] = in.r[t] + beta * in.p[t];
+                in.ps[t] = in.rs[t] + beta * in.ps[t];
+            }
+        }
+        if (!(ok = batch_sync(gb, G))) break;
+    }
+    if (!ok && blockIdx.x == 0 && thread0()) *active = -1;   // barrier gave up
+}
+
+// r32 = r / s, e = 0, r*_0 = p_0 = p*_0 = r_0 and rho_0 = (r_0, r_0) of one
+// instance's correction solve; the state is initialised by the last CTA.
+__global__ void __launch_bounds__(kVecThreads)
+batch_init32_kernel(const double* __restrict__ r64, double inv_s, float* __restrict__ r32, float* __restrict__ e,
+                    float* __restrict__ rs, float* __restrict__ p, float* __restrict__ ps, size_t len,
+                    double* partials, unsigned int* ticket, BatchState* st, double tol, int max_iter) {
+    __shared__ float shf[32];
+    __shared__ double sh[32];
+    __shared__ bool am_last;
+    float v = 0.f;
+    for (size_t t = blockIdx.x * (size_t)blockDim.x + threadIdx.x; t < len; t += (size_t)gridDim.x * blockDim.x) {
+        const float rv = (float)(r64[t] * inv_s);
+        r32[t] = rv;
+        e[t] = 0.f;
+        rs[t] = rv;
+        p[t] = rv;
+        ps[t] = rv;
+        v += rv * rv;
+    }
+    const double s = (double)block_sum(v, shf);
+    if (publish_partials(&s, 1, partials, ticket, &am_last)) {
+        const double tot = gather_partials(partials, 0, sh);
+        if (thread0()) {
+            st->rho = tot;
+            st->rr = tot;
+            st->alpha = st->beta = st->sigma = 0.0;
+            st->tol = tol * sqrt(tot);
+            st->iter = 0;
+            st->max_iter = max_iter;
+            const bool conv = sqrt(tot) <= st->tol;
+            st->done = conv ? 1 : 0;
+            st->status = conv ? kConverged : kRunning;
+            st->ticket_a = st->ticket_b = 0;
+            *ticket = 0;
+        }
+    }
+}
+
+__global__ void __launch_bounds__(kVecThreads)
+batch_correct_kernel(double* __restrict__ u, const float* __restrict__ e, size_t len, double s) {
+    for (size_t t = blockIdx.x * (size_t)blockDim.x + threadIdx.x; t < len; t += (size_t)gridDim.x * blockDim.x)
+        u[t] = u[t] + s * (double)e[t];
+}
+
+template <typename T>
+int batch_resident_ctas() {
+    static int occ = 0;
+    if (!occ) {
+        if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, batch_bicg_kernel<T>, S_NT, 0) != cudaSuccess) {
+            cudaGetLastError();
+            occ = 1;
+        }
+        if (occ < 1) occ = 1;
+        if (occ > 2) occ = 2;
+    }
+    return 152 * occ;
+}
+
+}  // namespace
+}  // namespace excmg
+
+using namespace excmg;
+
+// ------------------------------------------------------------------ host side
+namespace {
+
+enum Phase { kSetup = 0, kResidual = 1, kInner = 2, kFinal = 3, kDone = 4, kFailed = 5 };
+
+struct Instance {
+    int id = -1;
+    int n = 0, nc = 0, bc = 1, nl = 0, L = 0;
+    int prec = EXCMG_PRECISION_MIXED;
+    const double* f = nullptr;
+    const double* g1 = nullptr;
+    const double* g2 = nullptr;
+    double* u_out = nullptr;
+    double tol = 1e-8, inner_tol = 1e-4;
+    int tol_mode = EXCMG_TOL_UNIFORM;
+    int max_iter = 100000, max_total = 1000000;
+    // device buffers (one allocation)
+    void* block = nullptr;
+    size_t bytes = 0;
+    std::vector<double*> u;    // per level
+    double *fh = nullptr, *res = nullptr, *W = nullptr;
+    // FP64 Bi-CG vectors (r is `res`)
+    double *rs64 = nullptr, *p64 = nullptr, *ps64 = nullptr, *q64 = nullptr, *qs64 = nullptr;
+    // FP32 correction solve vectors
+    float *r32 = nullptr, *e = nullptr, *r = nullptr, *rs = nullptr, *p = nullptr, *ps = nullptr, *q = nullptr,
+          *qs = nullptr;
+    // progress
+    Phase phase = kSetup;
+    int level = 0;
+    int iters = 0, outer = 0, bad = 0, stag = 0;
+    double fnorm = 0.0, rel = 0.0, prev = 0.0, scale = 0.0;
+    int status = EXCMG_OK;
+    excmg_stats stats{};
+    double t_submit = 0.0, t_done = 0.0;
+};
+
+double now_s() {
+    return std::chrono::duration<double>(std::chrono::steady_clock::now().time_since_epoch()).count();
+}
+
+size_t align256(size_t b) { return (b + 255) / 256 * 256; }
+
+size_t instance_bytes(int n, int nc, int prec) {
+    size_t b = 0;
+    for (int m = nc; m <= n; m *= 2) b += align256(node_count(m) * sizeof(double));   // u per level
+    b += 2 * align256(node_count(n) * sizeof(double));                                   // fh, res
+    b += align256(node_count(n / 2) * sizeof(double));                                   // W
+    if (prec == EXCMG_PRECISION_FP64)
+        b += 5 * align256(node_count(n) * sizeof(double));                               // r*, p, p*, q, q*
+    else
+        b += 8 * align256(node_count(n) * sizeof(float));                                // r32, e, 6 vectors
+    return b;
+}
+
+}  // namespace
+
+struct excmg_batch {
+    excmg_ctx* ctx = nullptr;
+    size_t budget = 0, bytes = 0;
+    int max_instances = 0;
+    int next_id = 0;
+    std::vector<Instance*> live;
+    std::vector<Instance*> finished;
+    // device tables (one per value type)
+    BatchInst<float>* d_inst32 = nullptr;
+    BatchInst<double>* d_inst64 = nullptr;
+    int* d_unit_begin = nullptr;
+    int* d_chunk_begin = nullptr;
+    BatchState* d_states = nullptr;
+    BatchState* h_states = nullptr;
+    double* d_unit_part = nullptr;
+    double* d_chunk_part = nullptr;
+    int* d_active = nullptr;
+    int* h_active = nullptr;
+    unsigned int* d_barrier = nullptr;
+    double* d_norms = nullptr;   // per-slot norms
+    double* h_norms = nullptr;
+    size_t unit_cap = 0, chunk_cap = 0;
+    int inner_chunk = 256;       // iterations per batched launch
+    std::string last_error;
+    long long launches = 0;
+};
+
+namespace {
+
+void bnote(excmg_batch* b, long long k) {
+    b->launches += k;
+    note_launches(k);
+}
+
+int bfail(excmg_batch* b, int st, const std::string& m) {
+    b->last_error = m;
+    return st;
+}
+
+int bcuda(excmg_batch* b, cudaError_t e, const char* what) {
+    if (e == cudaSuccess) return EXCMG_OK;
+    cudaGetLastError();
+    return bfail(b, EXCMG_ERR_CUDA, std::string(what) + ": " + cudaGetErrorString(e));
+}
+
+int slot_of(excmg_batch* b, Instance* in) {
+    for (size_t k = 0; k < b->live.size(); ++k)
+        if (b->live[k] == in) return (int)k;
+    return -1;
+}
+
+void free_instance(excmg_batch* b, Instance* in) {
+    if (in->block) {
+        cudaFree(in->block);
+        b->bytes -= in->bytes;
+        in->block = nullptr;
+    }
+}
+
+// Level l's eps (Alg. 1, line 5).
+double level_eps(const Instance* in, int l) {
+    const int i = l - 1;
+    return in->tol_mode == EXCMG_TOL_PAPER ? in->tol * std::pow(10.0, (double)(i - in->L)) : in->tol;
+}
+
+// ||a||_2 over the level for every instance listed, one sync.
+int norms(excmg_batch* b, const std::vector<std::pair<Instance*, const double*>>& work) {
+    excmg_ctx* ctx = b->ctx;
+    for (size_t k = 0; k < work.size(); ++k) {
+        Instance* in = work[k].first;
+        const int N = in->nc << in->level;
+        cudaError_t e = launch_dot(work[k].second, work[k].second, node_count(N), ctx->partials, ctx->ticket,
+                                   b->d_norms + k, ctx->stream);
+        bnote(b, 1);
+        if (e != cudaSuccess) return bcuda(b, e, "batch norm");
+    }
+    if (work.empty()) return EXCMG_OK;
+    cudaError_t e = cudaMemcpyAsync(b->h_norms, b->d_norms, work.size() * sizeof(double), cudaMemcpyDeviceToHost,
+                                    ctx->stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(ctx->stream);
+    return bcuda(b, e, "batch norm read");
+}
+
+// Set up level `in->level`: right-hand side, initial guess, and for the two
+// coarsest levels the direct solve.
+int setup_level(excmg_batch* b, Instance* in) {
+    excmg_ctx* ctx = b->ctx;
+    const int l = in->level, N = in->nc << l, stride = in->n / N;
+    double* u = in->u[l];
+    cudaError_t e = launch_assemble_rhs(in->fh, N, in->bc, in->f, in->g1, in->g2, stride, ctx->stream);
+    if (e == cudaSuccess && l >= 2) e = launch_exp_finite(u, in->u[l - 1], in->u[l - 2], in->W, N, ctx->stream);
+    if (e == cudaSuccess) e = launch_set_boundary(u, N, in->g1, stride, ctx->stream);
+    bnote(b, l >= 2 ? 4 : 2);
+    if (e != cudaSuccess) return bcuda(b, e, "level setup");
+    if (l <= 1) {
+        const int st = dsolve_run(ctx, N, in->bc, in->fh, u);
+        bnote(b, 1);
+        if (st) return bfail(b, st, ctx->last_error);
+    }
+    return EXCMG_OK;
+}
+
+int finish(excmg_batch* b, Instance* in) {
+    excmg_ctx* ctx = b->ctx;
+    const int lf = in->nl - 1;
+    cudaError_t e = launch_exp_true(in->u_out, in->u[lf], in->u[lf - 1], in->n, ctx->stream);
+    bnote(b, 1);
+    return bcuda(b, e, "EXP_true");
+}
+
+bool grow(excmg_batch* b, double** buf, size_t* cap, size_t need) {
+    if (need <= *cap) return true;
+    cudaFree(*buf);
+    *cap = need * 2;
+    if (cudaMalloc(buf, *cap * sizeof(double)) != cudaSuccess) {
+        cudaGetLastError();
+        *cap = 0;
+        *buf = nullptr;
+        return false;
+    }
+    return true;
+}
+
+// Tile / chunk geometry of one instance's current level.
+template <typename T>
+BatchInst<T> geometry(Instance* in, int slot, int* units, int* chunks) {
+    const int N = in->nc << in->level, m = N - 1;
+    BatchInst<T> t{};
+    t.n = N;
+    t.sigma = in->bc == 1 ? 1 : -1;
+    t.gx = (m + S_TX - 1) / S_TX;
+    t.gy = (m + S_OY - 1) / S_OY;
+    t.kz_per = m < 8 ? m : 8;
+    t.nunits = t.gx * t.gy * ((m + t.kz_per - 1) / t.kz_per);
+    t.unit_begin = *units;
+    t.len = (long long)node_count(N);
+    t.nchunks = (int)((t.len + kChunk - 1) / kChunk);
+    t.chunk_begin = *chunks;
+    t.slot = slot;
+    *units += t.nunits;
+    *chunks += t.nchunks;
+    return t;
+}
+
+// One cooperative launch of up to `iters` Bi-CG iterations for the listed
+// instances of one value type.
+template <typename T>
+int run_batched(excmg_batch* b, const std::vector<Instance*>& list, BatchInst<T>* d_inst) {
+    excmg_ctx* ctx = b->ctx;
+    cudaStream_t s = ctx->stream;
+    std::vector<BatchInst<T>> tab;
+    std::vector<int> ub, cb;
+    int units = 0, chunks = 0, active = 0;
+    for (Instance* in : list) {
+        const int slot = slot_of(b, in);
+        if (b->h_states[slot].done) continue;
+        BatchInst<T> t = geometry<T>(in, slot, &units, &chunks);
+        if (sizeof(T) == sizeof(double)) {
+            t.x = (T*)in->u[in->level];
+            t.r = (T*)in->res;
+            t.rs = (T*)in->rs64;
+            t.p = (T*)in->p64;
+            t.ps = (T*)in->ps64;
+            t.q = (T*)in->q64;
+            t.qs = (T*)in->qs64;
+        } else {
+            t.x = (T*)in->e;
+            t.r = (T*)in->r;
+            t.rs = (T*)in->rs;
+            t.p = (T*)in->p;
+            t.ps = (T*)in->ps;
+            t.q = (T*)in->q;
+            t.qs = (T*)in->qs;
+        }
+        ub.push_back(t.unit_begin);
+        cb.push_back(t.chunk_begin);
+        tab.push_back(t);
+        ++active;
+    }
+    if (active == 0) return EXCMG_OK;
+    if (!grow(b, &b->d_unit_part, &b->unit_cap, (size_t)units) ||
+        !grow(b, &b->d_chunk_part, &b->chunk_cap, 2 * (size_t)chunks))
+        return bfail(b, EXCMG_ERR_OOM, "batch partials");
+    const int ninst = (int)tab.size();
+    *b->h_active = active;
+    cudaError_t e = cudaMemcpyAsync(d_inst, tab.data(), tab.size() * sizeof(BatchInst<T>), cudaMemcpyHostToDevice, s);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(b->d_unit_begin, ub.data(), ub.size() * sizeof(int), cudaMemcpyHostToDevice, s);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(b->d_chunk_begin, cb.data(), cb.size() * sizeof(int), cudaMemcpyHostToDevice, s);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(b->d_active, b->h_active, sizeof(int), cudaMemcpyHostToDevice, s);
+    if (e == cudaSuccess) e = cudaMemsetAsync(b->d_barrier, 0, 4 * sizeof(unsigned int), s);
+    if (e != cudaSuccess) return bcuda(b, e, "batch table upload");
+    int iters = b->inner_chunk;
+    const int G = batch_resident_ctas<T>();
+    const BatchInst<T>* di = d_inst;
+    const int* d_ub = b->d_unit_begin;
+    const int* d_cb = b->d_chunk_begin;
+    double* up = b->d_unit_part;
+    double* cp = b->d_chunk_part;
+    BatchState* sts = b->d_states;
+    int* act = b->d_active;
+    BatchBarrier gb{b->d_barrier, b->d_barrier + 1, (int*)(b->d_barrier + 2)};
+    void* args[] = {(void*)&di, (void*)&d_ub, (void*)&d_cb, (void*)&ninst, (void*)&units, (void*)&chunks,
+                    (void*)&up, (void*)&cp, (void*)&sts, (void*)&iters, (void*)&act, (void*)&gb};
+    e = cudaLaunchCooperativeKernel((const void*)batch_bicg_kernel<T>, dim3(G), dim3(S_TX, S_TY, 1), args, 0, s);
+    bnote(b, 1);
+    if (e != cudaSuccess) return bcuda(b, e, "batched Bi-CG launch");
+    e = cudaMemcpyAsync(b->h_active, b->d_active, sizeof(int), cudaMemcpyDeviceToHost, s);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+    if (e != cudaSuccess) return bcuda(b, e, "batched Bi-CG");
+    if (*b->h_active < 0) return bfail(b, EXCMG_ERR_TIMEOUT, "grid barrier of the batched Bi-CG gave up");
+    return EXCMG_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+int excmg_batch_create(excmg_ctx* ctx, size_t hbm_budget_bytes, int max_instances, excmg_batch** out) {
+    if (!ctx || !out || max_instances < 1 || max_instances > kBatchMaxInst) return EXCMG_ERR_ARG;
+    *out = nullptr;
+    excmg_batch* b = new (std::nothrow) excmg_batch();
+    if (!b) return EXCMG_ERR_OOM;
+    b->ctx = ctx;
+    b->budget = hbm_budget_bytes;
+    b->max_instances = max_instances;
+    const size_t mi = (size_t)max_instances;
+    bool ok = cudaMalloc(&b->d_inst32, mi * sizeof(BatchInst<float>)) == cudaSuccess &&
+              cudaMalloc(&b->d_inst64, mi * sizeof(BatchInst<double>)) == cudaSuccess &&
+              cudaMalloc(&b->d_unit_begin, mi * sizeof(int)) == cudaSuccess &&
+              cudaMalloc(&b->d_chunk_begin, mi * sizeof(int)) == cudaSuccess &&
+              cudaMalloc(&b->d_states, mi * sizeof(BatchState)) == cudaSuccess &&
+              cudaMallocHost(&b->h_states, mi * sizeof(BatchState)) == cudaSuccess &&
+              cudaMalloc(&b->d_active, sizeof(int)) == cudaSuccess &&
+              cudaMallocHost(&b->h_active, sizeof(int)) == cudaSuccess &&
+              cudaMalloc(&b->d_barrier, 4 * sizeof(unsigned int)) == cudaSuccess &&
+              cudaMalloc(&b->d_norms, mi * sizeof(double)) == cudaSuccess &&
+              cudaMallocHost(&b->h_norms, mi * sizeof(double)) == cudaSuccess &&
+              cudaMemset(b->d_states, 0, mi * sizeof(BatchState)) == cudaSuccess;
+    if (!ok) {
+        cudaGetLastError();
+        excmg_batch_destroy(b);
+        return EXCMG_ERR_OOM;
+    }
+    memset(b->h_states, 0, mi * sizeof(BatchState));
+    *out = b;
+    return EXCMG_OK;
+}
+
+int excmg_batch_destroy(excmg_batch* b) {
+    if (!b) return EXCMG_ERR_ARG;
+    if (b->ctx) {
+        if (b->ctx->stream) cudaStreamSynchronize(b->ctx->stream);
+        else cudaDeviceSynchronize();
+    }
+    for (Instance* in : b->live) {
+        free_instance(b, in);
+        delete in;
+    }
+    for (Instance* in : b->finished) {
+        free_instance(b, in);
+        delete in;
+    }
+    cudaFree(b->d_inst32);
+    cudaFree(b->d_inst64);
+    cudaFree(b->d_unit_begin);
+    cudaFree(b->d_chunk_begin);
+    cudaFree(b->d_states);
+    cudaFreeHost(b->h_states);
+    cudaFree(b->d_unit_part);
+    cudaFree(b->d_chunk_part);
+    cudaFree(b->d_active);
+    cudaFreeHost(b->h_active);
+    cudaFree(b->d_barrier);
+    cudaFree(b->d_norms);
+    cudaFreeHost(b->h_norms);
+    delete b;
+    return EXCMG_OK;
+}
+
+const char* excmg_batch_last_error(const excmg_batch* b) { return b ? b->last_error.c_str() : ""; }
+
+size_t excmg_batch_bytes(const excmg_batch* b) { return b ? b->bytes : 0; }
+
+size_t excmg_batch_instance_bytes(int n_finest, int n_coarsest, int precision) {
+    if (n_coarsest < 4 || n_finest < n_coarsest) return 0;
+    return instance_bytes(n_finest, n_coarsest, precision);
+}
+
+int excmg_batch_submit(excmg_batch* b, int n_finest, int n_coarsest, int bc_kind, const double* f, const double* g1,
+                       const double* g2, const excmg_params* params, double* u_out, int* id_out) {
+    if (!b || !f || !g1 || !g2 || !params || !u_out || !id_out) return EXCMG_ERR_ARG;
+    if (bc_kind != 1 && bc_kind != 2) return bfail(b, EXCMG_ERR_ARG, "bc_kind must be 1 or 2");
+    if (n_coarsest < 4 || 2 * n_coarsest > 16)
+        return bfail(b, EXCMG_ERR_ARG, "n_coarsest must be 4..8 (DSOLVE grids up to 16 intervals)");
+    int steps = 0, n = n_coarsest;
+    while (n < n_finest) {
+        n *= 2;
+        ++steps;
+    }
+    if (n != n_finest || steps < 2) return bfail(b, EXCMG_ERR_ARG, "n_finest must be n_coarsest * 2^(L+1), L >= 1");
+    if (params->precision != EXCMG_PRECISION_FP64 && params->precision != EXCMG_PRECISION_MIXED)
+        return bfail(b, EXCMG_ERR_ARG, "unknown precision");
+    if (!(params->tol > 0.0) || params->max_iter < 1 || params->max_total < 1 ||
+        (params->precision == EXCMG_PRECISION_MIXED && !(params->inner_tol > 0.0 && params->inner_tol < 1.0)))
+        return bfail(b, EXCMG_ERR_ARG, "bad parameters");
+    if ((int)b->live.size() >= b->max_instances) return bfail(b, EXCMG_ERR_BUDGET, "all instance slots are busy");
+    const int prec = params->precision;
+    const size_t need = instance_bytes(n_finest, n_coarsest, prec);
+    if (b->budget && b->bytes + need > b->budget)
+        return bfail(b, EXCMG_ERR_BUDGET, "device-memory budget of the batch is full");
+    Instance* in = new (std::nothrow) Instance();
+    if (!in) return EXCMG_ERR_OOM;
+    if (cudaMalloc(&in->block, need) != cudaSuccess) {
+        cudaGetLastError();
+        delete in;
+        return bfail(b, EXCMG_ERR_OOM, "cudaMalloc of an instance failed");
+    }
+    // boundary entries of every work vector must read zero (the operator
+    // writes interior entries only)
+    if (cudaMemsetAsync(in->block, 0, need, b->ctx->stream) != cudaSuccess) {
+        cudaGetLastError();
+        cudaFree(in->block);
+        delete in;
+        return bfail(b, EXCMG_ERR_CUDA, "clearing an instance failed");
+    }
+    in->bytes = need;
+    b->bytes += need;
+    in->id = b->next_id++;
+    in->n = n_finest;
+    in->nc = n_coarsest;
+    in->bc = bc_kind;
+    in->nl = steps + 1;
+    in->L = in->nl - 2;
+    in->prec = prec;
+    in->f = f;
+    in->g1 = g1;
+    in->g2 = g2;
+    in->u_out = u_out;
+    in->tol = params->tol;
+    in->inner_tol = params->inner_tol;
+    in->tol_mode = params->tol_mode;
+    in->max_iter = params->max_iter;
+    in->max_total = params->max_total;
+    char* c = (char*)in->block;
+    auto take = [&](size_t bytes) {
+        char* r = c;
+        c += align256(bytes);
+        return (void*)r;
+    };
+    for (int l = 0; l < in->nl; ++l) in->u.push_back((double*)take(node_count(n_coarsest << l) * sizeof(double)));
+    const size_t n64 = node_count(n_finest) * sizeof(double), n32 = node_count(n_finest) * sizeof(float);
+    in->fh = (double*)take(n64);
+    in->res = (double*)take(n64);
+    in->W = (double*)take(node_count(n_finest / 2) * sizeof(double));
+    if (prec == EXCMG_PRECISION_FP64) {
+        in->rs64 = (double*)take(n64);
+        in->p64 = (double*)take(n64);
+        in->ps64 = (double*)take(n64);
+        in->q64 = (double*)take(n64);
+        in->qs64 = (double*)take(n64);
+    } else {
+        in->r32 = (float*)take(n32);
+        in->e = (float*)take(n32);
+        in->r = (float*)take(n32);
+        in->rs = (float*)take(n32);
+        in->p = (float*)take(n32);
+        in->ps = (float*)take(n32);
+        in->q = (float*)take(n32);
+        in->qs = (float*)take(n32);
+    }
+    in->stats.levels = in->nl;
+    in->t_submit = now_s();
+    b->live.push_back(in);
+    const int slot = (int)b->live.size() - 1;
+    b->h_states[slot] = BatchState{};
+    b->h_states[slot].done = 1;   // no Bi-CG call yet
+    *id_out = in->id;
+    return EXCMG_OK;
+}
+
+// Advance every live instance: all pending per-instance steps, then one
+// batched launch of Bi-CG iterations per value type for the instances in
+// that phase.  *n_live receives the number of instances still running.
+int excmg_batch_step(excmg_batch* b, int* n_live) {
+    if (!b) return EXCMG_ERR_ARG;
+    excmg_ctx* ctx = b->ctx;
+    cudaStream_t s = ctx->stream;
+    int st = EXCMG_OK;
+    // 1. setup phases (the direct-solve levels run straight through)
+    for (Instance* in : b->live) {
+        while (in->phase == kSetup) {
+            if ((st = setup_level(b, in))) {
+                in->phase = kFailed;
+                in->status = st;
+                break;
+            }
+            if (in->level <= 1) {
+                in->stats.n[in->level] = in->nc << in->level;
+                ++in->level;
+                continue;
+            }
+            in->phase = kResidual;
+            in->iters = in->outer = in->bad = in->stag = 0;
+            in->rel = in->prev = 0.0;
+            in->fnorm = -1.0;   // formed with the first residual
+        }
+    }
+    // 2. FP64 true residuals (Alg. 1, line 7) and the decisions they drive
+    std::vector<Instance*> res;
+    for (Instance* in : b->live)
+        if (in->phase == kResidual) res.push_back(in);
+    bool states_dirty = false;
+    if (!res.empty()) {
+        std::vector<std::pair<Instance*, const double*>> need_f;
+        for (Instance* in : res)
+            if (in->fnorm < 0.0) need_f.push_back({in, in->fh});
+        if ((st = norms(b, need_f))) return st;
+        for (size_t k = 0; k < need_f.size(); ++k) need_f[k].first->fnorm = std::sqrt(b->h_norms[k]);
+        std::vector<std::pair<Instance*, const double*>> rw;
+        for (Instance* in : res) {
+            const int N = in->nc << in->level;
+            cudaError_t e = cudaMemsetAsync(in->res, 0, node_count(N) * sizeof(double), s);
+            if (e == cudaSuccess)
+                e = launch_stencil(in->u[in->level], in->res, in->fh, N, in->bc, false, nullptr, s, kStencilExact);
+            bnote(b, 1);
+            if (e != cudaSuccess) return bcuda(b, e, "batch residual");
+            rw.push_back({in, in->res});
+        }
+        if ((st = norms(b, rw))) return st;
+        for (size_t k = 0; k < rw.size(); ++k) {
+            Instance* in = rw[k].first;
+            const double rn = std::sqrt(b->h_norms[k]);
+            const int l = in->level, N = in->nc << l;
+            in->prev = in->rel;
+            in->rel = in->fnorm > 0.0 ? rn / in->fnorm : 0.0;
+            if (!std::isfinite(in->rel)) {
+                in->phase = kFailed;
+                in->status = EXCMG_ERR_NAN;
+                continue;
+            }
+            bool level_done = false;
+            if (in->outer > 0) {
+                // FP64: the rule of the single solver (two calls without halving
+                // the residual); mixed: two steps that remove less than a tenth
+                const double keep = in->prec == EXCMG_PRECISION_FP64 ? 0.5 : 0.9;
+                if (in->rel > keep * in->prev) {
+                    if (++in->bad >= 2) {
+                        in->stag = 1;
+                        level_done = true;
+                    }
+                } else {
+                    in->bad = 0;
+                }
+            }
+            if (in->rel <= level_eps(in, l) || in->iters >= in->max_total || rn == 0.0) level_done = true;
+            if (level_done) {
+                in->stats.n[l] = N;
+                in->stats.iters[l] = in->iters;
+                in->stats.calls[l] = in->outer;
+                in->stats.stagnated[l] = in->stag;
+                in->stats.relres[l] = in->rel;
+                if (l + 1 < in->nl) {
+                    ++in->level;
+                    in->phase = kSetup;
+                } else {
+                    in->phase = kFinal;
+                }
+                continue;
+            }
+            const int slot = slot_of(b, in);
+            int cap = in->max_total - in->iters;
+            if (cap > in->max_iter) cap = in->max_iter;
+            cudaError_t e = cudaSuccess;
+            if (in->prec == EXCMG_PRECISION_FP64) {
+                // a Bi-CG call of Alg. 1's WHILE loop: x = u, r_0 = the true
+                // residual just formed, r*_0 = p_0 = p*_0 = r_0,
+                // rho_0 = (r_0, r_0); stop at ||r|| <= eps ||f_h||
+                const size_t bytes = node_count(N) * sizeof(double);
+                e = cudaMemcpyAsync(in->rs64, in->res, bytes, cudaMemcpyDeviceToDevice, s);
+                if (e == cudaSuccess) e = cudaMemcpyAsync(in->p64, in->res, bytes, cudaMemcpyDeviceToDevice, s);
+                if (e == cudaSuccess) e = cudaMemcpyAsync(in->ps64, in->res, bytes, cudaMemcpyDeviceToDevice, s);
+                BatchState& hs = b->h_states[slot];
+                hs = BatchState{};
+                hs.rho = b->h_norms[k];   // (r_0, r_0) exactly as summed
+                hs.rr = b->h_norms[k];
+                hs.tol = level_eps(in, l) * in->fnorm;
+                hs.max_iter = cap;
+                hs.done = 0;
+                hs.status = kRunning;
+                states_dirty = true;
+            } else {
+                // FP32 correction solve on A e = r / ||r||
+                in->scale = rn;
+                batch_init32_kernel<<<kVecBlocks, kVecThreads, 0, s>>>(in->res, 1.0 / rn, in->r32, in->e, in->rs,
+                                                                       in->p, in->ps, node_count(N), ctx->partials,
+                                                                       ctx->ticket, b->d_states + slot,
+                                                                       in->inner_tol, cap);
+                bnote(b, 1);
+                e = cudaGetLastError();
+                if (e == cudaSuccess)
+                    e = cudaMemcpyAsync(in->r, in->r32, node_count(N) * sizeof(float), cudaMemcpyDeviceToDevice, s);
+            }
+            if (e != cudaSuccess) return bcuda(b, e, "Bi-CG call setup");
+            in->phase = kInner;
+        }
+    }
+    // FP64 states were prepared on the host; FP32 ones by their init kernels:
+    // upload the former, then read everything back once
+    if (states_dirty) {
+        for (Instance* in : b->live)
+            if (in->phase == kInner && in->prec == EXCMG_PRECISION_FP64 && b->h_states[slot_of(b, in)].iter == 0) {
+                const int slot = slot_of(b, in);
+                cudaError_t e = cudaMemcpyAsync(b->d_states + slot, b->h_states + slot, sizeof(BatchState),
+                                                cudaMemcpyHostToDevice, s);
+                if (e != cudaSuccess) return bcuda(b, e, "state upload");
+            }
+    }
+    std::vector<Instance*> inner32, inner64;
+    for (Instance* in : b->live)
+        if (in->phase == kInner) (in->prec == EXCMG_PRECISION_FP64 ? inner64 : inner32).push_back(in);
+    if (!inner32.empty() || !inner64.empty()) {
+        cudaError_t e = cudaMemcpyAsync(b->h_states, b->d_states, b->live.size() * sizeof(BatchState),
+                                        cudaMemcpyDeviceToHost, s);
+        if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+        if (e != cudaSuccess) return bcuda(b, e, "batch state read");
+        // 3. one batched launch per value type
+        if ((st = run_batched<double>(b, inner64, b->d_inst64))) return st;
+        if ((st = run_batched<float>(b, inner32, b->d_inst32))) return st;
+        e = cudaMemcpyAsync(b->h_states, b->d_states, b->live.size() * sizeof(BatchState), cudaMemcpyDeviceToHost, s);
+        if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+        if (e != cudaSuccess) return bcuda(b, e, "batch state read");
+        // 4. finished Bi-CG calls: FP64 goes back to the true-residual test;
+        // mixed applies u += ||r|| e in FP64 first
+        for (Instance* in : b->live) {
+            if (in->phase != kInner) continue;
+            const BatchState& hs = b->h_states[slot_of(b, in)];
+            if (!hs.done) continue;
+            if (hs.status == kBreakdown) {
+                in->phase = kFailed;
+                in->status = EXCMG_ERR_BREAKDOWN;
+                continue;
+            }
+            in->iters += hs.iter;
+            ++in->outer;
+            if (in->prec == EXCMG_PRECISION_MIXED) {
+                const int N = in->nc << in->level;
+                batch_correct_kernel<<<kVecBlocks, kVecThreads, 0, s>>>(in->u[in->level], in->e, node_count(N),
+                                                                        in->scale);
+                bnote(b, 1);
+                if ((e = cudaGetLastError()) != cudaSuccess) return bcuda(b, e, "batch correction");
+            }
+            in->phase = kResidual;
+        }
+    }
+    // 5. finals
+    bool any_final = false;
+    for (Instance* in : b->live)
+        if (in->phase == kFinal) {
+            if ((st = finish(b, in))) return st;
+            any_final = true;
+        }
+    if (any_final) {
+        cudaError_t e = cudaStreamSynchronize(s);
+        if (e != cudaSuccess) return bcuda(b, e, "batch finals");
+    }
+    const double t = now_s();
+    std::vector<Instance*> keep;
+    std::vector<BatchState> hs;
+    for (size_t k = 0; k < b->live.size(); ++k) {
+        Instance* in = b->live[k];
+        if (in->phase == kFinal || in->phase == kFailed) {
+            if (in->phase == kFinal) in->phase = kDone;
+            in->t_done = t;
+            free_instance(b, in);
+            b->finished.push_back(in);
+        } else {
+            keep.push_back(in);
+            hs.push_back(b->h_states[k]);
+        }
+    }
+    // slots are positions in `live`: compact the device states with them
+    if (keep.size() != b->live.size()) {
+        b->live = keep;
+        if (!hs.empty()) {
+            memcpy(b->h_states, hs.data(), hs.size() * sizeof(BatchState));
+            cudaError_t e = cudaMemcpyAsync(b->d_states, b->h_states, hs.size() * sizeof(BatchState),
+                                            cudaMemcpyHostToDevice, s);
+            if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+            if (e != cudaSuccess) return bcuda(b, e, "batch state compaction");
+        }
+    }
+    if (n_live) *n_live = (int)b->live.size();
+    return EXCMG_OK;
+}
+
+// Status of instance `id`: *done = 1 when finished (status in *status),
+// stats (may be NULL) per level, *latency_s the time from submit to finish.
+int excmg_batch_query(excmg_batch* b, int id, int* done, int* status, excmg_stats* stats, double* latency_s) {
+    if (!b || !done) return EXCMG_ERR_ARG;
+    for (Instance* in : b->finished)
+        if (in->id == id) {
+            *done = 1;
+            if (status) *status = in->phase == kDone ? EXCMG_OK : in->status;
+            if (stats) *stats = in->stats;
+            if (latency_s) *latency_s = in->t_done - in->t_submit;
+            return EXCMG_OK;
+        }
+    for (Instance* in : b->live)
+        if (in->id == id) {
+            *done = 0;
+            if (status) *status = EXCMG_OK;
+            return EXCMG_OK;
+        }
+    return bfail(b, EXCMG_ERR_ARG, "unknown instance id");
+}
+
+long long excmg_batch_launches(const excmg_batch* b) { return b ? b->launches : 0; }
+
+}  // extern "C"

@@ -36,7 +36,8 @@ int true_residual_norm(excmg_ctx* ctx, int n, int bc_kind, const double* b, cons
 }
 
 int bicg_run(excmg_ctx* ctx, int n, int bc_kind, const double* b, double* x, double tol,
-             double bnorm, int max_iter, int check_every, int* iters_out, double* relres_out) {
+             double bnorm, int max_iter, int check_every, int* iters_out, double* relres_out,
+             const double* shadow) {
     const size_t len = node_count(n);
     const size_t bytes = len * sizeof(double);
     int st = EXCMG_OK;
@@ -63,17 +64,38 @@ int bicg_run(excmg_ctx* ctx, int n, int bc_kind, const double* b, double* x, dou
     if (e == cudaSuccess) e = cudaMemsetAsync(qs, 0, bytes, s);
     // r_0 = b - A x_0; r*_0 = p_0 = p*_0 = r_0; rho_0
     if (e == cudaSuccess) e = launch_stencil(x, r, b, n, bc_kind, false, nullptr, s, ctx->stencil_variant);
-    if (e == cudaSuccess) e = launch_bicg_init(r, rs, p, ps, len, ctx->partials, ctx->state, s);
+    if (e == cudaSuccess) e = launch_bicg_init(r, shadow, rs, p, ps, len, ctx->partials, ctx->state, s);
+    // a caller's shadow may carry values on boundary nodes: the work vectors
+    // keep zeros there
+    if (e == cudaSuccess && shadow) e = launch_zero_boundary(rs, n, s);
+    if (e == cudaSuccess && shadow) e = launch_zero_boundary(ps, n, s);
     if (e != cudaSuccess) return ctx_cuda(ctx, e, "Bi-CG setup");
 
     const int* done = &ctx->state->done;
     // the integer operator has a fused two-field kernel; the FP64 one runs
     // as two applications and a separate inner product
     const bool fused = ctx->stencil_variant == kStencilExact && stencil_cta_count(n) <= kMaxPartials;
+    // small grids run whole iterations in one cooperative launch
+    const bool persistent = fused && n <= kPersistentMaxN;
+    if (persistent) {
+        for (;;) {
+            e = cudaMemcpyAsync(ctx->host_state, ctx->state, sizeof(BicgState), cudaMemcpyDeviceToHost, s);
+            if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+            if (e != cudaSuccess) return ctx_cuda(ctx, e, "Bi-CG state read");
+            if (ctx->host_state->done) break;
+            int chunk = 256;
+            const int left = max_iter - ctx->host_state->iter;
+            if (chunk > left) chunk = left;
+            e = launch_bicg_persistent(x, r, rs, p, ps, q, qs, n, bc_kind, chunk, ctx->partials, ctx->state,
+                                       ctx->barrier, s);
+            note_launches(1);
+            if (e != cudaSuccess) return ctx_cuda(ctx, e, "cooperative Bi-CG launch");
+        }
+    }
     note_launches(2);   // residual stencil + init (the memsets are not kernels)
     int batch = 0;
     int iter_before = 0;
-    for (;;) {
+    for (; !persistent;) {
         e = cudaMemcpyAsync(ctx->host_state, ctx->state, sizeof(BicgState), cudaMemcpyDeviceToHost, s);
         if (e == cudaSuccess) e = cudaStreamSynchronize(s);
         if (e != cudaSuccess) return ctx_cuda(ctx, e, "Bi-CG state read");
@@ -131,6 +153,7 @@ int bicg_run(excmg_ctx* ctx, int n, int bc_kind, const double* b, double* x, dou
     if (relres_out) *relres_out = bnorm > 0.0 ? rn / bnorm : rn;
     if (!std::isfinite(h.rr)) return ctx_fail(ctx, EXCMG_ERR_NAN, "Bi-CG residual is not finite");
     if (h.status == kBreakdown) return ctx_fail(ctx, EXCMG_ERR_BREAKDOWN, "Bi-CG breakdown");
+    if (h.status == kTimeout) return ctx_fail(ctx, EXCMG_ERR_TIMEOUT, "grid barrier of the cooperative Bi-CG gave up");
     if (h.status == kCapped) return EXCMG_ERR_NOCONV;
     return EXCMG_OK;
 }

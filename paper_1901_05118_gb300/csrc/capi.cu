@@ -98,6 +98,8 @@ int excmg_ctx_create(void* cuda_stream, size_t hbm_budget_bytes, excmg_ctx** out
               cudaMalloc(&c->ticket, sizeof(unsigned int)) == cudaSuccess &&
               cudaMalloc(&c->scalar, 8 * sizeof(double)) == cudaSuccess &&
               cudaMalloc(&c->state, sizeof(BicgState)) == cudaSuccess &&
+              cudaMalloc(&c->barrier, 4 * sizeof(unsigned int)) == cudaSuccess &&
+              cudaMemset(c->barrier, 0, 4 * sizeof(unsigned int)) == cudaSuccess &&
               cudaMallocHost(&c->host_state, sizeof(BicgState)) == cudaSuccess &&
               cudaMallocHost(&c->host_scalar, 8 * sizeof(double)) == cudaSuccess &&
               cudaMemset(c->ticket, 0, sizeof(unsigned int)) == cudaSuccess &&
@@ -123,6 +125,7 @@ int excmg_ctx_destroy(excmg_ctx* c) {
     if (c->ticket) cudaFree(c->ticket);
     if (c->scalar) cudaFree(c->scalar);
     if (c->state) cudaFree(c->state);
+    if (c->barrier) cudaFree(c->barrier);
     if (c->host_state) cudaFreeHost(c->host_state);
     if (c->host_scalar) cudaFreeHost(c->host_scalar);
     for (cudaEvent_t e : c->prof_events) cudaEventDestroy(e);
@@ -204,6 +207,18 @@ int bicg_solve(const excmg_level* level, const double* b, double* x_inout, doubl
     if (st) return st;
     return bicg_run(ctx, level->n, level->bc_kind, b, x_inout, tol, bnorm, max_iter, 16, iters_out,
                     relres_out);
+}
+
+int bicg_solve_ex(const excmg_level* level, const double* b, double* x_inout, const double* shadow_r0, double tol,
+                  int max_iter, int* iters_out, double* relres_out) {
+    if (!level || !b || !x_inout) return EXCMG_ERR_ARG;
+    excmg_ctx* ctx = level->ctx;
+    if (!(tol >= 0.0) || max_iter < 0) return ctx_fail(ctx, EXCMG_ERR_ARG, "bicg_solve_ex: bad tol / max_iter");
+    double bnorm = 0.0;
+    int st = interior_norm(ctx, level->n, b, &bnorm);
+    if (st) return st;
+    return bicg_run(ctx, level->n, level->bc_kind, b, x_inout, tol, bnorm, max_iter, 16, iters_out, relres_out,
+                    shadow_r0);
 }
 
 int extrapolate_interpolate_ex(excmg_ctx* ctx, int n_fine, const double* u_2h, const double* u_4h,

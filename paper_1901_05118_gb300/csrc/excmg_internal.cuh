@@ -43,7 +43,7 @@ struct BicgState {
     unsigned int ticket;   // last-block counter of the reductions
     int pad1[3];
 };
-enum { kRunning = 0, kConverged = 1, kCapped = 2, kBreakdown = 3 };
+enum { kRunning = 0, kConverged = 1, kCapped = 2, kBreakdown = 3, kTimeout = 4 };
 
 // ------------------------------------------------------------- kernels
 // Stencil (eq. (method1) + reflections): y = A u, or y = b - A u when b is
@@ -59,12 +59,18 @@ cudaError_t launch_zero_boundary(double* y, int n, cudaStream_t s);
 cudaError_t launch_bicg_stencil_pair(const double* p, double* q, const double* ps, double* qs, int n,
                                      int bc_kind, double* partials, BicgState* st, cudaStream_t s);
 int stencil_cta_count(int n);
+// Small grids: whole Bi-CG iterations (up to `iters`) in one cooperative
+// launch with bounded grid barriers; barrier_words: 3 device words.
+constexpr int kPersistentMaxN = 64;
+cudaError_t launch_bicg_persistent(double* x, double* r, double* rs, double* p, double* ps, double* q, double* qs,
+                                   int n, int bc_kind, int iters, double* partials, BicgState* st,
+                                   unsigned int* barrier_words, cudaStream_t s);
 
 // Vectors (flat over all (n+1)^3 entries; boundary entries of the Bi-CG
 // vectors are zero, so flat sums equal sums over the unknowns).
 cudaError_t launch_dot(const double* a, const double* b, size_t len, double* partials,
                        unsigned int* ticket, double* out, cudaStream_t s);
-cudaError_t launch_bicg_init(const double* r, double* rs, double* p, double* ps, size_t len,
+cudaError_t launch_bicg_init(const double* r, const double* shadow, double* rs, double* p, double* ps, size_t len,
                              double* partials, BicgState* st, cudaStream_t s);
 cudaError_t launch_bicg_sigma(const double* ps, const double* q, size_t len, double* partials,
                               BicgState* st, cudaStream_t s);
@@ -117,6 +123,7 @@ struct excmg_ctx {
     unsigned int* ticket = nullptr;
     double* scalar = nullptr;                 // one-off reduction results (8 doubles)
     excmg::BicgState* state = nullptr;        // device
+    unsigned int* barrier = nullptr;          // device words of the cooperative solver's grid barrier
     excmg::BicgState* host_state = nullptr;   // pinned host mirror
     double* host_scalar = nullptr;            // pinned host mirror of `scalar`
     int stencil_variant = excmg::kStencilExact;
@@ -141,7 +148,8 @@ int ctx_cuda(excmg_ctx* ctx, cudaError_t err, const char* what);
 double* ctx_buffer(excmg_ctx* ctx, const char* name, size_t bytes, int* status);
 // Bi-CG driver (bicg.cu): iterates on the context's stream.
 int bicg_run(excmg_ctx* ctx, int n, int bc_kind, const double* b, double* x, double tol,
-             double bnorm, int max_iter, int check_every, int* iters_out, double* relres_out);
+             double bnorm, int max_iter, int check_every, int* iters_out, double* relres_out,
+             const double* shadow = nullptr);
 // ||b - A x||_2 over the unknowns, via the context's workspace (result on host).
 int true_residual_norm(excmg_ctx* ctx, int n, int bc_kind, const double* b, const double* x,
                        double* out);

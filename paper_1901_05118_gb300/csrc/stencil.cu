@@ -22,6 +22,7 @@
 // diagonal, so this is the same arithmetic; the flag is kept so that A^T is
 // applied as Alg. 2 asks (its shadow recurrence multiplies by A^T).
 #include "excmg_internal.cuh"
+#include "march_fx.cuh"
 #include "reduce.cuh"
 
 namespace excmg {
@@ -92,239 +93,14 @@ stencil_f64_kernel(const double* __restrict__ u, double* __restrict__ y, const d
     }
 }
 
-// ---------------------------------------------------------------------------
-// Exact-integer variant.  GB300 issues FP64 arithmetic at a small fraction of
-// its integer rate, while the 25 weights are small integers (|w| summing to
-// 144).  Each input plane of the CTA is mapped to 64-bit integers on one
-// power-of-two scale: a double with biased exponent e and 53-bit significand
-// m becomes m >> (E - e), E being the largest exponent the CTA has met so
-// far; all sums are then exact integer additions (144 * 2^53 < 2^61), and
-// only the final value is rounded once back to double.  The result differs
-// from the exact weighted sum by less than 144 units of 2^(E-1075) plus the
-// final rounding, i.e. at most about 3.2e-14 of the largest input magnitude
-// the CTA reads (FP64 summation of the 25 terms carries errors of the same
-// order).  When E grows, the running
-// accumulators are shifted to the new scale.  A plane holding a non-finite
-// value turns the CTA's remaining outputs into NaN.
-__device__ __forceinline__ long long to_fixed(double v, int E) {
-    const unsigned hi = (unsigned)__double2hiint(v);
-    const unsigned lo = (unsigned)__double2loint(v);
-    const int e = (int)((hi >> 20) & 0x7FFu);
-    unsigned mh = hi & 0xFFFFFu;
-    int ee = 1;
-    if (e) { mh |= 0x100000u; ee = e; }
-    unsigned long long m = ((unsigned long long)mh << 32) | lo;
-    const int d = E - ee;
-    m = d < 64 ? (m >> d) : 0ull;
-    const long long r = (long long)m;
-    return ((int)hi < 0) ? -r : r;
-}
-
-// Y * 2^(E - 1075), rounded to nearest even; valid for 53 <= E <= 2037 and
-// |Y| < 2^62.
-__device__ __forceinline__ double from_fixed(long long Y, int E) {
-    if (Y == 0) return 0.0;
-    const unsigned long long sgn = Y < 0 ? (1ull << 63) : 0ull;
-    unsigned long long a = Y < 0 ? (unsigned long long)(-Y) : (unsigned long long)Y;
-    const int lz = __clzll((long long)a);
-    a <<= lz;
-    unsigned long long mant = a >> 11;
-    const unsigned rem = (unsigned)(a & 0x7FFull);
-    if (rem > 0x400u || (rem == 0x400u && (mant & 1ull))) mant += 1ull;
-    const unsigned long long bits = sgn + ((unsigned long long)(E + 11 - lz - 1) << 52) + mant;
-    return __longlong_as_double((long long)bits);
-}
-
-__device__ __forceinline__ int exponent_of(double v) {
-    return (int)(((unsigned)__double2hiint(v) >> 20) & 0x7FFu);
-}
-
-// Register-blocked integer kernel.  A CTA of FX_TX x FX_TY threads owns
-// FX_TX x (FX_TY * FX_RY) output columns; each thread produces FX_RY = 2
-// vertically adjacent columns, which share 9 of their 18 shared-memory reads.
-// NF fields are marched together through the same z-planes (NF = 2 applies A
-// to p and A^T to p* in one pass for Bi-CG); field f has its own running
-// scale exponent E[f].  Each thread's halo-load slots are the same on every
-// plane, so their offsets are computed once.
-//
-// The transposed operator gathers over the mirrored tap set; every tap d of
-// eq. (method1) has a partner -d of equal weight and integer sums do not
-// depend on order, so A^T u and A u come out bit for bit equal here.
-//
-// With kDot the kernel also forms the Bi-CG scalar sigma = (p*, A p) of
-// Alg. 2 (field 1's input against field 0's output) and, in the last CTA,
-// alpha = rho / sigma.
-constexpr int FX_TX = 32;
-constexpr int FX_TY = 8;
-constexpr int FX_RY = 2;
-constexpr int FX_OY = FX_TY * FX_RY;                 // output rows per CTA
-constexpr int FX_HX = FX_TX + 4;
-constexpr int FX_HY = FX_OY + 4;
-constexpr int FX_NT = FX_TX * FX_TY;
-constexpr int FX_SLOTS = (FX_HX * FX_HY + FX_NT - 1) / FX_NT;
-
-struct FxFields {
-    const double* in[2];
-    double* out[2];
-};
-
-__device__ __forceinline__ double fx_result(long long acc, int E, bool poisoned) {
-    if (poisoned) return __longlong_as_double(0x7FF8000000000000ll);
-    if (E >= 53 && E <= 2037) return from_fixed(acc, E);
-    return ldexp((double)acc, E - 1075);
-}
-
 template <int NF, bool kDot>
 __global__ void __launch_bounds__(FX_NT)
 stencil_fx_kernel(FxFields fl, const double* __restrict__ b, int n, int sigma, int kz_per_cta,
                   const int* __restrict__ skip, double* partials, BicgState* st) {
     if (skip != nullptr && *skip) return;
-    __shared__ long long tile[NF][FX_HY * FX_HX];
-    __shared__ int wmax[NF][FX_NT / 32];
-    const int np = n + 1;
-    const size_t plane = (size_t)np * np;
-    const int tx = threadIdx.x, ty = threadIdx.y, tid = ty * FX_TX + tx;
-    const int lane = tid & 31;
-    const int i0 = 1 + blockIdx.x * FX_TX, j0 = 1 + blockIdx.y * FX_OY;
     const int kz0 = 1 + blockIdx.z * kz_per_cta;
     const int kz1 = min(kz0 + kz_per_cta, n);
-
-    // halo-load slots of this thread: in-plane offset (-1: outside the
-    // interior, reads as zero) and shared-memory index (-1: no slot)
-    int soff[FX_SLOTS], sidx[FX_SLOTS];
-#pragma unroll
-    for (int r = 0; r < FX_SLOTS; ++r) {
-        const int e = tid + r * FX_NT;
-        soff[r] = -1;
-        sidx[r] = -1;
-        if (e < FX_HX * FX_HY) {
-            const int ly = e / FX_HX, lx = e - ly * FX_HX;
-            const int gi = i0 - 2 + lx, gj = j0 - 2 + ly;
-            sidx[r] = e;
-            if (gi >= 1 && gi <= n - 1 && gj >= 1 && gj <= n - 1) soff[r] = gj * np + gi;
-        }
-    }
-    const int i = i0 + tx, ja = j0 + ty * FX_RY;
-    const bool act0 = (i <= n - 1) && (ja <= n - 1);
-    const bool act1 = (i <= n - 1) && (ja + 1 <= n - 1);
-    const int cx = (i == 1) + (i == n - 1);
-    const int c0 = cx + (ja == 1) + (ja == n - 1);
-    const int c1 = cx + (ja + 1 == 1) + (ja + 1 == n - 1);
-    const int ry = ty * FX_RY + 2, rx = tx + 2;   // tile coordinates of the first output
-
-    long long acc[NF][FX_RY][5];
-    int E[NF];
-    bool poisoned[NF];
-#pragma unroll
-    for (int f = 0; f < NF; ++f) {
-#pragma unroll
-        for (int q = 0; q < FX_RY; ++q)
-#pragma unroll
-            for (int k = 0; k < 5; ++k) acc[f][q][k] = 0;
-        E[f] = 1;
-        poisoned[f] = false;
-    }
-    double dot = 0.0;
-
-    for (int zin = kz0 - 2; zin <= kz1 + 1; ++zin) {
-        const bool zok = (zin >= 1) && (zin <= n - 1);
-        const size_t zbase = zok ? (size_t)zin * plane : 0;
-        double v[NF][FX_SLOTS];
-#pragma unroll
-        for (int f = 0; f < NF; ++f) {
-            int emax = 0;
-#pragma unroll
-            for (int r = 0; r < FX_SLOTS; ++r) {
-                v[f][r] = (zok && soff[r] >= 0) ? fl.in[f][zbase + soff[r]] : 0.0;
-                emax = max(emax, exponent_of(v[f][r]));
-            }
-            emax = (int)__reduce_max_sync(0xffffffffu, (unsigned)emax);
-            if (lane == 0) wmax[f][tid >> 5] = emax;
-        }
-        __syncthreads();   // also: every thread is done reading the previous tiles
-#pragma unroll
-        for (int f = 0; f < NF; ++f) {
-            const int ep = (int)__reduce_max_sync(0xffffffffu, (unsigned)wmax[f][lane & (FX_NT / 32 - 1)]);
-            if (ep == 0x7FF) poisoned[f] = true;
-            if (ep > E[f]) {
-                const int d = ep - E[f];
-#pragma unroll
-                for (int q = 0; q < FX_RY; ++q)
-#pragma unroll
-                    for (int k = 0; k < 5; ++k) acc[f][q][k] = d >= 63 ? 0 : (acc[f][q][k] >> d);
-                E[f] = ep;
-            }
-#pragma unroll
-            for (int r = 0; r < FX_SLOTS; ++r)
-                if (sidx[r] >= 0) tile[f][sidx[r]] = to_fixed(v[f][r], E[f]);
-        }
-        __syncthreads();
-        const int cz = (zin == 1) + (zin == n - 1);
-        const int zo = zin - 2;
-        const bool zstore = zo >= kz0 && zo < kz1;
-        const size_t o0 = ((size_t)zo * np + ja) * np + i;
-#pragma unroll
-        for (int f = 0; f < NF; ++f) {
-            const long long* T = tile[f];
-            auto at = [&](int yy, int xx) { return T[yy * FX_HX + xx]; };
-            // column x: rows ry-2 .. ry+3; columns x-1, x+1: rows ry-1 .. ry+2;
-            // columns x-2, x+2: rows ry, ry+1
-            const long long cm2 = at(ry - 2, rx), cm1 = at(ry - 1, rx), c_0 = at(ry, rx),
-                            c_1 = at(ry + 1, rx), c_2 = at(ry + 2, rx), c_3 = at(ry + 3, rx);
-            const long long lm1 = at(ry - 1, rx - 1), l_0 = at(ry, rx - 1), l_1 = at(ry + 1, rx - 1),
-                            l_2 = at(ry + 2, rx - 1);
-            const long long rm1 = at(ry - 1, rx + 1), r_0 = at(ry, rx + 1), r_1 = at(ry + 1, rx + 1),
-                            r_2 = at(ry + 2, rx + 1);
-            const long long ll0 = at(ry, rx - 2), ll1 = at(ry + 1, rx - 2), rr0 = at(ry, rx + 2),
-                            rr1 = at(ry + 1, rx + 2);
-            {   // output row ja
-                const long long n4 = l_0 + r_0 + cm1 + c_1;
-                const long long f4 = ll0 + rr0 + cm2 + c_2;
-                const long long d4 = lm1 + l_1 + rm1 + r_1;
-                const long long p0 = (long long)(42 + sigma * (c0 + cz)) * c_0 - 12 * n4 + f4 + 2 * d4;
-                const long long p1 = 2 * n4 - 12 * c_0;
-                acc[f][0][0] += c_0;
-                acc[f][0][1] += p1;
-                acc[f][0][2] += p0;
-                acc[f][0][3] += p1;
-                acc[f][0][4] += c_0;
-            }
-            {   // output row ja + 1
-                const long long n4 = l_1 + r_1 + c_0 + c_2;
-                const long long f4 = ll1 + rr1 + cm1 + c_3;
-                const long long d4 = l_0 + l_2 + r_0 + r_2;
-                const long long p0 = (long long)(42 + sigma * (c1 + cz)) * c_1 - 12 * n4 + f4 + 2 * d4;
-                const long long p1 = 2 * n4 - 12 * c_1;
-                acc[f][1][0] += c_1;
-                acc[f][1][1] += p1;
-                acc[f][1][2] += p0;
-                acc[f][1][3] += p1;
-                acc[f][1][4] += c_1;
-            }
-            if (zstore) {
-                if (act0) {
-                    double val = fx_result(acc[f][0][0], E[f], poisoned[f]);
-                    if (NF == 1 && b != nullptr) val = b[o0] - val;
-                    fl.out[f][o0] = val;
-                    if (kDot && f == 0) dot += __ldg(&fl.in[1][o0]) * val;
-                }
-                if (act1) {
-                    double val = fx_result(acc[f][1][0], E[f], poisoned[f]);
-                    if (NF == 1 && b != nullptr) val = b[o0 + np] - val;
-                    fl.out[f][o0 + np] = val;
-                    if (kDot && f == 0) dot += __ldg(&fl.in[1][o0 + np]) * val;
-                }
-            }
-#pragma unroll
-            for (int q = 0; q < FX_RY; ++q) {
-                acc[f][q][0] = acc[f][q][1];
-                acc[f][q][1] = acc[f][q][2];
-                acc[f][q][2] = acc[f][q][3];
-                acc[f][q][3] = acc[f][q][4];
-                acc[f][q][4] = 0;
-            }
-        }
-    }
+    const double dot = fx_march<NF, kDot>(fl, b, n, sigma, blockIdx.x, blockIdx.y, kz0, kz1);
     if (kDot) {
         __shared__ double sh[32];
         __shared__ bool am_last;
@@ -343,6 +119,218 @@ stencil_fx_kernel(FxFields fl, const double* __restrict__ b, int n, int sigma, i
                 st->ticket = 0;
             }
         }
+    }
+}
+
+// A u at one interior node (i, j, k) with the integer arithmetic, without
+// shared memory: the node's own 25 taps are put on the scale of their
+// largest exponent and summed exactly.  Used where grids are so small that
+// a z-march would be all latency.
+__device__ __forceinline__ double fx_point(const double* __restrict__ u, int n, int sigma, int i, int j, int k) {
+    const int np = n + 1;
+    auto val = [&](int a, int b, int c) -> double {
+        if (a < 1 || a > n - 1 || b < 1 || b > n - 1 || c < 1 || c > n - 1) return 0.0;
+        return u[((size_t)c * np + b) * np + a];
+    };
+    const double ctr = val(i, j, k);
+    double ax[6], far[6], dg[12];
+    ax[0] = val(i - 1, j, k); ax[1] = val(i + 1, j, k); ax[2] = val(i, j - 1, k);
+    ax[3] = val(i, j + 1, k); ax[4] = val(i, j, k - 1); ax[5] = val(i, j, k + 1);
+    far[0] = val(i - 2, j, k); far[1] = val(i + 2, j, k); far[2] = val(i, j - 2, k);
+    far[3] = val(i, j + 2, k); far[4] = val(i, j, k - 2); far[5] = val(i, j, k + 2);
+    dg[0] = val(i - 1, j - 1, k); dg[1] = val(i - 1, j + 1, k); dg[2] = val(i + 1, j - 1, k); dg[3] = val(i + 1, j + 1, k);
+    dg[4] = val(i - 1, j, k - 1); dg[5] = val(i + 1, j, k - 1); dg[6] = val(i, j - 1, k - 1); dg[7] = val(i, j + 1, k - 1);
+    dg[8] = val(i - 1, j, k + 1); dg[9] = val(i + 1, j, k + 1); dg[10] = val(i, j - 1, k + 1); dg[11] = val(i, j + 1, k + 1);
+    int E = max(1, exponent_of(ctr));
+#pragma unroll
+    for (int t = 0; t < 6; ++t) E = max(E, max(exponent_of(ax[t]), exponent_of(far[t])));
+#pragma unroll
+    for (int t = 0; t < 12; ++t) E = max(E, exponent_of(dg[t]));
+    long long s_ax = 0, s_far = 0, s_dg = 0;
+#pragma unroll
+    for (int t = 0; t < 6; ++t) {
+        s_ax += to_fixed(ax[t], E);
+        s_far += to_fixed(far[t], E);
+    }
+#pragma unroll
+    for (int t = 0; t < 12; ++t) s_dg += to_fixed(dg[t], E);
+    const int c = (i == 1) + (i == n - 1) + (j == 1) + (j == n - 1) + (k == 1) + (k == n - 1);
+    const long long acc = (long long)(42 + sigma * c) * to_fixed(ctr, E) - 12 * s_ax + s_far + 2 * s_dg;
+    return fx_result(acc, E, E == 0x7FF);
+}
+
+// ---------------------------------------------------------------------------
+// Bi-CG iterations of a small grid in one cooperative launch.  On grids of a
+// few tens of thousands of unknowns every kernel of an iteration lasts a few
+// microseconds and launch gaps dominate; here all CTAs stay resident and run
+// the three phases of an iteration (operator pair + sigma, x/r/r* update +
+// (r*, r), (r, r), direction update) separated by grid barriers.  Every CTA
+// adds the per-CTA partial sums itself, in CTA order, so all CTAs derive the
+// same alpha, beta and stopping decision.  The barrier spins a bounded
+// number of times; if it gives up, every CTA leaves and the state reports a
+// timeout.
+struct BicgVectors {
+    double* x;
+    double* r;
+    double* rs;
+    double* p;
+    double* ps;
+    double* q;
+    double* qs;
+};
+
+struct GridBarrier {
+    unsigned int* count;
+    unsigned int* gen;
+    int* err;
+};
+
+constexpr long long kBarrierSpinLimit = 1ll << 22;   // x >= 32 ns each: well over 0.1 s
+
+__device__ bool grid_sync(const GridBarrier& gb, unsigned int nblocks) {
+    __syncthreads();
+    if (thread0()) {
+        volatile unsigned int* gen = gb.gen;
+        volatile int* err = gb.err;
+        const unsigned int g = *gen;
+        __threadfence();
+        if (atomicAdd(gb.count, 1u) == nblocks - 1u) {
+            atomicExch(gb.count, 0u);
+            __threadfence();
+            atomicAdd(gb.gen, 1u);
+        } else {
+            long long spins = 0;
+            while (*gen == g) {
+                if (*err) break;
+                if (++spins > kBarrierSpinLimit) {
+                    atomicExch(gb.err, 1);
+                    break;
+                }
+                __nanosleep(32);
+            }
+        }
+        __threadfence();
+    }
+    __syncthreads();
+    return *(volatile int*)gb.err == 0;
+}
+
+// Sum of component c of the per-CTA partials, in CTA order (every CTA).
+__device__ __forceinline__ double all_partials(const double* partials, int c, double* sh) {
+    const int G = flat_grid();
+    const int nthreads = blockDim.x * blockDim.y * blockDim.z;
+    const int tid = threadIdx.x + blockDim.x * (threadIdx.y + blockDim.y * threadIdx.z);
+    double v = 0.0;
+    for (int b = tid; b < G; b += nthreads) v += __ldcg(&partials[c * G + b]);
+    v = block_sum(v, sh);
+    __shared__ double bc;
+    if (thread0()) bc = v;
+    __syncthreads();
+    v = bc;
+    __syncthreads();
+    return v;
+}
+
+template <bool kPointwise>
+__global__ void __launch_bounds__(FX_NT)
+bicg_persistent_kernel(BicgVectors v, size_t len, int n, int sigma, int gx, int gy, int slabs, int kz_per,
+                       int iters, double* partials, BicgState* st, GridBarrier gb) {
+    __shared__ double sh[32];
+    const unsigned int G = gridDim.x;
+    const int units = gx * gy * slabs;
+    const int tid = threadIdx.x + blockDim.x * threadIdx.y;
+    const int nthreads = blockDim.x * blockDim.y;
+    double rho = st->rho, rr = st->rr, alpha = st->alpha, beta = st->beta, sigma_s = st->sigma;
+    int iter = st->iter, status = st->status, done = st->done;
+    const int max_iter = st->max_iter;
+    const double stop = st->tol * st->bnorm;
+    const FxFields fl{{v.p, v.ps}, {v.q, v.qs}};
+    bool ok = true;
+    for (int it = 0; it < iters && !done && ok; ++it) {
+        // phase A: q = A p, qs = A^T ps, sigma = (ps, q); per node on the
+        // smallest grids, by z-marching tiles otherwise
+        double dot = 0.0;
+        if (kPointwise) {
+            const int m = n - 1, np = n + 1;
+            const long long pts = (long long)m * m * m;
+            for (long long t = (long long)blockIdx.x * nthreads + tid; t < pts; t += (long long)G * nthreads) {
+                const int i = (int)(t % m) + 1, j = (int)((t / m) % m) + 1, k = (int)(t / ((long long)m * m)) + 1;
+                const size_t o = ((size_t)k * np + j) * np + i;
+                const double qv = fx_point(v.p, n, sigma, i, j, k);
+                v.q[o] = qv;
+                v.qs[o] = fx_point(v.ps, n, sigma, i, j, k);
+                dot += v.ps[o] * qv;
+            }
+        } else {
+            for (int u = blockIdx.x; u < units; u += G) {
+                const int bx = u % gx, by = (u / gx) % gy, bz = u / (gx * gy);
+                const int kz0 = 1 + bz * kz_per;
+                dot += fx_march<2, true>(fl, nullptr, n, sigma, bx, by, kz0, min(kz0 + kz_per, n));
+            }
+        }
+        dot = block_sum(dot, sh);
+        if (thread0()) partials[blockIdx.x] = dot;
+        if (!(ok = grid_sync(gb, G))) break;
+        sigma_s = all_partials(partials, 0, sh);
+        if (!(rho != 0.0 && isfinite(rho)) || !(sigma_s != 0.0 && isfinite(sigma_s))) {
+            status = kBreakdown;
+            done = 1;
+            break;
+        }
+        alpha = rho / sigma_s;
+        // phase B: x += alpha p; r -= alpha q; r* -= alpha q*; (r*, r), (r, r)
+        double vr = 0.0, vrr = 0.0;
+        for (size_t t = (size_t)blockIdx.x * nthreads + tid; t < len; t += (size_t)G * nthreads) {
+            v.x[t] = v.x[t] + alpha * v.p[t];
+            const double rn = v.r[t] - alpha * v.q[t];
+            const double rsn = v.rs[t] - alpha * v.qs[t];
+            v.r[t] = rn;
+            v.rs[t] = rsn;
+            vr += rsn * rn;
+            vrr += rn * rn;
+        }
+        vr = block_sum(vr, sh);
+        vrr = block_sum(vrr, sh);
+        if (thread0()) {
+            partials[G + blockIdx.x] = vr;
+            partials[2 * G + blockIdx.x] = vrr;
+        }
+        if (!(ok = grid_sync(gb, G))) break;
+        const double rho_new = all_partials(partials, 1, sh);
+        rr = all_partials(partials, 2, sh);
+        beta = rho_new / rho;
+        rho = rho_new;
+        ++iter;
+        if (sqrt(rr) <= stop) {
+            status = kConverged;
+            done = 1;
+            break;
+        }
+        if (iter >= max_iter) {
+            status = kCapped;
+            done = 1;
+            break;
+        }
+        // phase C: p = r + beta p; p* = r* + beta p*
+        for (size_t t = (size_t)blockIdx.x * nthreads + tid; t < len; t += (size_t)G * nthreads) {
+            v.p[t] = v.r[t] + beta * v.p[t];
+            v.ps[t] = v.rs[t] + beta * v.ps[t];
+        }
+        if (!(ok = grid_sync(gb, G))) break;
+    }
+    if (blockIdx.x == 0 && thread0()) {
+        if (!ok) {
+            status = kTimeout;
+            done = 1;
+        }
+        st->rho = rho;
+        st->rr = rr;
+        st->alpha = alpha;
+        st->beta = beta;
+        st->sigma = sigma_s;
+        st->iter = iter;
+        st->status = status;
+        st->done = done;
     }
 }
 
@@ -459,6 +447,48 @@ cudaError_t launch_stencil(const double* u, double* y, const double* b, int n, i
                                                                skip, nullptr, nullptr);
     }
     return cudaGetLastError();
+}
+
+constexpr int kPointwiseMaxN = 40;   // per-node operator on grids up to 40^3
+
+int persistent_grid(int n, int* gx, int* gy, int* slabs, int* kz_per) {
+    static int occ_pt = 0, occ_mz = 0;
+    if (!occ_pt) {
+        occ_pt = resident_per_sm(bicg_persistent_kernel<true>, FX_NT);
+        occ_mz = resident_per_sm(bicg_persistent_kernel<false>, FX_NT);
+        if (occ_pt > 2) occ_pt = 2;
+        if (occ_mz > 2) occ_mz = 2;
+    }
+    const int m = n - 1;
+    *gx = (m + FX_TX - 1) / FX_TX;
+    *gy = (m + FX_OY - 1) / FX_OY;
+    *kz_per = m < 8 ? m : 4;
+    *slabs = (m + *kz_per - 1) / *kz_per;
+    if (n > kPointwiseMaxN) return 152 * occ_mz;
+    // one CTA per ~256 interior nodes, at most every resident slot: fewer
+    // CTAs keep the grid barriers short on small grids
+    const long long pts = (long long)m * m * m;
+    long long want = (pts + 255) / 256;
+    if (want < 8) want = 8;
+    if (want > 152LL * occ_pt) want = 152LL * occ_pt;
+    return (int)want;
+}
+
+cudaError_t launch_bicg_persistent(double* x, double* r, double* rs, double* p, double* ps, double* q, double* qs,
+                                   int n, int bc_kind, int iters, double* partials, BicgState* st,
+                                   unsigned int* barrier_words, cudaStream_t s) {
+    int gx, gy, slabs, kz_per;
+    const int G = persistent_grid(n, &gx, &gy, &slabs, &kz_per);
+    cudaError_t e = cudaMemsetAsync(barrier_words, 0, 3 * sizeof(unsigned int), s);
+    if (e != cudaSuccess) return e;
+    BicgVectors v{x, r, rs, p, ps, q, qs};
+    size_t len = node_count(n);
+    int sigma = bc_kind == 1 ? 1 : -1;
+    GridBarrier gb{barrier_words, barrier_words + 1, (int*)(barrier_words + 2)};
+    void* args[] = {&v, &len, &n, &sigma, &gx, &gy, &slabs, &kz_per, &iters, &partials, &st, &gb};
+    const void* fn = n <= kPointwiseMaxN ? (const void*)bicg_persistent_kernel<true>
+                                         : (const void*)bicg_persistent_kernel<false>;
+    return cudaLaunchCooperativeKernel(fn, dim3(G), dim3(FX_TX, FX_TY, 1), args, 0, s);
 }
 
 cudaError_t launch_bicg_stencil_pair(const double* p, double* q, const double* ps, double* qs, int n,

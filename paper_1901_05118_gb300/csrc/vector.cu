@@ -32,30 +32,36 @@ dot_kernel(const double* __restrict__ a, const double* __restrict__ b, size_t le
     }
 }
 
-// r*_0 = r_0, p_0 = r_0, p*_0 = r*_0; rho_0 = (r*_0, r_0), rr = (r_0, r_0).
+// r*_0 = shadow (or r_0), p_0 = r_0, p*_0 = r*_0; rho_0 = (r*_0, r_0),
+// rr = (r_0, r_0).
 __global__ void __launch_bounds__(kVecThreads)
-bicg_init_kernel(const double* __restrict__ r, double* __restrict__ rs, double* __restrict__ p,
-                 double* __restrict__ ps, size_t len, double* partials, BicgState* st) {
+bicg_init_kernel(const double* __restrict__ r, const double* __restrict__ shadow, double* __restrict__ rs,
+                 double* __restrict__ p, double* __restrict__ ps, size_t len, double* partials, BicgState* st) {
     __shared__ double sh[32];
     __shared__ bool am_last;
-    double v = 0.0;
+    double vr = 0.0, vrr = 0.0;
     for (size_t t = blockIdx.x * (size_t)blockDim.x + threadIdx.x; t < len;
          t += (size_t)gridDim.x * blockDim.x) {
         const double rv = r[t];
-        rs[t] = rv;
+        const double sv = shadow ? shadow[t] : rv;
+        rs[t] = sv;
         p[t] = rv;
-        ps[t] = rv;
-        v += rv * rv;
+        ps[t] = sv;
+        vr += sv * rv;
+        vrr += rv * rv;
     }
-    double s = block_sum(v, sh);
-    if (publish_partials(&s, 1, partials, &st->ticket, &am_last)) {
-        const double tot = gather_partials(partials, 0, sh);
+    double s2[2];
+    s2[0] = block_sum(vr, sh);
+    s2[1] = block_sum(vrr, sh);
+    if (publish_partials(s2, 2, partials, &st->ticket, &am_last)) {
+        const double rho = gather_partials(partials, 0, sh);
+        const double rr = gather_partials(partials, 1, sh);
         if (thread0()) {
-            st->rho = tot;   // (r*_0, r_0) with r*_0 = r_0
-            st->rr = tot;
+            st->rho = rho;
+            st->rr = rr;
             st->iter = 0;
             st->alpha = st->beta = st->sigma = 0.0;
-            const bool conv = sqrt(tot) <= st->tol * st->bnorm;
+            const bool conv = sqrt(rr) <= st->tol * st->bnorm;
             st->done = (conv || st->max_iter <= 0) ? 1 : 0;
             st->status = conv ? kConverged : (st->max_iter <= 0 ? kCapped : kRunning);
             st->ticket = 0;
@@ -93,6 +99,12 @@ bicg_sigma_kernel(const double* __restrict__ ps, const double* __restrict__ q, s
 
 // x += alpha p; r -= alpha A p; r* -= alpha A^T p*;
 // rho_{k+1} = (r*, r), beta = rho_{k+1} / rho_k; stopping test on ||r||.
+// Where r* and A^T p* equal r and A p bit for bit (always so with
+// r*_0 = r_0 and the integer operator) the shadow update gives the same
+// bits as the primal one and the product r* r equals r r, so it is formed
+// once; a thread that meets a differing entry continues with separate sums
+// from the identical partial sums it has so far.  FP64 issue is scarce on
+// GB300: this saves two of the five FMAs per entry.
 __global__ void __launch_bounds__(kVecThreads)
 bicg_update_kernel(double* __restrict__ x, const double* __restrict__ p, double* __restrict__ r,
                    const double* __restrict__ q, double* __restrict__ rs,
@@ -102,16 +114,34 @@ bicg_update_kernel(double* __restrict__ x, const double* __restrict__ p, double*
     __shared__ bool am_last;
     const double alpha = st->alpha;
     double vr = 0.0, vrr = 0.0;
+    bool twin = true;   // so far every entry of this thread was a twin: vr == vrr
     for (size_t t = blockIdx.x * (size_t)blockDim.x + threadIdx.x; t < len;
          t += (size_t)gridDim.x * blockDim.x) {
         x[t] = x[t] + alpha * p[t];
-        const double rn = r[t] - alpha * q[t];
-        const double rsn = rs[t] - alpha * qs[t];
+        const double rv = r[t], qv = q[t], rsv = rs[t], qsv = qs[t];
+        const double rn = rv - alpha * qv;
         r[t] = rn;
-        rs[t] = rsn;
-        vr += rsn * rn;
-        vrr += rn * rn;
+        if (__double_as_longlong(rsv) == __double_as_longlong(rv) &&
+            __double_as_longlong(qsv) == __double_as_longlong(qv)) {
+            rs[t] = rn;
+            if (twin) {
+                vrr += rn * rn;
+            } else {
+                vr += rn * rn;
+                vrr += rn * rn;
+            }
+        } else {
+            if (twin) {
+                vr = vrr;
+                twin = false;
+            }
+            const double rsn = rsv - alpha * qsv;
+            rs[t] = rsn;
+            vr += rsn * rn;
+            vrr += rn * rn;
+        }
     }
+    if (twin) vr = vrr;
     double s[2];
     s[0] = block_sum(vr, sh);
     s[1] = block_sum(vrr, sh);
@@ -135,7 +165,8 @@ bicg_update_kernel(double* __restrict__ x, const double* __restrict__ p, double*
     }
 }
 
-// p_{k+1} = r_{k+1} + beta p_k; p*_{k+1} = r*_{k+1} + beta p*_k.
+// p_{k+1} = r_{k+1} + beta p_k; p*_{k+1} = r*_{k+1} + beta p*_k (one FMA
+// where the shadow entries equal the primal ones bit for bit).
 __global__ void __launch_bounds__(kVecThreads)
 bicg_pupdate_kernel(double* __restrict__ p, const double* __restrict__ r, double* __restrict__ ps,
                     const double* __restrict__ rs, size_t len, const BicgState* st) {
@@ -143,8 +174,13 @@ bicg_pupdate_kernel(double* __restrict__ p, const double* __restrict__ r, double
     const double beta = st->beta;
     for (size_t t = blockIdx.x * (size_t)blockDim.x + threadIdx.x; t < len;
          t += (size_t)gridDim.x * blockDim.x) {
-        p[t] = r[t] + beta * p[t];
-        ps[t] = rs[t] + beta * ps[t];
+        const double rv = r[t], pv = p[t], rsv = rs[t], psv = ps[t];
+        const double pn = rv + beta * pv;
+        p[t] = pn;
+        if (__double_as_longlong(rsv) == __double_as_longlong(rv) && __double_as_longlong(psv) == __double_as_longlong(pv))
+            ps[t] = pn;
+        else
+            ps[t] = rsv + beta * psv;
     }
 }
 
@@ -156,9 +192,9 @@ cudaError_t launch_dot(const double* a, const double* b, size_t len, double* par
     return cudaGetLastError();
 }
 
-cudaError_t launch_bicg_init(const double* r, double* rs, double* p, double* ps, size_t len,
+cudaError_t launch_bicg_init(const double* r, const double* shadow, double* rs, double* p, double* ps, size_t len,
                              double* partials, BicgState* st, cudaStream_t s) {
-    bicg_init_kernel<<<kVecBlocks, kVecThreads, 0, s>>>(r, rs, p, ps, len, partials, st);
+    bicg_init_kernel<<<kVecBlocks, kVecThreads, 0, s>>>(r, shadow, rs, p, ps, len, partials, st);
     return cudaGetLastError();
 }
 

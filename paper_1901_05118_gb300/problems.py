@@ -160,16 +160,59 @@ def sin2pi_plus_poly() -> Manufactured:
     return separable("sin2pi_plus_poly", [(1.0, s, s, s), (1.0, q, q, q)])
 
 
-def random_sines(seed: int, n_terms: int = 4) -> Manufactured:
-    """u = sum of n_terms A sin(a pi x) sin(b pi y) sin(c pi z), a,b,c in [1,4]
-    integers and A ~ N(0,1), drawn from numpy's PCG64 with the given seed."""
+def random_sine_terms(seed: int, n_terms: int = 4):
+    """[(A, a, b, c)]: a, b, c integers in [1, 4], A ~ N(0, 1), numpy PCG64(seed)."""
     rng = np.random.Generator(np.random.PCG64(seed))
     terms = []
     for _ in range(n_terms):
         a, b, c = (int(v) for v in rng.integers(1, 5, size=3))
         A = float(rng.standard_normal())
-        terms.append((A, sin_factor(a), sin_factor(b), sin_factor(c)))
+        terms.append((A, a, b, c))
+    return terms
+
+
+def random_sines(seed: int, n_terms: int = 4) -> Manufactured:
+    """u = sum of n_terms A sin(a pi x) sin(b pi y) sin(c pi z), a,b,c in [1,4]
+    integers and A ~ N(0,1), drawn from numpy's PCG64 with the given seed."""
+    terms = [(A, sin_factor(a), sin_factor(b), sin_factor(c)) for A, a, b, c in random_sine_terms(seed, n_terms)]
     return separable(f"random_sines[{seed}]", terms)
+
+
+def random_sines_torch(seed: int, N: int, bc_kind: int, device, n_terms: int = 4):
+    """(f, g1, g2) of random_sines(seed) evaluated with torch on `device`
+    (used to build many request inputs quickly on the GPU).  The same closed
+    forms as the numpy version: f = sum A pi^4 (a^2+b^2+c^2)^2 s(x)s(y)s(z);
+    g1 = u; g2 the outward normal derivative (first kind) or the second
+    normal derivative (second kind) on the six faces."""
+    import torch
+
+    s = torch.arange(N + 1, dtype=torch.float64, device=device) / N
+    f = torch.zeros((N + 1,) * 3, dtype=torch.float64, device=device)
+    u = torch.zeros_like(f)
+    g2 = torch.zeros((6, N + 1, N + 1), dtype=torch.float64, device=device)
+    pi = float(PI)
+    for A, a, b, c in random_sine_terms(seed, n_terms):
+        sx, sy, sz = torch.sin(a * pi * s), torch.sin(b * pi * s), torch.sin(c * pi * s)
+        prod = sz[:, None, None] * sy[None, :, None] * sx[None, None, :]
+        u += A * prod
+        f += A * pi ** 4 * (a * a + b * b + c * c) ** 2 * prod
+        w = (a * pi, b * pi, c * pi)
+        for face in range(6):
+            axis, side = divmod(face, 2)
+            c1 = 1.0 if side else 0.0
+            if axis == 0:    # in-face (a, b) = (y, z): rows z, columns y
+                other = sz[:, None] * sy[None, :]
+            elif axis == 1:  # (x, z)
+                other = sz[:, None] * sx[None, :]
+            else:            # (x, y)
+                other = sy[:, None] * sx[None, :]
+            k = w[axis]
+            if bc_kind == 1:
+                d = k * np.cos(k * c1)
+                g2[face] += A * (d if side else -d) * other
+            else:
+                g2[face] += A * (-k * k * np.sin(k * c1)) * other
+    return f, u, g2
 
 
 def paper_problem1() -> Manufactured:

@@ -1,0 +1,96 @@
+"""The batch engine: many EXCMG solves resident on one GPU, their FP32
+correction solves advanced together in one cooperative launch."""
+import numpy as np
+import pytest
+
+import oracle
+from paper_1901_05118_gb300 import problems as P
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+if not torch.cuda.is_available():  # pragma: no cover - collected on CPU machines only
+    pytest.skip("needs a CUDA GPU", allow_module_level=True)
+
+from paper_1901_05118_gb300 import binding as B  # noqa: E402
+
+DEV = torch.device("cuda", 0)
+
+# (n_finest, n_coarsest, bc_kind, problem)
+MIX = [(32, 4, 1, "sin_pi"), (48, 6, 2, "random_sines:3"), (64, 8, 1, "random_sines:4"),
+       (24, 6, 2, "exp_sum"), (40, 5, 1, "sin2pi_plus_poly")]
+
+
+def data(n, bc, name):
+    prob = P.by_name(name)
+    f, g1, g2 = prob.data(n, bc)
+    return prob, tuple(torch.from_numpy(np.array(a, order="C")).to(DEV) for a in (f, g1, g2))
+
+
+@pytest.mark.parametrize("precision", ["fp64", "mixed"])
+def test_batch_matches_single_solves_and_oracle(precision):
+    """A mix of sizes, coarsest grids and kinds solved together matches each
+    instance solved alone and the oracle.  FP64: within the 1e-9 bound of a
+    full solve; mixed: reaches the same FP64 residual tolerance."""
+    tol = 1e-10
+    batch = B.Batch(max_instances=16)
+    subs = []
+    for n, nc, bc, name in MIX:
+        prob, (f, g1, g2) = data(n, bc, name)
+        ident, u = batch.submit(n, nc, bc, f, g1, g2, tol, precision=precision)
+        subs.append((ident, u, n, nc, bc, prob, f, g1, g2))
+    batch.run()
+    for ident, u, n, nc, bc, prob, f, g1, g2 in subs:
+        q = batch.query(ident)
+        assert q["done"] and q["status"] == 0
+        for s in q["stats"][2:]:
+            assert s["relres"] <= tol
+        fr, g1r, g2r = prob.data(n, bc)
+        _, ref_t, _ = oracle.excmg(n, nc, bc, fr, g1r, g2r, tol)
+        got = u.cpu().numpy()
+        scale = np.abs(ref_t).max()
+        if precision == "fp64":
+            single = B.excmg_solve(n, nc, bc, f, g1, g2, tol)
+            assert np.abs(got - ref_t).max() <= 1e-9 * scale
+            assert np.abs(got - single.cpu().numpy()).max() <= 1e-9 * scale
+        else:
+            disc = np.abs(ref_t - prob.exact(n)).max()
+            assert np.abs(got - ref_t).max() <= 0.05 * disc
+
+
+@pytest.mark.parametrize("precision", ["fp64", "mixed"])
+def test_batch_result_is_the_same_alone_and_in_the_mix(precision):
+    """An instance's tiles, chunks and partial sums never mix with another
+    instance's, so its result does not depend on what else is running --
+    bit for bit."""
+    n, nc, bc, name = 48, 6, 1, "random_sines:7"
+    _, (f, g1, g2) = data(n, bc, name)
+    alone = B.Batch(max_instances=4)
+    _, ua = alone.submit(n, nc, bc, f, g1, g2, 1e-10, precision=precision)
+    alone.run()
+    mixed = B.Batch(max_instances=8)
+    others = []
+    for k, (m, mc, mb, mn) in enumerate(MIX[:3]):
+        _, (mf, mg1, mg2) = data(m, mb, mn)
+        others.append(mixed.submit(m, mc, mb, mf, mg1, mg2, 1e-10, precision=["fp64", "mixed"][k % 2]))
+    mixed.step()
+    mixed.step()           # the instance joins a batch already under way
+    ident, um = mixed.submit(n, nc, bc, f, g1, g2, 1e-10, precision=precision)
+    mixed.run()
+    assert mixed.query(ident)["done"]
+    assert torch.equal(ua, um)
+
+
+def test_batch_admission_respects_the_budget():
+    n, nc = 32, 4
+    need = B.Batch.instance_bytes(n, nc, "mixed")
+    batch = B.Batch(hbm_budget_bytes=int(need * 1.5), max_instances=8)
+    _, (f, g1, g2) = data(n, 1, "sin_pi")
+    first = batch.submit(n, nc, 1, f, g1, g2, 1e-10)
+    assert first is not None
+    assert batch.submit(n, nc, 1, f, g1, g2, 1e-10) is None     # over budget: not admitted
+    batch.run()
+    assert batch.query(first[0])["done"]
+    assert batch.bytes == 0
+    assert batch.submit(n, nc, 1, f, g1, g2, 1e-10) is not None  # room again
+    batch.run()

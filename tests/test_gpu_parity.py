@@ -299,3 +299,20 @@ def test_mixed_precision_exact_polynomial():
     f, g1, g2 = prob.data(n, 1)
     ut = B.excmg_solve(n, 4, 1, dev(f), dev(g1), dev(g2), 1e-12, precision="mixed")
     assert np.abs(host(ut) - prob.exact(n)).max() <= 1e-11
+
+
+@pytest.mark.parametrize("n,bc_kind", [(20, 1), (80, 2)])
+def test_bicg_with_chosen_shadow(n, bc_kind):
+    """Alg. 2 with r*_0 != r_0: the shadow sequence now differs from the
+    primal one, so A^T p* is applied to a different vector (on 80^3 by the
+    fused z-march's general path, on 20^3 by the cooperative small-grid
+    kernel)."""
+    b = P.random_field(n, 51)
+    shadow = P.random_field(n, 52)
+    lvl = level(n, bc_kind)
+    x = torch.zeros((n + 1,) * 3, dtype=torch.float64, device=DEV)
+    it, rel, rc = B.bicg_solve(lvl, dev(b), x, 1e-11, 20000, shadow=dev(shadow))
+    xr, itr, relr, rcr = oracle.bicg(n, bc_kind, b, np.zeros_like(b), 1e-11, shadow=shadow)
+    assert rc == 0 and rcr == 0 and rel <= 1e-11
+    assert abs(it - itr) <= max(3, 0.05 * itr)
+    assert rel_max(host(x), xr) <= 1e-8

@@ -455,3 +455,15 @@ def test_problem_forcing_terms_match_symbolic():
             assert prob.f(px, py, pz) == pytest.approx(f(px, py, pz), rel=1e-10, abs=1e-10)
             np.testing.assert_allclose(prob.grad(px, py, pz), gx(px, py, pz), rtol=1e-12, atol=1e-12)
             np.testing.assert_allclose(prob.d2(px, py, pz), hx(px, py, pz), rtol=1e-12, atol=1e-12)
+
+
+@pytest.mark.parametrize("bc_kind", [1, 2])
+def test_bicg_with_chosen_shadow_matches_direct_solve(bc_kind):
+    """Alg. 2 leaves the shadow vectors free: any r*_0 with (r_0, r*_0) != 0
+    leads to the same solution (here against the direct solve)."""
+    N = 8
+    fh = P.random_field(N, 61)
+    xd = oracle.dsolve(N, bc_kind, fh, np.zeros_like(fh))
+    x, it, rel, rc = oracle.bicg(N, bc_kind, fh, np.zeros_like(fh), 1e-13, shadow=P.random_field(N, 62))
+    assert rc == 0 and rel <= 1e-13
+    np.testing.assert_allclose(interior(x), interior(xd), rtol=0, atol=1e-9 * np.abs(xd).max())
