@@ -57,8 +57,10 @@ def parse():
     ap.add_argument("--mixed-steps", type=int, default=2)
     ap.add_argument("--no-batch", action="store_true", help="skip the 64-instance batched leg")
     ap.add_argument("--no-serve", action="store_true", help="skip the request-stream leg")
-    ap.add_argument("--serve-requests", type=int, default=300)
+    ap.add_argument("--serve-requests", type=int, default=120)
     ap.add_argument("--serve-precision", choices=["fp64", "mixed"], default="fp64")
+    ap.add_argument("--oracle-report", action="store_true",
+                    help="time the CPU oracle on the small workload and one 512^3 operator application, then exit")
     return ap.parse_args()
 
 
@@ -267,7 +269,7 @@ def run_ours(args):
         barrier()
     ms_total = e0.elapsed_time(e1)
     launches = B.launch_count() - launches0
-    st_ms, st_cnt = ctx.profile_read(n)
+    st_ms, st_cnt, st_bytes = ctx.profile_read(n)
     ctx.profile(False)
     ms_step = max_over_ranks(ms_total / args.steps, world, dev)
     value = seconds_per_solve(ms_step, len(bcs), world)
@@ -316,13 +318,19 @@ def run_ours(args):
     except (OSError, ValueError):
         pass
     hbm_peak = float(peaks.get("hbm_gbs", 6800.0))
-    bytes_per_launch = 16.0 * (n - 1) ** 3          # read u + write y, 8 B each per unknown
+    # algorithmic bytes per launch as the library counts them: 8 B per unknown
+    # for every field read or written (the fused launch that also forms the
+    # directions: r, r*, p_old, p*_old in; p, p*, A p, A^T p* out)
     avg_ms = st_ms / st_cnt if st_cnt else float("nan")
-    achieved = bytes_per_launch / (avg_ms * 1e-3) / 1e9 if st_cnt else None
-    roofline = {"kernel": f"stencil_{args.stencil} (A p and A^T p* on the {n}^3 grid)", "bound": "hbm",
+    bytes_per_launch = st_bytes / st_cnt if st_cnt else None
+    achieved = st_bytes / (st_ms * 1e-3) / 1e9 if st_cnt else None
+    kernel = (f"stencil_fx_kernel: p = r + beta p, p* = r* + beta p*, A p and A^T p* and sigma on the {n}^3 grid"
+              if args.stencil == "exact" else f"stencil_f64_kernel: A p or A^T p* on the {n}^3 grid")
+    roofline = {"kernel": kernel, "bound": "hbm",
                 "achieved": achieved, "peak": hbm_peak, "unit": "GB/s",
                 "frac": (achieved / hbm_peak) if achieved else None, "traffic": None,
-                "launches": st_cnt, "avg_ms": avg_ms, "peak_source": "MEASURED_PEAKS.json hbm_gbs (of measured)"}
+                "launches": st_cnt, "avg_ms": avg_ms, "bytes_per_launch": bytes_per_launch,
+                "peak_source": "MEASURED_PEAKS.json hbm_gbs (of measured)"}
 
     mixed = None
     if not args.no_mixed:
@@ -499,8 +507,32 @@ def serving_leg(args, B, ctx, dev):
     return summ
 
 
+def oracle_report():
+    """CPU-baseline figures of the oracle on this host (single-threaded C):
+    the whole small workload (32^3, coarsest 4, first kind, u = sin pi x sin
+    pi y sin pi z, tol 1e-10 per level) and one operator application on 512^3."""
+    import oracle
+    from paper_1901_05118_gb300 import problems
+
+    prob = problems.sin_pi()
+    f, g1, g2 = prob.data(32, 1)
+    t0 = time.perf_counter()
+    _, _, st = oracle.excmg(32, 4, 1, f, g1, g2, 1e-10)
+    t_small = time.perf_counter() - t0
+    u = problems.random_field(512, 7)
+    t0 = time.perf_counter()
+    oracle.stencil_apply(512, 1, u)
+    t_op = time.perf_counter() - t0
+    print(json.dumps({"oracle_small_workload_s": t_small, "levels": st[:, 0].astype(int).tolist(),
+                      "oracle_stencil_512_s": t_op, "oracle_stencil_512_GBs": 16 * 511 ** 3 / t_op / 1e9,
+                      "cores": 1, "host_cpus": os.cpu_count()}), flush=True)
+
+
 def main():
     args = parse()
+    if args.oracle_report:
+        oracle_report()
+        return
     if args.impl == "reference":
         run_reference(args)
     else:

@@ -114,11 +114,15 @@ const char *excmg_last_error(const excmg_ctx *ctx);
  * made in this process (all contexts).  excmg_ctx_profile(ctx, 1) makes the
  * context time every operator launch inside Bi-CG with CUDA events on its
  * stream (and clears earlier records); excmg_ctx_profile_read returns, for
- * grids with n intervals, the summed device time (ms) and the number of
- * operator launches timed since. */
+ * grids with n intervals, the summed device time (ms), the number of
+ * operator launches timed since and (bytes may be NULL) the algorithmic
+ * bytes those launches read and wrote: 8 B per unknown for every field in
+ * or out (a launch of the fused pair that also forms the directions moves
+ * eight fields, the plain pair four, one FP64 application two). */
 long long excmg_launch_count(void);
 int excmg_ctx_profile(excmg_ctx *ctx, int enable);
-int excmg_ctx_profile_read(const excmg_ctx *ctx, int n, double *ms_total, long long *launches);
+int excmg_ctx_profile_read(const excmg_ctx *ctx, int n, double *ms_total, long long *launches,
+                           double *bytes);
 
 /* One grid with N intervals (N >= 4) and the given kind of boundary data.
  * The level borrows the context (destroy levels before their context). */
@@ -141,8 +145,10 @@ int stencil_apply(const excmg_level *level, int transpose, const double *u, doub
  * residual r*_0 = r_0, on A_h x = b.  b: node array (interior entries read);
  * x_inout: node array, initial guess in, iterate out (boundary entries left
  * unchanged).  Iterates until the recursively updated residual satisfies
- * ||r_k||_2 <= tol * ||b||_2 or max_iter iterations.  iters_out / relres_out
- * (may be NULL) receive the iteration count and ||r_k||_2 / ||b||_2.
+ * ||r_k||_2 <= tol * ||b||_2 or max_iter iterations, both norms taken over
+ * the unknowns (b's boundary entries are not part of the system and are
+ * ignored).  iters_out / relres_out (may be NULL) receive the iteration
+ * count and ||r_k||_2 / ||b||_2.
  * Returns EXCMG_OK on convergence, EXCMG_ERR_NOCONV at the cap,
  * EXCMG_ERR_BREAKDOWN on a breakdown. */
 int bicg_solve(const excmg_level *level, const double *b, double *x_inout, double tol,

@@ -70,7 +70,8 @@ _lib.excmg_ctx_set_stencil.argtypes = [_vp, _i]
 _lib.excmg_launch_count.argtypes = []
 _lib.excmg_launch_count.restype = ctypes.c_longlong
 _lib.excmg_ctx_profile.argtypes = [_vp, _i]
-_lib.excmg_ctx_profile_read.argtypes = [_vp, _i, ctypes.POINTER(_d), ctypes.POINTER(ctypes.c_longlong)]
+_lib.excmg_ctx_profile_read.argtypes = [_vp, _i, ctypes.POINTER(_d), ctypes.POINTER(ctypes.c_longlong),
+                                        ctypes.POINTER(_d)]
 _lib.excmg_last_error.argtypes = [_vp]
 _lib.excmg_last_error.restype = ctypes.c_char_p
 _lib.excmg_level_create.argtypes = [_vp, _i, _i, ctypes.POINTER(_vp)]
@@ -176,12 +177,14 @@ class Context:
         self.check(_lib.excmg_ctx_profile(self.handle, int(bool(enable))), "excmg_ctx_profile")
 
     def profile_read(self, n: int):
-        """(total ms, launches) of the operator on grids with n intervals since profile()."""
+        """(total ms, launches, algorithmic bytes) of the operator launches on
+        grids with n intervals since profile()."""
         ms = ctypes.c_double(0.0)
         cnt = ctypes.c_longlong(0)
-        self.check(_lib.excmg_ctx_profile_read(self.handle, int(n), ctypes.byref(ms), ctypes.byref(cnt)),
-                   "excmg_ctx_profile_read")
-        return ms.value, cnt.value
+        nbytes = ctypes.c_double(0.0)
+        self.check(_lib.excmg_ctx_profile_read(self.handle, int(n), ctypes.byref(ms), ctypes.byref(cnt),
+                                               ctypes.byref(nbytes)), "excmg_ctx_profile_read")
+        return ms.value, cnt.value, nbytes.value
 
     @property
     def bytes(self) -> int:

@@ -50,7 +50,7 @@ __device__ __forceinline__ float march_pair(const BatchInst<float>& in, int bx, 
     return f32_march<2, true>(in.p, in.ps, in.q, in.qs, in.n, (float)in.sigma, bx, by, kz0, kz1);
 }
 __device__ __forceinline__ double march_pair(const BatchInst<double>& in, int bx, int by, int kz0, int kz1) {
-    const FxFields fl{{in.p, in.ps}, {in.q, in.qs}};
+    const FxFields fl{{in.p, in.ps}, {in.q, in.qs}, {nullptr, nullptr}, {nullptr, nullptr}, 0.0};
     return fx_march<2, true>(fl, nullptr, in.n, in.sigma, bx, by, kz0, kz1);
 }
 
@@ -450,6 +450,20 @@ int setup_level(excmg_batch* b, Instance* in) {
     cudaError_t e = launch_assemble_rhs(in->fh, N, in->bc, in->f, in->g1, in->g2, stride, ctx->stream);
     if (e == cudaSuccess && l >= 2) e = launch_exp_finite(u, in->u[l - 1], in->u[l - 2], in->W, N, ctx->stream);
     if (e == cudaSuccess) e = launch_set_boundary(u, N, in->g1, stride, ctx->stream);
+    // the operator writes interior entries only and the buffers of A p, A p*
+    // are shared by all levels: clear them in this level's layout, or the
+    // previous level's values would sit on this level's boundary nodes and
+    // enter r, the inner products and u through the vector updates
+    if (e == cudaSuccess && l >= 2) {
+        const size_t len = node_count(N);
+        if (in->prec == EXCMG_PRECISION_FP64) {
+            e = cudaMemsetAsync(in->q64, 0, len * sizeof(double), ctx->stream);
+            if (e == cudaSuccess) e = cudaMemsetAsync(in->qs64, 0, len * sizeof(double), ctx->stream);
+        } else {
+            e = cudaMemsetAsync(in->q, 0, len * sizeof(float), ctx->stream);
+            if (e == cudaSuccess) e = cudaMemsetAsync(in->qs, 0, len * sizeof(float), ctx->stream);
+        }
+    }
     bnote(b, l >= 2 ? 4 : 2);
     if (e != cudaSuccess) return bcuda(b, e, "level setup");
     if (l <= 1) {

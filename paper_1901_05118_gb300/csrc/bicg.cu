@@ -3,6 +3,8 @@
 // device-resident BicgState, so iterations are enqueued in batches and the
 // host only looks at the state between batches.
 #include <cmath>
+#include <utility>
+#include <vector>
 
 #include "excmg_internal.cuh"
 
@@ -11,6 +13,19 @@ namespace excmg {
 int interior_norm(excmg_ctx* ctx, int n, const double* a, double* out) {
     const size_t len = node_count(n);
     cudaError_t e = launch_dot(a, a, len, ctx->partials, ctx->ticket, ctx->scalar, ctx->stream);
+    note_launches(1);
+    if (e == cudaSuccess)
+        e = cudaMemcpyAsync(ctx->host_scalar, ctx->scalar, sizeof(double), cudaMemcpyDeviceToHost, ctx->stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(ctx->stream);
+    if (e != cudaSuccess) return ctx_cuda(ctx, e, "norm");
+    *out = sqrt(*ctx->host_scalar);
+    return EXCMG_OK;
+}
+
+// ||a||_2 over the unknowns only, for vectors from a caller (their boundary
+// entries are not part of the system and may hold anything).
+int unknowns_norm(excmg_ctx* ctx, int n, const double* a, double* out) {
+    cudaError_t e = launch_interior_dot(a, n, ctx->partials, ctx->ticket, ctx->scalar, ctx->stream);
     note_launches(1);
     if (e == cudaSuccess)
         e = cudaMemcpyAsync(ctx->host_scalar, ctx->scalar, sizeof(double), cudaMemcpyDeviceToHost, ctx->stream);
@@ -48,6 +63,19 @@ int bicg_run(excmg_ctx* ctx, int n, int bc_kind, const double* b, double* x, dou
     double* q = st ? nullptr : ctx_buffer(ctx, "bicg_q", bytes, &st);
     double* qs = st ? nullptr : ctx_buffer(ctx, "bicg_qs", bytes, &st);
     if (st) return st;
+    // the integer operator has a fused two-field kernel; the FP64 one runs
+    // as two applications and a separate inner product
+    const bool fused = ctx->stencil_variant == kStencilExact && stencil_cta_count(n) <= kMaxPartials;
+    // small grids run whole iterations in one cooperative launch
+    const bool persistent = fused && n <= kPersistentMaxN;
+    // other grids, and the z-march variant of the cooperative kernel, fold
+    // p = r + beta p into the operator step, which reads the previous
+    // directions from one buffer pair and writes the new ones to the other
+    // (neighbouring blocks still read the old values)
+    const bool dir_fused = fused && !(persistent && persistent_pointwise(n));
+    double* p2 = dir_fused ? ctx_buffer(ctx, "bicg_p2", bytes, &st) : nullptr;
+    double* ps2 = (dir_fused && !st) ? ctx_buffer(ctx, "bicg_ps2", bytes, &st) : nullptr;
+    if (st) return st;
     cudaStream_t s = ctx->stream;
     if (check_every < 1) check_every = 1;
 
@@ -69,14 +97,12 @@ int bicg_run(excmg_ctx* ctx, int n, int bc_kind, const double* b, double* x, dou
     // keep zeros there
     if (e == cudaSuccess && shadow) e = launch_zero_boundary(rs, n, s);
     if (e == cudaSuccess && shadow) e = launch_zero_boundary(ps, n, s);
+    if (e == cudaSuccess && dir_fused) e = launch_zero_boundary(p2, n, s);
+    if (e == cudaSuccess && dir_fused) e = launch_zero_boundary(ps2, n, s);
     if (e != cudaSuccess) return ctx_cuda(ctx, e, "Bi-CG setup");
+    note_launches(dir_fused ? 2 : 0);
 
     const int* done = &ctx->state->done;
-    // the integer operator has a fused two-field kernel; the FP64 one runs
-    // as two applications and a separate inner product
-    const bool fused = ctx->stencil_variant == kStencilExact && stencil_cta_count(n) <= kMaxPartials;
-    // small grids run whole iterations in one cooperative launch
-    const bool persistent = fused && n <= kPersistentMaxN;
     if (persistent) {
         for (;;) {
             e = cudaMemcpyAsync(ctx->host_state, ctx->state, sizeof(BicgState), cudaMemcpyDeviceToHost, s);
@@ -86,7 +112,7 @@ int bicg_run(excmg_ctx* ctx, int n, int bc_kind, const double* b, double* x, dou
             int chunk = 256;
             const int left = max_iter - ctx->host_state->iter;
             if (chunk > left) chunk = left;
-            e = launch_bicg_persistent(x, r, rs, p, ps, q, qs, n, bc_kind, chunk, ctx->partials, ctx->state,
+            e = launch_bicg_persistent(x, r, rs, p, ps, p2, ps2, q, qs, n, bc_kind, chunk, ctx->partials, ctx->state,
                                        ctx->barrier, s);
             note_launches(1);
             if (e != cudaSuccess) return ctx_cuda(ctx, e, "cooperative Bi-CG launch");
@@ -95,6 +121,15 @@ int bicg_run(excmg_ctx* ctx, int n, int bc_kind, const double* b, double* x, dou
     note_launches(2);   // residual stencil + init (the memsets are not kernels)
     int batch = 0;
     int iter_before = 0;
+    // algorithmic bytes of one timed operator launch: 8 B per unknown for
+    // each field read or written
+    const double unknowns = (double)(n - 1) * (n - 1) * (n - 1);
+    std::vector<double> launch_bytes;
+    long long enqueued = 0;    // iterations enqueued so far
+    double* pc = p;            // directions of the current iteration
+    double* psc = ps;
+    double* pn = p2;           // buffer pair the next directions go to
+    double* psn = ps2;
     for (; !persistent;) {
         e = cudaMemcpyAsync(ctx->host_state, ctx->state, sizeof(BicgState), cudaMemcpyDeviceToHost, s);
         if (e == cudaSuccess) e = cudaStreamSynchronize(s);
@@ -102,13 +137,14 @@ int bicg_run(excmg_ctx* ctx, int n, int bc_kind, const double* b, double* x, dou
         if (ctx->profile && batch > 0) {
             // credit only the iterations of the last batch that really ran
             const int ran = ctx->host_state->iter - iter_before;
-            auto& rec = ctx->prof[n];
+            ProfRecord& rec = ctx->prof[n];
             for (int it = 0; it < ran && it < batch; ++it) {
                 float a = 0.f, b2 = 0.f;
                 cudaEventElapsedTime(&a, ctx->prof_events[3 * it], ctx->prof_events[3 * it + 1]);
                 cudaEventElapsedTime(&b2, ctx->prof_events[3 * it + 1], ctx->prof_events[3 * it + 2]);
-                rec.first += (double)a + (double)b2;
-                rec.second += 2;
+                rec.ms += (double)a + (double)b2;
+                rec.launches += fused ? 1 : 2;
+                rec.bytes += launch_bytes[it];
             }
         }
         if (ctx->host_state->done) break;
@@ -123,16 +159,29 @@ int bicg_run(excmg_ctx* ctx, int n, int bc_kind, const double* b, double* x, dou
                 ctx->prof_events.push_back(ev);
             }
         }
+        launch_bytes.assign(batch, 0.0);
         for (int it = 0; it < batch && e == cudaSuccess; ++it) {
             if (ctx->profile) cudaEventRecord(ctx->prof_events[3 * it], s);
             if (fused) {
-                // A p_k and A^T p*_k in one z-march, sigma_k and alpha_k fused
-                e = launch_bicg_stencil_pair(p, q, ps, qs, n, bc_kind, ctx->partials, ctx->state, s);
+                // A p_k and A^T p*_k in one z-march, sigma_k and alpha_k fused;
+                // from the second iteration on the launch first forms
+                // p_k = r_k + beta_{k-1} p_{k-1} (and p*_k) on the fly
+                if (enqueued == 0) {
+                    e = launch_bicg_stencil_pair(pc, q, psc, qs, n, bc_kind, ctx->partials, ctx->state, s);
+                    launch_bytes[it] = 32.0 * unknowns;   // p, p* in; q, q* out
+                } else {
+                    e = launch_bicg_stencil_pair_dir(r, rs, pc, psc, pn, psn, q, qs, n, bc_kind, ctx->partials,
+                                                     ctx->state, s);
+                    std::swap(pc, pn);
+                    std::swap(psc, psn);
+                    launch_bytes[it] = 64.0 * unknowns;   // r, r*, p, p* in; p, p*, q, q* out
+                }
                 if (ctx->profile) {
                     cudaEventRecord(ctx->prof_events[3 * it + 1], s);
                     cudaEventRecord(ctx->prof_events[3 * it + 2], s);
                 }
             } else {
+                launch_bytes[it] = 32.0 * unknowns;       // two launches of u in, y out
                 e = launch_stencil(p, q, nullptr, n, bc_kind, false, done, s, ctx->stencil_variant);  // A p_k
                 if (ctx->profile) cudaEventRecord(ctx->prof_events[3 * it + 1], s);
                 if (e == cudaSuccess)
@@ -141,10 +190,11 @@ int bicg_run(excmg_ctx* ctx, int n, int bc_kind, const double* b, double* x, dou
                 if (e == cudaSuccess) e = launch_bicg_sigma(ps, q, len, ctx->partials, ctx->state, s);
             }
             if (e == cudaSuccess)
-                e = launch_bicg_update(x, p, r, q, rs, qs, len, ctx->partials, ctx->state, s);
-            if (e == cudaSuccess) e = launch_bicg_pupdate(p, r, ps, rs, len, ctx->state, s);
+                e = launch_bicg_update(x, pc, r, q, rs, qs, len, ctx->partials, ctx->state, s);
+            if (e == cudaSuccess && !fused) e = launch_bicg_pupdate(p, r, ps, rs, len, ctx->state, s);
+            ++enqueued;
         }
-        note_launches((fused ? 3LL : 5LL) * batch);
+        note_launches((fused ? 2LL : 5LL) * batch);
         if (e != cudaSuccess) return ctx_cuda(ctx, e, "Bi-CG iteration");
     }
     const BicgState& h = *ctx->host_state;

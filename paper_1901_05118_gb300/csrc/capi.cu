@@ -153,11 +153,13 @@ int excmg_ctx_profile(excmg_ctx* c, int enable) {
     return EXCMG_OK;
 }
 
-int excmg_ctx_profile_read(const excmg_ctx* c, int n, double* ms_total, long long* launches) {
+int excmg_ctx_profile_read(const excmg_ctx* c, int n, double* ms_total, long long* launches, double* bytes) {
     if (!c || !ms_total || !launches) return EXCMG_ERR_ARG;
     auto it = c->prof.find(n);
-    *ms_total = it == c->prof.end() ? 0.0 : it->second.first;
-    *launches = it == c->prof.end() ? 0 : it->second.second;
+    const bool have = it != c->prof.end();
+    *ms_total = have ? it->second.ms : 0.0;
+    *launches = have ? it->second.launches : 0;
+    if (bytes) *bytes = have ? it->second.bytes : 0.0;
     return EXCMG_OK;
 }
 
@@ -203,7 +205,7 @@ int bicg_solve(const excmg_level* level, const double* b, double* x_inout, doubl
     excmg_ctx* ctx = level->ctx;
     if (!(tol >= 0.0) || max_iter < 0) return ctx_fail(ctx, EXCMG_ERR_ARG, "bicg_solve: bad tol / max_iter");
     double bnorm = 0.0;
-    int st = interior_norm(ctx, level->n, b, &bnorm);
+    int st = unknowns_norm(ctx, level->n, b, &bnorm);
     if (st) return st;
     return bicg_run(ctx, level->n, level->bc_kind, b, x_inout, tol, bnorm, max_iter, 16, iters_out,
                     relres_out);
@@ -215,7 +217,7 @@ int bicg_solve_ex(const excmg_level* level, const double* b, double* x_inout, co
     excmg_ctx* ctx = level->ctx;
     if (!(tol >= 0.0) || max_iter < 0) return ctx_fail(ctx, EXCMG_ERR_ARG, "bicg_solve_ex: bad tol / max_iter");
     double bnorm = 0.0;
-    int st = interior_norm(ctx, level->n, b, &bnorm);
+    int st = unknowns_norm(ctx, level->n, b, &bnorm);
     if (st) return st;
     return bicg_run(ctx, level->n, level->bc_kind, b, x_inout, tol, bnorm, max_iter, 16, iters_out, relres_out,
                     shadow_r0);

@@ -41,7 +41,8 @@ struct BicgState {
     int done;          // 1 once converged, capped or broken down
     int status;        // kRunning / kConverged / kCapped / kBreakdown
     unsigned int ticket;   // last-block counter of the reductions
-    int pad1[3];
+    int fault;         // set by a kernel whose bounded wait for a copy gave up
+    int pad1[2];
 };
 enum { kRunning = 0, kConverged = 1, kCapped = 2, kBreakdown = 3, kTimeout = 4 };
 
@@ -59,17 +60,30 @@ cudaError_t launch_zero_boundary(double* y, int n, cudaStream_t s);
 cudaError_t launch_bicg_stencil_pair(const double* p, double* q, const double* ps, double* qs, int n,
                                      int bc_kind, double* partials, BicgState* st, cudaStream_t s);
 int stencil_cta_count(int n);
+// As launch_bicg_stencil_pair, with the direction update of the previous
+// iteration fused in: p = r + beta p_prev, p* = r* + beta p*_prev (beta from
+// st), written to p / ps (which must not alias p_prev / ps_prev).
+cudaError_t launch_bicg_stencil_pair_dir(const double* r, const double* rs, const double* p_prev,
+                                         const double* ps_prev, double* p, double* ps, double* q, double* qs, int n,
+                                         int bc_kind, double* partials, BicgState* st, cudaStream_t s);
 // Small grids: whole Bi-CG iterations (up to `iters`) in one cooperative
-// launch with bounded grid barriers; barrier_words: 3 device words.
-constexpr int kPersistentMaxN = 64;
-cudaError_t launch_bicg_persistent(double* x, double* r, double* rs, double* p, double* ps, double* q, double* qs,
-                                   int n, int bc_kind, int iters, double* partials, BicgState* st,
-                                   unsigned int* barrier_words, cudaStream_t s);
+// launch with bounded grid barriers; barrier_words: 3 device words.  Unless
+// persistent_pointwise(n), the directions alternate between (p, ps) and
+// (p2, ps2), whose boundary entries must be zero; p, ps must hold p_0 on
+// entry (iteration k reads p_{k-1} from one pair, writes p_k to the other).
+constexpr int kPersistentMaxN = 128;
+bool persistent_pointwise(int n);
+cudaError_t launch_bicg_persistent(double* x, double* r, double* rs, double* p, double* ps, double* p2, double* ps2,
+                                   double* q, double* qs, int n, int bc_kind, int iters, double* partials,
+                                   BicgState* st, unsigned int* barrier_words, cudaStream_t s);
 
 // Vectors (flat over all (n+1)^3 entries; boundary entries of the Bi-CG
 // vectors are zero, so flat sums equal sums over the unknowns).
 cudaError_t launch_dot(const double* a, const double* b, size_t len, double* partials,
                        unsigned int* ticket, double* out, cudaStream_t s);
+// (a, a) over the interior nodes only (a's boundary entries are ignored).
+cudaError_t launch_interior_dot(const double* a, int n, double* partials, unsigned int* ticket, double* out,
+                                cudaStream_t s);
 cudaError_t launch_bicg_init(const double* r, const double* shadow, double* rs, double* p, double* ps, size_t len,
                              double* partials, BicgState* st, cudaStream_t s);
 cudaError_t launch_bicg_sigma(const double* ps, const double* q, size_t len, double* partials,
@@ -108,6 +122,14 @@ struct excmg_buffer {
     size_t bytes = 0;
 };
 
+// Operator launches timed inside Bi-CG on one grid size: device time,
+// launch count and the algorithmic bytes those launches read and wrote.
+struct ProfRecord {
+    double ms = 0.0;
+    long long launches = 0;
+    double bytes = 0.0;
+};
+
 struct excmg_ctx {
     int device = 0;
     cudaStream_t stream = nullptr;
@@ -130,7 +152,7 @@ struct excmg_ctx {
     // optional timing of the operator launches inside Bi-CG
     bool profile = false;
     std::vector<cudaEvent_t> prof_events;
-    std::map<int, std::pair<double, long long>> prof;   // n -> (ms, launches)
+    std::map<int, ProfRecord> prof;   // grid intervals n -> timed operator launches
 };
 
 struct excmg_level {
@@ -153,7 +175,8 @@ int bicg_run(excmg_ctx* ctx, int n, int bc_kind, const double* b, double* x, dou
 // ||b - A x||_2 over the unknowns, via the context's workspace (result on host).
 int true_residual_norm(excmg_ctx* ctx, int n, int bc_kind, const double* b, const double* x,
                        double* out);
-int interior_norm(excmg_ctx* ctx, int n, const double* a, double* out);
+int interior_norm(excmg_ctx* ctx, int n, const double* a, double* out);   // flat: zero boundary assumed
+int unknowns_norm(excmg_ctx* ctx, int n, const double* a, double* out);   // interior nodes only
 // DSOLVE (dsolve.cu)
 int dsolve_run(excmg_ctx* ctx, int n, int bc_kind, const double* fh, double* u);
 // FP32 inner solves + FP64 refinement on one level (mixed.cu).

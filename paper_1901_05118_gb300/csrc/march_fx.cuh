@@ -86,7 +86,85 @@ constexpr int FX_SLOTS = (FX_HX * FX_HY + FX_NT - 1) / FX_NT;
 struct FxFields {
     const double* in[2];
     double* out[2];
+    // direction update fused into the march (kDir): the inputs in[] are the
+    // previous directions p, p*, and each loaded value becomes
+    // r + beta p (r* + beta p* for field 1); nodes the CTA owns are written
+    // to pn[] (a second buffer: neighbours still read the old directions)
+    const double* dr[2];
+    double* pn[2];
+    double beta;
+    // staged loads: shared-memory stages (fx_stage_bytes) and a device word
+    // set to 1 when a bounded wait for a copy gave up
+    unsigned char* stage;
+    int* fault;
 };
+
+// ---------------------------------------------------------------------------
+// Staged loads (kBulk).  The CTA's input rows of the next planes are brought
+// into shared memory by the bulk-copy engine while the current plane is
+// computed, so the plane loop does not wait for DRAM.  Rows hold n + 1
+// doubles; n is even on every level of the method, so a row's byte pitch is
+// not a multiple of 16 and no tiled tensor map describes the grid.  Each
+// halo row (36 doubles from x = i0 - 2) is therefore one untiled bulk copy
+// of FX_ROW doubles starting at the 16-byte boundary at or below it; readers
+// add that row's shift (0 or 1 element).  Only rows and planes inside the
+// interior are copied (the rest reads as zero, as in the direct loads); all
+// copied bytes lie inside the grid array for n >= 16.  Each stage has one
+// mbarrier that the copies of one plane complete.
+constexpr int FX_ROW = 40;   // 320 B: 36 needed + shift, a multiple of 16 B
+template <int NL, int S>
+__host__ __device__ constexpr size_t fx_stage_bytes() {
+    return (size_t)S * NL * FX_HY * FX_ROW * sizeof(double) + 128;   // + mbarriers
+}
+__host__ __device__ constexpr int fx_stages(bool dir) { return dir ? 2 : 3; }
+
+__device__ __forceinline__ unsigned smem_u32(const void* p) {
+    return (unsigned)__cvta_generic_to_shared(p);
+}
+
+__device__ __forceinline__ void mbar_init(unsigned long long* bar, unsigned count) {
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(bar)), "r"(count) : "memory");
+}
+
+__device__ __forceinline__ void mbar_arrive_tx(unsigned long long* bar, unsigned tx) {
+    unsigned long long state;
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 %0, [%1], %2;"
+                 : "=l"(state) : "r"(smem_u32(bar)), "r"(tx) : "memory");
+    (void)state;
+}
+
+__device__ __forceinline__ void mbar_arrive(unsigned long long* bar) {
+    unsigned long long state;
+    asm volatile("mbarrier.arrive.shared::cta.b64 %0, [%1];" : "=l"(state) : "r"(smem_u32(bar)) : "memory");
+    (void)state;
+}
+
+__device__ __forceinline__ bool mbar_try_wait(unsigned long long* bar, unsigned parity) {
+    unsigned ok;
+    asm volatile(
+        "{\n\t.reg .pred p;\n\t"
+        "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
+        "selp.u32 %0, 1, 0, p;\n\t}"
+        : "=r"(ok) : "r"(smem_u32(bar)), "r"(parity) : "memory");
+    return ok != 0;
+}
+
+// Bounded wait for the phase with the given parity; false when it gave up.
+__device__ __forceinline__ bool mbar_wait(unsigned long long* bar, unsigned parity) {
+    for (int spin = 0; spin < (1 << 22); ++spin)
+        if (mbar_try_wait(bar, parity)) return true;
+    return false;
+}
+
+__device__ __forceinline__ void bulk_g2s(void* dst, const void* src, unsigned bytes, unsigned long long* bar) {
+    asm volatile(
+        "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];"
+        ::"r"(smem_u32(dst)), "l"(src), "r"(bytes), "r"(smem_u32(bar)) : "memory");
+}
+
+__device__ __forceinline__ void fence_async_smem() {
+    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+}
 
 // Rare cases (a non-finite input, or a scale outside the normal range of the
 // fast conversion) leave the hot path through a call, so that the compiler
@@ -104,7 +182,7 @@ __device__ __forceinline__ double fx_result(long long acc, int E, bool poisoned)
 // One CTA's z-march over the output columns of tile (bx, by) and the output
 // planes [kz0, kz1).  Returns this thread's share of (field 1 in, field 0
 // out) when kDot.  Called uniformly by all threads of the CTA.
-template <int NF, bool kDot>
+template <int NF, bool kDot, bool kDir = false, bool kBulk = false>
 __device__ __forceinline__ double fx_march(const FxFields& fl, const double* __restrict__ b, int n, int sigma,
                                            int bx, int by, int kz0, int kz1) {
     __shared__ long long tile[NF][FX_HY * FX_HX];
@@ -118,16 +196,19 @@ __device__ __forceinline__ double fx_march(const FxFields& fl, const double* __r
     // halo-load slots of this thread: in-plane offset (-1: outside the
     // interior, reads as zero) and shared-memory index (-1: no slot)
     int soff[FX_SLOTS], sidx[FX_SLOTS];
+    bool own[FX_SLOTS];   // the slot is one of this CTA's output columns
 #pragma unroll
     for (int r = 0; r < FX_SLOTS; ++r) {
         const int e = tid + r * FX_NT;
         soff[r] = -1;
         sidx[r] = -1;
+        own[r] = false;
         if (e < FX_HX * FX_HY) {
             const int ly = e / FX_HX, lx = e - ly * FX_HX;
             const int gi = i0 - 2 + lx, gj = j0 - 2 + ly;
             sidx[r] = e;
             if (gi >= 1 && gi <= n - 1 && gj >= 1 && gj <= n - 1) soff[r] = gj * np + gi;
+            own[r] = soff[r] >= 0 && lx >= 2 && lx < 2 + FX_TX && ly >= 2 && ly < 2 + FX_OY;
         }
     }
     const int i = i0 + tx, ja = j0 + ty * FX_RY;
@@ -137,6 +218,69 @@ __device__ __forceinline__ double fx_march(const FxFields& fl, const double* __r
     const int c0 = cx + (ja == 1) + (ja == n - 1);
     const int c1 = cx + (ja + 1 == 1) + (ja + 1 == n - 1);
     const int ry = ty * FX_RY + 2, rx = tx + 2;   // tile coordinates of the first output
+
+    // staged loads: arrays copied per plane (kDir: p, r, p*, r*), stages
+    constexpr int NL = kDir ? 2 * NF : NF;
+    constexpr int S = fx_stages(kDir);
+    double* raw = reinterpret_cast<double*>(fl.stage);
+    unsigned long long* bar =
+        reinterpret_cast<unsigned long long*>(fl.stage + (size_t)S * NL * FX_HY * FX_ROW * sizeof(double));
+    const double* src[NL];
+    if (kBulk) {
+#pragma unroll
+        for (int a = 0; a < NL; ++a) src[a] = kDir ? ((a & 1) ? fl.dr[a >> 1] : fl.in[a >> 1]) : fl.in[a];
+    }
+    // rows of the halo inside the interior, and this thread's row shifts
+    const int row_lo = max(0, 1 - (j0 - 2)), row_hi = min(FX_HY, n - 1 - (j0 - 2) + 1);
+    const unsigned plane_tx = kBulk ? (unsigned)(max(0, row_hi - row_lo) * NL * FX_ROW * sizeof(double)) : 0u;
+    int rpar[FX_SLOTS], rbase[FX_SLOTS];   // row parity at plane 0, staged row offset
+#pragma unroll
+    for (int r = 0; r < FX_SLOTS; ++r) {
+        rpar[r] = 0;
+        rbase[r] = 0;
+        if (kBulk && sidx[r] >= 0) {
+            const int ly = sidx[r] / FX_HX, lx = sidx[r] - ly * FX_HX;
+            const long long L = (long long)(j0 - 2 + ly) * np + (i0 - 2);
+            rpar[r] = (int)(L & 1);
+            rbase[r] = ly * FX_ROW + lx;
+        }
+    }
+    const int plane_par = (int)(plane & 1);
+    const int T = kz1 - kz0 + 4;   // planes zin = kz0 - 2 .. kz1 + 1
+    bool stalled = false;
+    // copy plane t of the march into stage t % S (warp 0)
+    auto issue = [&](int t) {
+        if (t >= T || tid >= 32) return;
+        const int zin = kz0 - 2 + t;
+        unsigned long long* bt = bar + (t % S);
+        const bool load = zin >= 1 && zin <= n - 1 && plane_tx > 0;
+        // the stage was last read through ordinary loads: order those reads
+        // before the copy engine's writes
+        fence_async_smem();
+        if (lane == 0) {
+            if (load) mbar_arrive_tx(bt, plane_tx);
+            else mbar_arrive(bt);
+        }
+        __syncwarp();
+        if (load && lane >= row_lo && lane < row_hi) {
+            const long long L = ((long long)zin * np + (j0 - 2 + lane)) * np + (i0 - 2);
+            const long long La = L & ~1ll;
+            double* dst = raw + ((size_t)(t % S) * NL * FX_HY + lane) * FX_ROW;
+#pragma unroll
+            for (int a = 0; a < NL; ++a)
+                bulk_g2s(dst + (size_t)a * FX_HY * FX_ROW, src[a] + La, FX_ROW * sizeof(double), bt);
+        }
+    };
+    if (kBulk) {
+        if (tid == 0) {
+#pragma unroll
+            for (int k = 0; k < S; ++k) mbar_init(bar + k, 1);
+            asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+        }
+        __syncthreads();
+#pragma unroll
+        for (int t = 0; t < S - 1; ++t) issue(t);
+    }
 
     long long acc[NF][FX_RY][5];
     int E[NF];
@@ -157,14 +301,65 @@ __device__ __forceinline__ double fx_march(const FxFields& fl, const double* __r
         const size_t zbase = zok ? (size_t)zin * plane : 0;
         double v[NF][FX_SLOTS];
         bool same = true;
+        // staged input of this plane: element (array a, slot r)
+        const int t = zin - (kz0 - 2);
+        const double* stg = raw + (size_t)(t % S) * NL * FX_HY * FX_ROW;
+        const int zpar = plane_par & zin;
+        auto staged = [&](int a, int r) {
+            return stg[(size_t)a * FX_HY * FX_ROW + rbase[r] + (rpar[r] ^ zpar)];
+        };
+        if (kBulk) {
+            // the stage that plane t - 1 used is free again (every thread
+            // passed the barriers after reading it): refill it
+            issue(t + S - 1);
+            if (!mbar_wait(bar + (t % S), (unsigned)((t / S) & 1))) {
+                // a copy did not arrive: flag the launch, wait once more
+                // (bounded) for the copies in flight, carry on
+                stalled = true;
+                mbar_wait(bar + (t % S), (unsigned)((t / S) & 1));
+            }
+        }
+        if (kDir) {
+            // p = r + beta p, p* = r* + beta p* on every loaded node; where
+            // r*, p* equal r, p bit for bit, p* takes p's bits
+            const bool zown = zin >= kz0 && zin < kz1;
+#pragma unroll
+            for (int r = 0; r < FX_SLOTS; ++r) {
+                double pv = 0.0, psv = 0.0;
+                if (zok && soff[r] >= 0) {
+                    const size_t o = zbase + soff[r];
+                    const double rv = kBulk ? staged(1, r) : fl.dr[0][o];
+                    const double po = kBulk ? staged(0, r) : fl.in[0][o];
+                    pv = rv + fl.beta * po;
+                    if (NF == 2) {
+                        const double rsv = kBulk ? staged(NL - 1, r) : fl.dr[NF - 1][o];
+                        const double pso = kBulk ? staged(NL - 2, r) : fl.in[NF - 1][o];
+                        if (__double_as_longlong(rsv) == __double_as_longlong(rv) &&
+                            __double_as_longlong(pso) == __double_as_longlong(po))
+                            psv = pv;
+                        else
+                            psv = rsv + fl.beta * pso;
+                    }
+                    if (zown && own[r]) {
+                        fl.pn[0][o] = pv;
+                        if (NF == 2) fl.pn[NF - 1][o] = psv;
+                    }
+                }
+                v[0][r] = pv;
+                if (NF == 2) v[NF - 1][r] = psv;
+            }
+        } else {
+#pragma unroll
+            for (int f = 0; f < NF; ++f)
+#pragma unroll
+                for (int r = 0; r < FX_SLOTS; ++r)
+                    v[f][r] = (zok && soff[r] >= 0) ? (kBulk ? staged(f, r) : fl.in[f][zbase + soff[r]]) : 0.0;
+        }
 #pragma unroll
         for (int f = 0; f < NF; ++f) {
             int emax = 0;
 #pragma unroll
-            for (int r = 0; r < FX_SLOTS; ++r) {
-                v[f][r] = (zok && soff[r] >= 0) ? fl.in[f][zbase + soff[r]] : 0.0;
-                emax = max(emax, exponent_of(v[f][r]));
-            }
+            for (int r = 0; r < FX_SLOTS; ++r) emax = max(emax, exponent_of(v[f][r]));
             emax = (int)__reduce_max_sync(0xffffffffu, (unsigned)emax);
             if (lane == 0) wmax[f][tid >> 5] = emax;
         }
@@ -277,7 +472,9 @@ __device__ __forceinline__ double fx_march(const FxFields& fl, const double* __r
                     if (f == 0) val0[q] = val;
                     if (NF == 1 && b != nullptr) val = b[o] - val;
                     fl.out[f][o] = val;
-                    if (kDot && f == 0) dot += __ldg(&fl.in[1][o]) * val;
+                    if (kDot && f == 0)
+                        // p*'s new value was written by this CTA two planes ago
+                        dot += (kDir ? __ldcg(&fl.pn[1][o]) : __ldg(&fl.in[1][o])) * val;
                 }
             }
 #pragma unroll
@@ -290,6 +487,7 @@ __device__ __forceinline__ double fx_march(const FxFields& fl, const double* __r
             }
         }
     }
+    if (kBulk && stalled) atomicExch(fl.fault, 1);
     return dot;
 }
 

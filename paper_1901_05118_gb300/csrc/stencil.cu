@@ -21,6 +21,8 @@
 // of p + d).  Each tap d has a partner -d of equal weight and the folding is
 // diagonal, so this is the same arithmetic; the flag is kept so that A^T is
 // applied as Alg. 2 asks (its shadow recurrence multiplies by A^T).
+#include <initializer_list>
+
 #include "excmg_internal.cuh"
 #include "march_fx.cuh"
 #include "reduce.cuh"
@@ -93,14 +95,20 @@ stencil_f64_kernel(const double* __restrict__ u, double* __restrict__ y, const d
     }
 }
 
-template <int NF, bool kDot>
+template <int NF, bool kDot, bool kDir = false, bool kBulk = false>
 __global__ void __launch_bounds__(FX_NT)
 stencil_fx_kernel(FxFields fl, const double* __restrict__ b, int n, int sigma, int kz_per_cta,
                   const int* __restrict__ skip, double* partials, BicgState* st) {
+    extern __shared__ __align__(128) unsigned char fx_stage_smem[];
     if (skip != nullptr && *skip) return;
     const int kz0 = 1 + blockIdx.z * kz_per_cta;
     const int kz1 = min(kz0 + kz_per_cta, n);
-    const double dot = fx_march<NF, kDot>(fl, b, n, sigma, blockIdx.x, blockIdx.y, kz0, kz1);
+    if (kDir) fl.beta = st->beta;
+    if (kBulk) {
+        fl.stage = fx_stage_smem;
+        fl.fault = &st->fault;
+    }
+    const double dot = fx_march<NF, kDot, kDir, kBulk>(fl, b, n, sigma, blockIdx.x, blockIdx.y, kz0, kz1);
     if (kDot) {
         __shared__ double sh[32];
         __shared__ bool am_last;
@@ -110,7 +118,10 @@ stencil_fx_kernel(FxFields fl, const double* __restrict__ b, int n, int sigma, i
             if (thread0()) {
                 const double rho = st->rho;
                 st->sigma = sg;
-                if (!(rho != 0.0 && isfinite(rho)) || !(sg != 0.0 && isfinite(sg))) {
+                if (kBulk && *(volatile int*)&st->fault) {
+                    st->status = kTimeout;
+                    st->done = 1;
+                } else if (!(rho != 0.0 && isfinite(rho)) || !(sg != 0.0 && isfinite(sg))) {
                     st->status = kBreakdown;
                     st->done = 1;
                 } else {
@@ -175,6 +186,8 @@ struct BicgVectors {
     double* rs;
     double* p;
     double* ps;
+    double* p2;    // second direction pair of the z-march variant (p_k lives
+    double* ps2;   // in p / ps for odd k, in p2 / ps2 for even k)
     double* q;
     double* qs;
 };
@@ -232,7 +245,7 @@ __device__ __forceinline__ double all_partials(const double* partials, int c, do
 }
 
 template <bool kPointwise>
-__global__ void __launch_bounds__(FX_NT)
+__global__ void __launch_bounds__(FX_NT, 2)
 bicg_persistent_kernel(BicgVectors v, size_t len, int n, int sigma, int gx, int gy, int slabs, int kz_per,
                        int iters, double* partials, BicgState* st, GridBarrier gb) {
     __shared__ double sh[32];
@@ -240,13 +253,21 @@ bicg_persistent_kernel(BicgVectors v, size_t len, int n, int sigma, int gx, int 
     const int units = gx * gy * slabs;
     const int tid = threadIdx.x + blockDim.x * threadIdx.y;
     const int nthreads = blockDim.x * blockDim.y;
+    extern __shared__ __align__(128) unsigned char persistent_stage_smem[];
     double rho = st->rho, rr = st->rr, alpha = st->alpha, beta = st->beta, sigma_s = st->sigma;
     int iter = st->iter, status = st->status, done = st->done;
     const int max_iter = st->max_iter;
     const double stop = st->tol * st->bnorm;
-    const FxFields fl{{v.p, v.ps}, {v.q, v.qs}};
+    const FxFields fl{{v.p, v.ps}, {v.q, v.qs}, {nullptr, nullptr}, {nullptr, nullptr}, 0.0, nullptr, nullptr};
     bool ok = true;
     for (int it = 0; it < iters && !done && ok; ++it) {
+        // z-march variant: iteration k forms p_k = r_k + beta_{k-1} p_{k-1}
+        // (p*_k likewise) inside the operator phase, reading p_{k-1} from one
+        // buffer pair and writing p_k to the other; k = 0 reads the copy of
+        // r_0 made by the set-up with beta = 0, which gives r_0 exactly
+        const bool odd = iter & 1;
+        double* const pk = odd ? v.p : v.p2;
+        double* const psk = odd ? v.ps : v.ps2;
         // phase A: q = A p, qs = A^T ps, sigma = (ps, q); per node on the
         // smallest grids, by z-marching tiles otherwise
         double dot = 0.0;
@@ -262,10 +283,12 @@ bicg_persistent_kernel(BicgVectors v, size_t len, int n, int sigma, int gx, int 
                 dot += v.ps[o] * qv;
             }
         } else {
+            FxFields fd{{odd ? v.p2 : v.p, odd ? v.ps2 : v.ps}, {v.q, v.qs}, {v.r, v.rs}, {pk, psk}, beta,
+                        persistent_stage_smem, &st->fault};
             for (int u = blockIdx.x; u < units; u += G) {
                 const int bx = u % gx, by = (u / gx) % gy, bz = u / (gx * gy);
                 const int kz0 = 1 + bz * kz_per;
-                dot += fx_march<2, true>(fl, nullptr, n, sigma, bx, by, kz0, min(kz0 + kz_per, n));
+                dot += fx_march<2, true, true, true>(fd, nullptr, n, sigma, bx, by, kz0, min(kz0 + kz_per, n));
             }
         }
         dot = block_sum(dot, sh);
@@ -280,15 +303,34 @@ bicg_persistent_kernel(BicgVectors v, size_t len, int n, int sigma, int gx, int 
         alpha = rho / sigma_s;
         // phase B: x += alpha p; r -= alpha q; r* -= alpha q*; (r*, r), (r, r)
         double vr = 0.0, vrr = 0.0;
+        const double* const pcur = kPointwise ? v.p : pk;
+        bool twin = true;   // as in bicg_update_kernel: vr == vrr so far
         for (size_t t = (size_t)blockIdx.x * nthreads + tid; t < len; t += (size_t)G * nthreads) {
-            v.x[t] = v.x[t] + alpha * v.p[t];
-            const double rn = v.r[t] - alpha * v.q[t];
-            const double rsn = v.rs[t] - alpha * v.qs[t];
+            v.x[t] = v.x[t] + alpha * pcur[t];
+            const double rv = v.r[t], qv = v.q[t], rsv = v.rs[t], qsv = v.qs[t];
+            const double rn = rv - alpha * qv;
             v.r[t] = rn;
-            v.rs[t] = rsn;
-            vr += rsn * rn;
-            vrr += rn * rn;
+            if (__double_as_longlong(rsv) == __double_as_longlong(rv) &&
+                __double_as_longlong(qsv) == __double_as_longlong(qv)) {
+                v.rs[t] = rn;
+                if (twin) {
+                    vrr += rn * rn;
+                } else {
+                    vr += rn * rn;
+                    vrr += rn * rn;
+                }
+            } else {
+                if (twin) {
+                    vr = vrr;
+                    twin = false;
+                }
+                const double rsn = rsv - alpha * qsv;
+                v.rs[t] = rsn;
+                vr += rsn * rn;
+                vrr += rn * rn;
+            }
         }
+        if (twin) vr = vrr;
         vr = block_sum(vr, sh);
         vrr = block_sum(vrr, sh);
         if (thread0()) {
@@ -311,15 +353,18 @@ bicg_persistent_kernel(BicgVectors v, size_t len, int n, int sigma, int gx, int 
             done = 1;
             break;
         }
-        // phase C: p = r + beta p; p* = r* + beta p*
-        for (size_t t = (size_t)blockIdx.x * nthreads + tid; t < len; t += (size_t)G * nthreads) {
-            v.p[t] = v.r[t] + beta * v.p[t];
-            v.ps[t] = v.rs[t] + beta * v.ps[t];
+        if (kPointwise) {
+            // phase C: p = r + beta p; p* = r* + beta p* (the z-march variant
+            // does this in the next operator phase)
+            for (size_t t = (size_t)blockIdx.x * nthreads + tid; t < len; t += (size_t)G * nthreads) {
+                v.p[t] = v.r[t] + beta * v.p[t];
+                v.ps[t] = v.rs[t] + beta * v.ps[t];
+            }
+            if (!(ok = grid_sync(gb, G))) break;
         }
-        if (!(ok = grid_sync(gb, G))) break;
     }
     if (blockIdx.x == 0 && thread0()) {
-        if (!ok) {
+        if (!ok || *(volatile int*)&st->fault) {
             status = kTimeout;
             done = 1;
         }
@@ -359,6 +404,7 @@ namespace {
 struct StencilGrid {
     dim3 grid, block;
     int kz_per_cta;
+    size_t smem = 0;   // dynamic shared memory per CTA
 };
 
 // Column tiles x z-slabs.  The slab count is chosen so that the CTAs fill
@@ -391,13 +437,28 @@ StencilGrid stencil_grid(int n, int tx, int rows, int per_sm) {
 }
 
 template <typename K>
-int resident_per_sm(K kernel, int threads) {
+int resident_per_sm(K kernel, int threads, size_t smem = 0) {
     int v = 0;
-    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&v, kernel, threads, 0) != cudaSuccess) {
+    if (smem > 0 &&
+        cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) != cudaSuccess) {
+        cudaGetLastError();
+        return 1;
+    }
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&v, kernel, threads, smem) != cudaSuccess) {
         cudaGetLastError();
         v = 1;
     }
     return v > 0 ? v : 1;
+}
+
+// The staged (bulk-copy) march needs n >= 16 (all copied rows then lie in
+// the array) and 16-byte aligned arrays (the copies start on 16-byte
+// boundaries of the array).
+bool bulk_ok(int n, std::initializer_list<const double*> arrays) {
+    if (n < 16) return false;
+    for (const double* a : arrays)
+        if (((uintptr_t)a & 15u) != 0) return false;
+    return true;
 }
 
 StencilGrid fx_grid(int n, int nf) {
@@ -406,6 +467,24 @@ StencilGrid fx_grid(int n, int nf) {
         if (!occ1) occ1 = resident_per_sm(stencil_fx_kernel<1, false>, FX_NT);
         StencilGrid g = stencil_grid(n, FX_TX, FX_OY, occ1);
         g.block = dim3(FX_TX, FX_TY, 1);
+        return g;
+    }
+    if (nf == 3) {
+        static int occ3 = 0;
+        if (!occ3) occ3 = resident_per_sm(stencil_fx_kernel<2, true, true>, FX_NT);
+        StencilGrid g = stencil_grid(n, FX_TX, FX_OY, occ3);
+        g.block = dim3(FX_TX, FX_TY, 1);
+        return g;
+    }
+    if (nf == 4 || nf == 5) {   // staged loads: pair (4), pair with directions (5)
+        static int occ4 = 0, occ5 = 0;
+        const size_t smem4 = fx_stage_bytes<2, fx_stages(false)>();
+        const size_t smem5 = fx_stage_bytes<4, fx_stages(true)>();
+        if (nf == 4 && !occ4) occ4 = resident_per_sm(stencil_fx_kernel<2, true, false, true>, FX_NT, smem4);
+        if (nf == 5 && !occ5) occ5 = resident_per_sm(stencil_fx_kernel<2, true, true, true>, FX_NT, smem5);
+        StencilGrid g = stencil_grid(n, FX_TX, FX_OY, nf == 4 ? occ4 : occ5);
+        g.block = dim3(FX_TX, FX_TY, 1);
+        g.smem = nf == 4 ? smem4 : smem5;
         return g;
     }
     if (!occ2) occ2 = resident_per_sm(stencil_fx_kernel<2, true>, FX_NT);
@@ -425,8 +504,12 @@ StencilGrid f64_grid(int n) {
 }  // namespace
 
 int stencil_cta_count(int n) {
-    const StencilGrid g = fx_grid(n, 2);
-    return (int)(g.grid.x * g.grid.y * g.grid.z);
+    unsigned most = 0;
+    for (int nf = 2; nf <= 5; ++nf) {
+        const StencilGrid g = fx_grid(n, nf);
+        most = max(most, g.grid.x * g.grid.y * g.grid.z);
+    }
+    return (int)most;
 }
 
 cudaError_t launch_stencil(const double* u, double* y, const double* b, int n, int bc_kind,
@@ -442,7 +525,7 @@ cudaError_t launch_stencil(const double* u, double* y, const double* b, int n, i
         // A^T u == A u bit for bit in integer arithmetic (see above)
         (void)transpose;
         const StencilGrid g = fx_grid(n, 1);
-        FxFields fl{{u, nullptr}, {y, nullptr}};
+        FxFields fl{{u, nullptr}, {y, nullptr}, {nullptr, nullptr}, {nullptr, nullptr}, 0.0};
         stencil_fx_kernel<1, false><<<g.grid, g.block, 0, s>>>(fl, b, n, bc_kind == 1 ? 1 : -1, g.kz_per_cta,
                                                                skip, nullptr, nullptr);
     }
@@ -451,18 +534,22 @@ cudaError_t launch_stencil(const double* u, double* y, const double* b, int n, i
 
 constexpr int kPointwiseMaxN = 40;   // per-node operator on grids up to 40^3
 
+// dynamic shared memory of the z-march variant: the staged loads of the
+// operator phase with the direction update fused in
+size_t persistent_stage_bytes() { return fx_stage_bytes<4, fx_stages(true)>(); }
+
 int persistent_grid(int n, int* gx, int* gy, int* slabs, int* kz_per) {
     static int occ_pt = 0, occ_mz = 0;
     if (!occ_pt) {
         occ_pt = resident_per_sm(bicg_persistent_kernel<true>, FX_NT);
-        occ_mz = resident_per_sm(bicg_persistent_kernel<false>, FX_NT);
+        occ_mz = resident_per_sm(bicg_persistent_kernel<false>, FX_NT, persistent_stage_bytes());
         if (occ_pt > 2) occ_pt = 2;
         if (occ_mz > 2) occ_mz = 2;
     }
     const int m = n - 1;
     *gx = (m + FX_TX - 1) / FX_TX;
     *gy = (m + FX_OY - 1) / FX_OY;
-    *kz_per = m < 8 ? m : 4;
+    *kz_per = m < 8 ? m : (n <= 64 ? 4 : 8);
     *slabs = (m + *kz_per - 1) / *kz_per;
     if (n > kPointwiseMaxN) return 152 * occ_mz;
     // one CTA per ~256 interior nodes, at most every resident slot: fewer
@@ -474,29 +561,56 @@ int persistent_grid(int n, int* gx, int* gy, int* slabs, int* kz_per) {
     return (int)want;
 }
 
-cudaError_t launch_bicg_persistent(double* x, double* r, double* rs, double* p, double* ps, double* q, double* qs,
-                                   int n, int bc_kind, int iters, double* partials, BicgState* st,
-                                   unsigned int* barrier_words, cudaStream_t s) {
+bool persistent_pointwise(int n) { return n <= kPointwiseMaxN; }
+
+cudaError_t launch_bicg_persistent(double* x, double* r, double* rs, double* p, double* ps, double* p2, double* ps2,
+                                   double* q, double* qs, int n, int bc_kind, int iters, double* partials,
+                                   BicgState* st, unsigned int* barrier_words, cudaStream_t s) {
     int gx, gy, slabs, kz_per;
     const int G = persistent_grid(n, &gx, &gy, &slabs, &kz_per);
     cudaError_t e = cudaMemsetAsync(barrier_words, 0, 3 * sizeof(unsigned int), s);
     if (e != cudaSuccess) return e;
-    BicgVectors v{x, r, rs, p, ps, q, qs};
+    BicgVectors v{x, r, rs, p, ps, p2, ps2, q, qs};
     size_t len = node_count(n);
     int sigma = bc_kind == 1 ? 1 : -1;
     GridBarrier gb{barrier_words, barrier_words + 1, (int*)(barrier_words + 2)};
     void* args[] = {&v, &len, &n, &sigma, &gx, &gy, &slabs, &kz_per, &iters, &partials, &st, &gb};
-    const void* fn = n <= kPointwiseMaxN ? (const void*)bicg_persistent_kernel<true>
-                                         : (const void*)bicg_persistent_kernel<false>;
-    return cudaLaunchCooperativeKernel(fn, dim3(G), dim3(FX_TX, FX_TY, 1), args, 0, s);
+    const bool pw = persistent_pointwise(n);
+    const void* fn = pw ? (const void*)bicg_persistent_kernel<true> : (const void*)bicg_persistent_kernel<false>;
+    return cudaLaunchCooperativeKernel(fn, dim3(G), dim3(FX_TX, FX_TY, 1), args, pw ? 0 : persistent_stage_bytes(),
+                                       s);
+}
+
+cudaError_t launch_bicg_stencil_pair_dir(const double* r, const double* rs, const double* p_prev,
+                                         const double* ps_prev, double* p, double* ps, double* q, double* qs, int n,
+                                         int bc_kind, double* partials, BicgState* st, cudaStream_t s) {
+    FxFields fl{{p_prev, ps_prev}, {q, qs}, {r, rs}, {p, ps}, 0.0, nullptr, nullptr};
+    const int sg = bc_kind == 1 ? 1 : -1;
+    if (bulk_ok(n, {r, rs, p_prev, ps_prev})) {
+        const StencilGrid g = fx_grid(n, 5);
+        stencil_fx_kernel<2, true, true, true><<<g.grid, g.block, g.smem, s>>>(fl, nullptr, n, sg, g.kz_per_cta,
+                                                                               &st->done, partials, st);
+    } else {
+        const StencilGrid g = fx_grid(n, 3);
+        stencil_fx_kernel<2, true, true><<<g.grid, g.block, 0, s>>>(fl, nullptr, n, sg, g.kz_per_cta, &st->done,
+                                                                    partials, st);
+    }
+    return cudaGetLastError();
 }
 
 cudaError_t launch_bicg_stencil_pair(const double* p, double* q, const double* ps, double* qs, int n,
                                      int bc_kind, double* partials, BicgState* st, cudaStream_t s) {
-    const StencilGrid g = fx_grid(n, 2);
-    FxFields fl{{p, ps}, {q, qs}};
-    stencil_fx_kernel<2, true><<<g.grid, g.block, 0, s>>>(fl, nullptr, n, bc_kind == 1 ? 1 : -1, g.kz_per_cta,
-                                                          &st->done, partials, st);
+    FxFields fl{{p, ps}, {q, qs}, {nullptr, nullptr}, {nullptr, nullptr}, 0.0, nullptr, nullptr};
+    const int sg = bc_kind == 1 ? 1 : -1;
+    if (bulk_ok(n, {p, ps})) {
+        const StencilGrid g = fx_grid(n, 4);
+        stencil_fx_kernel<2, true, false, true><<<g.grid, g.block, g.smem, s>>>(fl, nullptr, n, sg, g.kz_per_cta,
+                                                                                &st->done, partials, st);
+    } else {
+        const StencilGrid g = fx_grid(n, 2);
+        stencil_fx_kernel<2, true><<<g.grid, g.block, 0, s>>>(fl, nullptr, n, sg, g.kz_per_cta, &st->done,
+                                                              partials, st);
+    }
     return cudaGetLastError();
 }
 

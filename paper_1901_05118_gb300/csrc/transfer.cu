@@ -53,8 +53,12 @@ __global__ void exp_finite_w_kernel(double* __restrict__ W, const double* __rest
         for (int b = 0; b < nj; ++b)
             for (int a = 0; a < ni; ++a)
                 sum += u1[nidx(np1, 2 * ci[a], 2 * cj[b], 2 * ck[c])] - u0[nidx(np0, ci[a], cj[b], ck[c])];
-    const double cnt = (double)(ni * nj * nk);
-    W[nidx(np1, i, j, k)] = u1[nidx(np1, i, j, k)] + sum / (4.0 * cnt);
+    // 1/(4 * 2^m), m = number of odd coordinates: a power of two, so the
+    // product is exact; an FP64 division would cost many of GB300's scarce
+    // FP64 instructions per node
+    const int m = (i & 1) + (j & 1) + (k & 1);
+    const double w = m == 0 ? 0.25 : (m == 1 ? 0.125 : (m == 2 ? 0.0625 : 0.03125));
+    W[nidx(np1, i, j, k)] = u1[nidx(np1, i, j, k)] + sum * w;
 }
 
 // Lagrange weights on the cell's middle-grid nodes for local offset o (0..4)
@@ -113,8 +117,11 @@ __global__ void exp_true_kernel(double* __restrict__ ut, const double* __restric
         for (int b = 0; b < nj; ++b)
             for (int a = 0; a < ni; ++a)
                 sum += uh[nidx(np, 2 * ci[a], 2 * cj[b], 2 * ck[c])] - u2h[nidx(npc, ci[a], cj[b], ck[c])];
-    const double cnt = (double)(ni * nj * nk);
-    ut[nidx(np, i, j, k)] = uh[nidx(np, i, j, k)] + sum / (3.0 * cnt);
+    // weight 1/(3 * 2^m), m = number of odd coordinates (one table load
+    // instead of an FP64 division per node)
+    const int m = (i & 1) + (j & 1) + (k & 1);
+    const double w = m == 0 ? 1.0 / 3.0 : (m == 1 ? 1.0 / 6.0 : (m == 2 ? 1.0 / 12.0 : 1.0 / 24.0));
+    ut[nidx(np, i, j, k)] = uh[nidx(np, i, j, k)] + sum * w;
 }
 
 }  // namespace

@@ -32,6 +32,31 @@ dot_kernel(const double* __restrict__ a, const double* __restrict__ b, size_t le
     }
 }
 
+// (a, a) over the unknowns (interior nodes) of a grid with n intervals:
+// for caller-supplied vectors whose boundary entries need not be zero.
+__global__ void __launch_bounds__(kVecThreads)
+interior_dot_kernel(const double* __restrict__ a, int n, double* partials, unsigned int* ticket, double* out) {
+    __shared__ double sh[32];
+    __shared__ bool am_last;
+    const long long m = n - 1, np = n + 1;
+    const long long pts = m * m * m;
+    double v = 0.0;
+    for (long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x; t < pts;
+         t += (long long)gridDim.x * blockDim.x) {
+        const long long i = t % m + 1, j = (t / m) % m + 1, k = t / (m * m) + 1;
+        const double x = a[(k * np + j) * np + i];
+        v += x * x;
+    }
+    double s = block_sum(v, sh);
+    if (publish_partials(&s, 1, partials, ticket, &am_last)) {
+        const double tot = gather_partials(partials, 0, sh);
+        if (thread0()) {
+            *out = tot;
+            *ticket = 0;
+        }
+    }
+}
+
 // r*_0 = shadow (or r_0), p_0 = r_0, p*_0 = r*_0; rho_0 = (r*_0, r_0),
 // rr = (r_0, r_0).
 __global__ void __launch_bounds__(kVecThreads)
@@ -189,6 +214,12 @@ bicg_pupdate_kernel(double* __restrict__ p, const double* __restrict__ r, double
 cudaError_t launch_dot(const double* a, const double* b, size_t len, double* partials,
                        unsigned int* ticket, double* out, cudaStream_t s) {
     dot_kernel<<<kVecBlocks, kVecThreads, 0, s>>>(a, b, len, partials, ticket, out);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_interior_dot(const double* a, int n, double* partials, unsigned int* ticket, double* out,
+                                cudaStream_t s) {
+    interior_dot_kernel<<<kVecBlocks, kVecThreads, 0, s>>>(a, n, partials, ticket, out);
     return cudaGetLastError();
 }
 

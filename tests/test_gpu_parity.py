@@ -198,6 +198,33 @@ def test_bicg_is_deterministic():
     assert r1 == r2 and torch.equal(x1, x2)
 
 
+@pytest.mark.parametrize("n,bc_kind", [(138, 1), (133, 2)])
+def test_bicg_large_grid_fixed_iterations(n, bc_kind):
+    """Grids above 128^3 run the launched path, whose operator launch also
+    forms the new directions p, p* (ragged tiles in x, y and z here): 20
+    iterations of Alg. 2 against the oracle's 20, iterates entry by entry."""
+    b = P.random_field(n, 81)
+    x0 = P.random_field(n, 82) * 0.1
+    lvl = level(n, bc_kind)
+    x = dev(x0)
+    it, rel, rc = B.bicg_solve(lvl, dev(b), x, 0.0, 20)
+    xr, itr, relr, rcr = oracle.bicg(n, bc_kind, b, x0, 0.0, max_iter=20)
+    assert it == itr == 20
+    assert rel == pytest.approx(relr, rel=1e-8)
+    assert rel_max(host(x), xr) <= 1e-10
+
+
+def test_bicg_large_grid_is_deterministic():
+    n = 144
+    b = dev(P.random_field(n, 83))
+    x1 = torch.zeros((n + 1,) * 3, dtype=torch.float64, device=DEV)
+    x2 = torch.zeros_like(x1)
+    lvl = level(n, 1)
+    r1 = B.bicg_solve(lvl, b, x1, 0.0, 37)
+    r2 = B.bicg_solve(lvl, b, x2, 0.0, 37)
+    assert r1 == r2 and torch.equal(x1, x2)
+
+
 # ---------------------------------------------------------- full solve
 @pytest.mark.parametrize("name,bc_kind,variant", [("sin_pi", 1, "exact"), ("exp_sum", 1, "exact"),
                                                    ("exp_sum", 2, "exact"), ("paper_p4", 1, "exact"),
@@ -253,6 +280,26 @@ def test_excmg_paper_table_rows_64():
         assert linf == pytest.approx(gold[name]["rows"]["64"]["linf"], rel=0.006)
 
 
+def test_excmg_paper_table_rows_full_size():
+    """Table 1 rows at 256^3 and 512^3 (the full-size workload) through the
+    GPU path: the printed error norms of u_h to their three digits."""
+    import json
+    import os
+    gold = json.load(open(os.path.join(os.path.dirname(__file__), "golden", "paper_tables.json")))["problems"]
+    prob = P.by_name("paper_p1")
+    for n in (256, 512):
+        f, g1, g2 = prob.data(n, 1)
+        uh = torch.empty((n + 1,) * 3, dtype=torch.float64, device=DEV)
+        B.excmg_solve(n, 8, 1, dev(f), dev(g1), dev(g2), 1e-11, u_h_out=uh)
+        del f, g1, g2
+        e = host(uh) - prob.exact(n)
+        del uh
+        l2 = np.sqrt((e ** 2).mean())
+        linf = np.abs(e).max()
+        assert l2 == pytest.approx(gold["paper_p1"]["rows"][str(n)]["l2"], rel=0.006)
+        assert linf == pytest.approx(gold["paper_p1"]["rows"][str(n)]["linf"], rel=0.006)
+
+
 # ------------------------------------------------------------ errors
 def test_bad_arguments_raise():
     lvl = B.Level(8, 1)
@@ -301,14 +348,25 @@ def test_mixed_precision_exact_polynomial():
     assert np.abs(host(ut) - prob.exact(n)).max() <= 1e-11
 
 
-@pytest.mark.parametrize("n,bc_kind", [(20, 1), (80, 2)])
-def test_bicg_with_chosen_shadow(n, bc_kind):
+def chosen_shadow(b, n, kind):
+    """r*_0 for the tests of Alg. 2 with r*_0 != r_0 (x_0 = 0, so r_0 = b):
+    an unrelated random field, or r_0 perturbed by 1 % entry by entry.  The
+    perturbed one keeps the two-sided recurrences far from breakdown, so
+    rounding differences stay small and iterates can be compared tightly;
+    with an unrelated field the iteration count swings by tens of percent
+    with rounding alone."""
+    noise = P.random_field(n, 52)
+    return noise if kind == "random" else b * (1.0 + 0.01 * noise)
+
+
+@pytest.mark.parametrize("n,bc_kind,kind", [(20, 1, "random"), (80, 2, "perturbed")])
+def test_bicg_with_chosen_shadow(n, bc_kind, kind):
     """Alg. 2 with r*_0 != r_0: the shadow sequence now differs from the
-    primal one, so A^T p* is applied to a different vector (on 80^3 by the
-    fused z-march's general path, on 20^3 by the cooperative small-grid
-    kernel)."""
+    primal one, so A^T p* is applied to a different vector (both grids run
+    in the cooperative small-grid kernel: per node on 20^3, staged z-march
+    with the direction update folded in on 80^3)."""
     b = P.random_field(n, 51)
-    shadow = P.random_field(n, 52)
+    shadow = chosen_shadow(b, n, kind)
     lvl = level(n, bc_kind)
     x = torch.zeros((n + 1,) * 3, dtype=torch.float64, device=DEV)
     it, rel, rc = B.bicg_solve(lvl, dev(b), x, 1e-11, 20000, shadow=dev(shadow))
@@ -316,3 +374,19 @@ def test_bicg_with_chosen_shadow(n, bc_kind):
     assert rc == 0 and rcr == 0 and rel <= 1e-11
     assert abs(it - itr) <= max(3, 0.05 * itr)
     assert rel_max(host(x), xr) <= 1e-8
+
+
+def test_bicg_with_chosen_shadow_large_grid_fixed_iterations():
+    """The launched (non-cooperative) path on a grid above 128^3 with a
+    differing shadow: 20 iterations of Alg. 2 on both sides, iterates
+    compared entry by entry."""
+    n, bc_kind = 132, 2
+    b = P.random_field(n, 71)
+    shadow = chosen_shadow(b, n, "perturbed")
+    lvl = level(n, bc_kind)
+    x = torch.zeros((n + 1,) * 3, dtype=torch.float64, device=DEV)
+    it, rel, rc = B.bicg_solve(lvl, dev(b), x, 0.0, 20, shadow=dev(shadow))
+    xr, itr, relr, rcr = oracle.bicg(n, bc_kind, b, np.zeros_like(b), 0.0, max_iter=20, shadow=shadow)
+    assert it == itr == 20
+    assert rel == pytest.approx(relr, rel=1e-8)
+    assert rel_max(host(x), xr) <= 1e-10
