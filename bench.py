@@ -58,6 +58,7 @@ def parse():
     ap.add_argument("--no-batch", action="store_true", help="skip the 64-instance batched leg")
     ap.add_argument("--no-serve", action="store_true", help="skip the request-stream leg")
     ap.add_argument("--serve-requests", type=int, default=120)
+    ap.add_argument("--no-elided", action="store_true", help="skip the shadow-elided variant leg")
     ap.add_argument("--serve-precision", choices=["fp64", "mixed"], default="fp64")
     ap.add_argument("--oracle-report", action="store_true",
                     help="time the CPU oracle on the small workload and one 512^3 operator application, then exit")
@@ -209,6 +210,39 @@ def config(args):
 
 
 # --------------------------------------------------------------- GPU arm
+def _cpulist(text):
+    cpus = set()
+    for part in text.strip().split(","):
+        if not part:
+            continue
+        lo, _, hi = part.partition("-")
+        cpus.update(range(int(lo), int(hi or lo) + 1))
+    return cpus
+
+
+def bind_host_to_gpu_numa(dev_index):
+    """Run this process on the CPUs of the GPU's NUMA node, so that the pinned
+    host buffers of the end-to-end leg (placed by first touch) sit next to the
+    GPU's host link, as `numactl --cpunodebind` would.  Returns what was done,
+    or None where the system does not say which node that is."""
+    import torch
+
+    try:
+        p = torch.cuda.get_device_properties(dev_index)
+        bdf = f"{p.pci_domain_id:04x}:{p.pci_bus_id:02x}:{p.pci_device_id:02x}.0"
+        node = int(open(f"/sys/bus/pci/devices/{bdf}/numa_node").read())
+        if node < 0:
+            return None
+        cpus = _cpulist(open(f"/sys/devices/system/node/node{node}/cpulist").read())
+        cpus &= os.sched_getaffinity(0)
+        if not cpus:
+            return None
+        os.sched_setaffinity(0, cpus)
+        return {"numa_node": node, "cpus": len(cpus)}
+    except (OSError, ValueError, AttributeError):
+        return None
+
+
 def run_ours(args):
     import torch
     import torch.distributed as dist
@@ -221,6 +255,7 @@ def run_ours(args):
 
     from paper_1901_05118_gb300 import binding as B, problems
 
+    host_binding = bind_host_to_gpu_numa(local)
     n, nc = args.n, args.nc
     prob = problems.exp_sum()
     bcs = (1, 2)
@@ -309,7 +344,8 @@ def run_ours(args):
         ns = args.steps * len(bcs)
         e2e = {"value": seconds_per_solve(ms_e2e, len(bcs), world), "unit": "s",
                "h2d_bytes_per_step": h2d * len(bcs), "d2h_bytes_per_step": d2h * len(bcs),
-               "per_solve_ms": {"h2d": h2d_ms / ns, "solve": solve_ms / ns, "d2h": d2h_ms / ns}}
+               "per_solve_ms": {"h2d": h2d_ms / ns, "solve": solve_ms / ns, "d2h": d2h_ms / ns},
+               "host_binding": host_binding}
 
     # ---- roofline of the operator kernel on the finest grid
     peaks = {}
@@ -332,6 +368,10 @@ def run_ours(args):
                 "launches": st_cnt, "avg_ms": avg_ms, "bytes_per_launch": bytes_per_launch,
                 "peak_source": "MEASURED_PEAKS.json hbm_gbs (of measured)"}
 
+    elided = None
+    if not args.no_elided:
+        elided = elided_leg(args, B, lambda bc: solve(bc), d, dev, stream, barrier, world)
+
     mixed = None
     if not args.no_mixed:
         mixed = precision_leg(args, B, problems, ctx, dev, stream, barrier, world)
@@ -350,8 +390,8 @@ def run_ours(args):
             "e2e": e2e, "gpu_launches": launches, "roofline": roofline, "clocks": clk.summary(),
             "levels": {str(bc): [{"n": s["n"], "iters": s["iters"], "ms": round(s["ms"], 3),
                                   "relres": s["relres"]} for s in stats[bc]] for bc in bcs},
-            "work_units": {str(bc): round(w, 2) for bc, w in wu.items()}, "precision_leg": mixed,
-            "batched_leg": batched, "serving_leg": served}
+            "work_units": {str(bc): round(w, 2) for bc, w in wu.items()}, "shadow_elided_leg": elided,
+            "precision_leg": mixed, "batched_leg": batched, "serving_leg": served}
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         cpu_value, info = oracle_sample(n, nc, bcs, wu)
         info["value"] = cpu_value
@@ -361,6 +401,37 @@ def run_ours(args):
         print(json.dumps(line), flush=True)
     if world > 1:
         dist.destroy_process_group()
+
+
+def elided_leg(args, B, solve_full, d, dev, stream, barrier, world):
+    """The headline workload with the shadow-elided Bi-CG, a labelled
+    variant that is not the paper's Alg. 2 as printed: r*, p* and A^T p*
+    (bit for bit r, p and A p here) are not stored.  Reports seconds per solve
+    and whether every result equals the full mode's bit for bit."""
+    import torch
+
+    n, nc, bcs = args.n, args.nc, (1, 2)
+    ctx_e = B.Context(dev)
+    ctx_e.set_stencil(args.stencil)
+    ctx_e.set_shadow_mode("elided")
+    u_e = torch.empty((n + 1,) * 3, dtype=torch.float64, device=dev)
+    same = True
+    for bc in bcs:
+        u_full = solve_full(bc).clone()
+        B.excmg_solve(n, nc, bc, d["f"], d["g1"], d[f"g2_{bc}"], args.tol, u_e, ctx=ctx_e)   # warm-up
+        same = same and bool(torch.equal(u_full, u_e))
+        del u_full
+    barrier()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    for _ in range(args.steps):
+        for bc in bcs:
+            B.excmg_solve(n, nc, bc, d["f"], d["g1"], d[f"g2_{bc}"], args.tol, u_e, ctx=ctx_e)
+    e1.record(stream)
+    barrier()
+    ms = max_over_ranks(e0.elapsed_time(e1) / args.steps, world, dev)
+    return {"label": "non-paper variant: shadow sequence of Alg. 2 not stored (equal to the primal one bit for bit)",
+            "value": seconds_per_solve(ms, len(bcs), world), "unit": "s", "bitwise_equal_to_full": same}
 
 
 def precision_leg(args, B, problems, ctx, dev, stream, barrier, world):

@@ -108,6 +108,22 @@ size_t excmg_ctx_bytes(const excmg_ctx *ctx);
  * Both give results within 1e-13 relative of each other on the same input. */
 enum { EXCMG_STENCIL_EXACT = 0, EXCMG_STENCIL_FP64 = 1 };
 int excmg_ctx_set_stencil(excmg_ctx *ctx, int variant);
+
+/* Shadow sequence of Bi-CG (Alg. 2) on this context.
+ * EXCMG_SHADOW_FULL (default): r*, p* and A^T p* are carried in memory as
+ *   Alg. 2 prints them.
+ * EXCMG_SHADOW_ELIDED -- not the paper's algorithm as printed, a labelled
+ *   variant: A_h is symmetric, and with r*_0 = r_0 and the exact operator
+ *   (EXCMG_STENCIL_EXACT) A^T p* and A p are the same bits, so the shadow
+ *   sequence equals the primal one bit for bit; it is then neither stored
+ *   nor read (80 instead of 136 bytes per unknown and iteration on large
+ *   grids) and every iterate, stopping decision and result is bit for bit
+ *   that of EXCMG_SHADOW_FULL.  It applies to the exact operator only: with
+ *   EXCMG_STENCIL_FP64, and in calls that pass their own r*_0
+ *   (bicg_solve_ex), the full sequence runs.  The batch engine always runs
+ *   the full sequence. */
+enum { EXCMG_SHADOW_FULL = 0, EXCMG_SHADOW_ELIDED = 1 };
+int excmg_ctx_set_shadow_mode(excmg_ctx *ctx, int mode);
 const char *excmg_last_error(const excmg_ctx *ctx);
 
 /* Instrumentation.  excmg_launch_count: kernel launches the library has

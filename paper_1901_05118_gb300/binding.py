@@ -31,6 +31,7 @@ STATUS_NAMES = {0: "EXCMG_OK", -1: "EXCMG_ERR_ARG", -2: "EXCMG_ERR_OOM", -3: "EX
                 -7: "EXCMG_ERR_TIMEOUT", -9: "EXCMG_ERR_BUDGET", -10: "EXCMG_ERR_SIZE"}
 TOL_MODES = {"paper": 0, "uniform": 1}
 STENCIL_VARIANTS = {"exact": 0, "fp64": 1}
+SHADOW_MODES = {"full": 0, "elided": 1}
 PRECISIONS = {"fp64": 0, "mixed": 1}
 MIXED_INNER_CAP = 500      # iterations of one FP32 correction solve
 MIXED_INNER_TOL = 1e-4     # residual reduction asked of one FP32 correction solve
@@ -67,6 +68,7 @@ _lib.excmg_ctx_destroy.argtypes = [_vp]
 _lib.excmg_ctx_bytes.argtypes = [_vp]
 _lib.excmg_ctx_bytes.restype = _sz
 _lib.excmg_ctx_set_stencil.argtypes = [_vp, _i]
+_lib.excmg_ctx_set_shadow_mode.argtypes = [_vp, _i]
 _lib.excmg_launch_count.argtypes = []
 _lib.excmg_launch_count.restype = ctypes.c_longlong
 _lib.excmg_ctx_profile.argtypes = [_vp, _i]
@@ -109,7 +111,8 @@ for _name in ("excmg_batch_create", "excmg_batch_destroy", "excmg_batch_submit",
               "excmg_batch_query"):
     getattr(_lib, _name).restype = _i
 
-for _name in ("excmg_ctx_create", "excmg_ctx_destroy", "excmg_ctx_set_stencil", "excmg_ctx_profile",
+for _name in ("excmg_ctx_create", "excmg_ctx_destroy", "excmg_ctx_set_stencil", "excmg_ctx_set_shadow_mode",
+              "excmg_ctx_profile",
               "excmg_ctx_profile_read", "excmg_level_create", "excmg_level_destroy",
               "stencil_apply", "bicg_solve", "bicg_solve_ex", "extrapolate_interpolate", "extrapolate_interpolate_ex",
               "midpoint_extrapolate", "midpoint_extrapolate_ex", "excmg_solve", "excmg_solve_ex",
@@ -171,6 +174,13 @@ class Context:
     def set_stencil(self, variant: str):
         """'exact' (integer accumulation, default) or 'fp64' arithmetic for the operator."""
         self.check(_lib.excmg_ctx_set_stencil(self.handle, STENCIL_VARIANTS[variant]), "excmg_ctx_set_stencil")
+
+    def set_shadow_mode(self, mode: str):
+        """'full' (default: Alg. 2 with r*, p*, A^T p* in memory) or 'elided'
+        (a labelled variant, not the paper's algorithm as printed: the shadow
+        sequence, bit for bit the primal one with the exact operator, is not
+        stored; results are the same bits)."""
+        self.check(_lib.excmg_ctx_set_shadow_mode(self.handle, SHADOW_MODES[mode]), "excmg_ctx_set_shadow_mode")
 
     def profile(self, enable: bool = True):
         """Time every operator launch inside Bi-CG (CUDA events on this context's stream)."""

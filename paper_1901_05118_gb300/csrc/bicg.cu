@@ -56,12 +56,17 @@ int bicg_run(excmg_ctx* ctx, int n, int bc_kind, const double* b, double* x, dou
     const size_t len = node_count(n);
     const size_t bytes = len * sizeof(double);
     int st = EXCMG_OK;
+    // shadow-elided mode (a labelled variant, not Alg. 2 as printed): with
+    // r*_0 = r_0 and the integer operator the shadow vectors are the primal
+    // ones bit for bit, so they are neither stored nor read
+    const bool elide =
+        ctx->shadow_mode == EXCMG_SHADOW_ELIDED && shadow == nullptr && ctx->stencil_variant == kStencilExact;
     double* r = ctx_buffer(ctx, "bicg_r", bytes, &st);
-    double* rs = st ? nullptr : ctx_buffer(ctx, "bicg_rs", bytes, &st);
+    double* rs = (st || elide) ? nullptr : ctx_buffer(ctx, "bicg_rs", bytes, &st);
     double* p = st ? nullptr : ctx_buffer(ctx, "bicg_p", bytes, &st);
-    double* ps = st ? nullptr : ctx_buffer(ctx, "bicg_ps", bytes, &st);
+    double* ps = (st || elide) ? nullptr : ctx_buffer(ctx, "bicg_ps", bytes, &st);
     double* q = st ? nullptr : ctx_buffer(ctx, "bicg_q", bytes, &st);
-    double* qs = st ? nullptr : ctx_buffer(ctx, "bicg_qs", bytes, &st);
+    double* qs = (st || elide) ? nullptr : ctx_buffer(ctx, "bicg_qs", bytes, &st);
     if (st) return st;
     // the integer operator has a fused two-field kernel; the FP64 one runs
     // as two applications and a separate inner product
@@ -74,7 +79,7 @@ int bicg_run(excmg_ctx* ctx, int n, int bc_kind, const double* b, double* x, dou
     // (neighbouring blocks still read the old values)
     const bool dir_fused = fused && !(persistent && persistent_pointwise(n));
     double* p2 = dir_fused ? ctx_buffer(ctx, "bicg_p2", bytes, &st) : nullptr;
-    double* ps2 = (dir_fused && !st) ? ctx_buffer(ctx, "bicg_ps2", bytes, &st) : nullptr;
+    double* ps2 = (dir_fused && !elide && !st) ? ctx_buffer(ctx, "bicg_ps2", bytes, &st) : nullptr;
     if (st) return st;
     cudaStream_t s = ctx->stream;
     if (check_every < 1) check_every = 1;
@@ -89,18 +94,20 @@ int bicg_run(excmg_ctx* ctx, int n, int bc_kind, const double* b, double* x, dou
     // interior entries only
     if (e == cudaSuccess) e = cudaMemsetAsync(r, 0, bytes, s);
     if (e == cudaSuccess) e = cudaMemsetAsync(q, 0, bytes, s);
-    if (e == cudaSuccess) e = cudaMemsetAsync(qs, 0, bytes, s);
+    if (e == cudaSuccess && !elide) e = cudaMemsetAsync(qs, 0, bytes, s);
     // r_0 = b - A x_0; r*_0 = p_0 = p*_0 = r_0; rho_0
     if (e == cudaSuccess) e = launch_stencil(x, r, b, n, bc_kind, false, nullptr, s, ctx->stencil_variant);
-    if (e == cudaSuccess) e = launch_bicg_init(r, shadow, rs, p, ps, len, ctx->partials, ctx->state, s);
+    if (e == cudaSuccess)
+        e = elide ? launch_cg_init(r, p, len, ctx->partials, ctx->state, s)
+                  : launch_bicg_init(r, shadow, rs, p, ps, len, ctx->partials, ctx->state, s);
     // a caller's shadow may carry values on boundary nodes: the work vectors
     // keep zeros there
     if (e == cudaSuccess && shadow) e = launch_zero_boundary(rs, n, s);
     if (e == cudaSuccess && shadow) e = launch_zero_boundary(ps, n, s);
     if (e == cudaSuccess && dir_fused) e = launch_zero_boundary(p2, n, s);
-    if (e == cudaSuccess && dir_fused) e = launch_zero_boundary(ps2, n, s);
+    if (e == cudaSuccess && dir_fused && !elide) e = launch_zero_boundary(ps2, n, s);
     if (e != cudaSuccess) return ctx_cuda(ctx, e, "Bi-CG setup");
-    note_launches(dir_fused ? 2 : 0);
+    note_launches(dir_fused ? (elide ? 1 : 2) : 0);
 
     const int* done = &ctx->state->done;
     if (persistent) {
@@ -113,7 +120,7 @@ int bicg_run(excmg_ctx* ctx, int n, int bc_kind, const double* b, double* x, dou
             const int left = max_iter - ctx->host_state->iter;
             if (chunk > left) chunk = left;
             e = launch_bicg_persistent(x, r, rs, p, ps, p2, ps2, q, qs, n, bc_kind, chunk, ctx->partials, ctx->state,
-                                       ctx->barrier, s);
+                                       ctx->barrier, s, elide);
             note_launches(1);
             if (e != cudaSuccess) return ctx_cuda(ctx, e, "cooperative Bi-CG launch");
         }
@@ -167,14 +174,18 @@ int bicg_run(excmg_ctx* ctx, int n, int bc_kind, const double* b, double* x, dou
                 // from the second iteration on the launch first forms
                 // p_k = r_k + beta_{k-1} p_{k-1} (and p*_k) on the fly
                 if (enqueued == 0) {
-                    e = launch_bicg_stencil_pair(pc, q, psc, qs, n, bc_kind, ctx->partials, ctx->state, s);
-                    launch_bytes[it] = 32.0 * unknowns;   // p, p* in; q, q* out
+                    e = elide ? launch_cg_stencil(pc, q, n, bc_kind, ctx->partials, ctx->state, s)
+                              : launch_bicg_stencil_pair(pc, q, psc, qs, n, bc_kind, ctx->partials, ctx->state, s);
+                    // p (, p*) in; q (, q*) out
+                    launch_bytes[it] = (elide ? 16.0 : 32.0) * unknowns;
                 } else {
-                    e = launch_bicg_stencil_pair_dir(r, rs, pc, psc, pn, psn, q, qs, n, bc_kind, ctx->partials,
-                                                     ctx->state, s);
+                    e = elide ? launch_cg_stencil_dir(r, pc, pn, q, n, bc_kind, ctx->partials, ctx->state, s)
+                              : launch_bicg_stencil_pair_dir(r, rs, pc, psc, pn, psn, q, qs, n, bc_kind,
+                                                             ctx->partials, ctx->state, s);
                     std::swap(pc, pn);
                     std::swap(psc, psn);
-                    launch_bytes[it] = 64.0 * unknowns;   // r, r*, p, p* in; p, p*, q, q* out
+                    // r (, r*), p_old (, p*_old) in; p (, p*), q (, q*) out
+                    launch_bytes[it] = (elide ? 32.0 : 64.0) * unknowns;
                 }
                 if (ctx->profile) {
                     cudaEventRecord(ctx->prof_events[3 * it + 1], s);
@@ -190,7 +201,8 @@ int bicg_run(excmg_ctx* ctx, int n, int bc_kind, const double* b, double* x, dou
                 if (e == cudaSuccess) e = launch_bicg_sigma(ps, q, len, ctx->partials, ctx->state, s);
             }
             if (e == cudaSuccess)
-                e = launch_bicg_update(x, pc, r, q, rs, qs, len, ctx->partials, ctx->state, s);
+                e = elide ? launch_cg_update(x, pc, r, q, len, ctx->partials, ctx->state, s)
+                          : launch_bicg_update(x, pc, r, q, rs, qs, len, ctx->partials, ctx->state, s);
             if (e == cudaSuccess && !fused) e = launch_bicg_pupdate(p, r, ps, rs, len, ctx->state, s);
             ++enqueued;
         }

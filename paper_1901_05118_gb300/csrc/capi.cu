@@ -144,6 +144,15 @@ int excmg_ctx_set_stencil(excmg_ctx* c, int variant) {
     return EXCMG_OK;
 }
 
+int excmg_ctx_set_shadow_mode(excmg_ctx* c, int mode) {
+    if (!c) c = default_ctx();
+    if (!c) return EXCMG_ERR_CUDA;
+    if (mode != EXCMG_SHADOW_FULL && mode != EXCMG_SHADOW_ELIDED)
+        return ctx_fail(c, EXCMG_ERR_ARG, "unknown shadow mode");
+    c->shadow_mode = mode;
+    return EXCMG_OK;
+}
+
 long long excmg_launch_count(void) { return g_launches.load(); }
 
 int excmg_ctx_profile(excmg_ctx* c, int enable) {

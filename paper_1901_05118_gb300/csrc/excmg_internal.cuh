@@ -73,9 +73,23 @@ cudaError_t launch_bicg_stencil_pair_dir(const double* r, const double* rs, cons
 // entry (iteration k reads p_{k-1} from one pair, writes p_k to the other).
 constexpr int kPersistentMaxN = 128;
 bool persistent_pointwise(int n);
+// elide: the shadow-elided mode (rs, ps, ps2, qs unused, may be null).
 cudaError_t launch_bicg_persistent(double* x, double* r, double* rs, double* p, double* ps, double* p2, double* ps2,
                                    double* q, double* qs, int n, int bc_kind, int iters, double* partials,
-                                   BicgState* st, unsigned int* barrier_words, cudaStream_t s);
+                                   BicgState* st, unsigned int* barrier_words, cudaStream_t s, bool elide);
+// Shadow-elided mode (r* = r, p* = p, A^T p* = A p not stored): the one-field
+// operator launches with sigma = (p, A p) and alpha (the second also forms
+// p = r + beta p_prev into p), and the matching set-up and update kernels.
+// They run on the grids of the two-field kernels, so every sum adds the same
+// partial sums in the same order and the iterates are bit for bit those of
+// the full mode.
+cudaError_t launch_cg_stencil(const double* p, double* q, int n, int bc_kind, double* partials, BicgState* st,
+                              cudaStream_t s);
+cudaError_t launch_cg_stencil_dir(const double* r, const double* p_prev, double* p, double* q, int n, int bc_kind,
+                                  double* partials, BicgState* st, cudaStream_t s);
+cudaError_t launch_cg_init(const double* r, double* p, size_t len, double* partials, BicgState* st, cudaStream_t s);
+cudaError_t launch_cg_update(double* x, const double* p, double* r, const double* q, size_t len, double* partials,
+                             BicgState* st, cudaStream_t s);
 
 // Vectors (flat over all (n+1)^3 entries; boundary entries of the Bi-CG
 // vectors are zero, so flat sums equal sums over the unknowns).
@@ -149,6 +163,7 @@ struct excmg_ctx {
     excmg::BicgState* host_state = nullptr;   // pinned host mirror
     double* host_scalar = nullptr;            // pinned host mirror of `scalar`
     int stencil_variant = excmg::kStencilExact;
+    int shadow_mode = EXCMG_SHADOW_FULL;
     // optional timing of the operator launches inside Bi-CG
     bool profile = false;
     std::vector<cudaEvent_t> prof_events;

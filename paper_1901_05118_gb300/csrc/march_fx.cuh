@@ -149,12 +149,28 @@ __device__ __forceinline__ bool mbar_try_wait(unsigned long long* bar, unsigned 
     return ok != 0;
 }
 
-// Bounded wait for the phase with the given parity; false when it gave up.
-__device__ __forceinline__ bool mbar_wait(unsigned long long* bar, unsigned parity) {
-    for (int spin = 0; spin < (1 << 22); ++spin)
+__device__ __forceinline__ void mbar_inval(unsigned long long* bar) {
+    asm volatile("mbarrier.inval.shared::cta.b64 [%0];" ::"r"(smem_u32(bar)) : "memory");
+}
+
+__device__ __forceinline__ unsigned long long global_ns() {
+    unsigned long long t;
+    asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+    return t;
+}
+
+// Wait for the phase with the given parity for at most limit_ns
+// nanoseconds; false when it gave up.
+__device__ __forceinline__ bool mbar_wait(unsigned long long* bar, unsigned parity, unsigned long long limit_ns) {
+    if (mbar_try_wait(bar, parity)) return true;
+    const unsigned long long t0 = global_ns();
+    do {
         if (mbar_try_wait(bar, parity)) return true;
+    } while (global_ns() - t0 < limit_ns);
     return false;
 }
+constexpr unsigned long long kStageWaitNs = 50000000ull;   // 50 ms: copies take microseconds
+constexpr unsigned long long kStageDrainNs = 1000000ull;   // 1 ms once a wait has given up
 
 __device__ __forceinline__ void bulk_g2s(void* dst, const void* src, unsigned bytes, unsigned long long* bar) {
     asm volatile(
@@ -312,11 +328,13 @@ __device__ __forceinline__ double fx_march(const FxFields& fl, const double* __r
             // the stage that plane t - 1 used is free again (every thread
             // passed the barriers after reading it): refill it
             issue(t + S - 1);
-            if (!mbar_wait(bar + (t % S), (unsigned)((t / S) & 1))) {
+            const unsigned par = (unsigned)((t / S) & 1);
+            if (!mbar_wait(bar + (t % S), par, stalled ? kStageDrainNs : kStageWaitNs)) {
                 // a copy did not arrive: flag the launch, wait once more
-                // (bounded) for the copies in flight, carry on
+                // (briefly) for the copies in flight, carry on with what is
+                // there; later waits of this CTA are short
                 stalled = true;
-                mbar_wait(bar + (t % S), (unsigned)((t / S) & 1));
+                mbar_wait(bar + (t % S), par, kStageDrainNs);
             }
         }
         if (kDir) {
@@ -473,8 +491,10 @@ __device__ __forceinline__ double fx_march(const FxFields& fl, const double* __r
                     if (NF == 1 && b != nullptr) val = b[o] - val;
                     fl.out[f][o] = val;
                     if (kDot && f == 0)
-                        // p*'s new value was written by this CTA two planes ago
-                        dot += (kDir ? __ldcg(&fl.pn[1][o]) : __ldg(&fl.in[1][o])) * val;
+                        // sigma = (p*, A p) (with one field: (p, A p)); with
+                        // kDir p*'s new value was written by this CTA two
+                        // planes ago
+                        dot += (kDir ? __ldcg(&fl.pn[NF - 1][o]) : __ldg(&fl.in[NF - 1][o])) * val;
                 }
             }
 #pragma unroll
@@ -487,7 +507,16 @@ __device__ __forceinline__ double fx_march(const FxFields& fl, const double* __r
             }
         }
     }
-    if (kBulk && stalled) atomicExch(fl.fault, 1);
+    if (kBulk) {
+        if (stalled) atomicExch(fl.fault, 1);
+        // every thread has passed its last wait (the plane loop ends with
+        // barriers): release the mbarriers, which a caller marching another
+        // tile in the same launch initialises again
+        if (tid == 0) {
+#pragma unroll
+            for (int k = 0; k < S; ++k) mbar_inval(bar + k);
+        }
+    }
     return dot;
 }
 

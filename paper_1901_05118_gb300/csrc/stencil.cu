@@ -244,7 +244,11 @@ __device__ __forceinline__ double all_partials(const double* partials, int c, do
     return v;
 }
 
-template <bool kPointwise>
+// kElide: the shadow-elided mode (not the paper's Alg. 2 as printed): r*,
+// p*, A^T p* are not stored because they equal r, p, A p bit for bit (the
+// integer operator is symmetric and r*_0 = r_0); v.rs, v.ps, v.ps2, v.qs are
+// unused and the iterates are the same bits as with kElide = false.
+template <bool kPointwise, bool kElide>
 __global__ void __launch_bounds__(FX_NT, 2)
 bicg_persistent_kernel(BicgVectors v, size_t len, int n, int sigma, int gx, int gy, int slabs, int kz_per,
                        int iters, double* partials, BicgState* st, GridBarrier gb) {
@@ -279,8 +283,12 @@ bicg_persistent_kernel(BicgVectors v, size_t len, int n, int sigma, int gx, int 
                 const size_t o = ((size_t)k * np + j) * np + i;
                 const double qv = fx_point(v.p, n, sigma, i, j, k);
                 v.q[o] = qv;
-                v.qs[o] = fx_point(v.ps, n, sigma, i, j, k);
-                dot += v.ps[o] * qv;
+                if (kElide) {
+                    dot += v.p[o] * qv;
+                } else {
+                    v.qs[o] = fx_point(v.ps, n, sigma, i, j, k);
+                    dot += v.ps[o] * qv;
+                }
             }
         } else {
             FxFields fd{{odd ? v.p2 : v.p, odd ? v.ps2 : v.ps}, {v.q, v.qs}, {v.r, v.rs}, {pk, psk}, beta,
@@ -288,7 +296,11 @@ bicg_persistent_kernel(BicgVectors v, size_t len, int n, int sigma, int gx, int 
             for (int u = blockIdx.x; u < units; u += G) {
                 const int bx = u % gx, by = (u / gx) % gy, bz = u / (gx * gy);
                 const int kz0 = 1 + bz * kz_per;
-                dot += fx_march<2, true, true, true>(fd, nullptr, n, sigma, bx, by, kz0, min(kz0 + kz_per, n));
+                const int kz1 = min(kz0 + kz_per, n);
+                if (kElide)
+                    dot += fx_march<1, true, true, true>(fd, nullptr, n, sigma, bx, by, kz0, kz1);
+                else
+                    dot += fx_march<2, true, true, true>(fd, nullptr, n, sigma, bx, by, kz0, kz1);
             }
         }
         dot = block_sum(dot, sh);
@@ -307,6 +319,12 @@ bicg_persistent_kernel(BicgVectors v, size_t len, int n, int sigma, int gx, int 
         bool twin = true;   // as in bicg_update_kernel: vr == vrr so far
         for (size_t t = (size_t)blockIdx.x * nthreads + tid; t < len; t += (size_t)G * nthreads) {
             v.x[t] = v.x[t] + alpha * pcur[t];
+            if (kElide) {
+                const double rn = v.r[t] - alpha * v.q[t];
+                v.r[t] = rn;
+                vrr += rn * rn;
+                continue;
+            }
             const double rv = v.r[t], qv = v.q[t], rsv = v.rs[t], qsv = v.qs[t];
             const double rn = rv - alpha * qv;
             v.r[t] = rn;
@@ -358,7 +376,7 @@ bicg_persistent_kernel(BicgVectors v, size_t len, int n, int sigma, int gx, int 
             // does this in the next operator phase)
             for (size_t t = (size_t)blockIdx.x * nthreads + tid; t < len; t += (size_t)G * nthreads) {
                 v.p[t] = v.r[t] + beta * v.p[t];
-                v.ps[t] = v.rs[t] + beta * v.ps[t];
+                if (!kElide) v.ps[t] = v.rs[t] + beta * v.ps[t];
             }
             if (!(ok = grid_sync(gb, G))) break;
         }
@@ -476,6 +494,19 @@ StencilGrid fx_grid(int n, int nf) {
         g.block = dim3(FX_TX, FX_TY, 1);
         return g;
     }
+    if (nf == 6 || nf == 7) {
+        // shadow-elided operator (one field, staged loads): the grid of the
+        // pair kernel it replaces (4 / 5), so that sigma adds the same
+        // per-CTA partial sums
+        static bool attr6 = false, attr7 = false;
+        const size_t smem6 = fx_stage_bytes<1, fx_stages(false)>();
+        const size_t smem7 = fx_stage_bytes<2, fx_stages(true)>();
+        if (nf == 6 && !attr6) attr6 = resident_per_sm(stencil_fx_kernel<1, true, false, true>, FX_NT, smem6) > 0;
+        if (nf == 7 && !attr7) attr7 = resident_per_sm(stencil_fx_kernel<1, true, true, true>, FX_NT, smem7) > 0;
+        StencilGrid g = fx_grid(n, nf - 2);
+        g.smem = nf == 6 ? smem6 : smem7;
+        return g;
+    }
     if (nf == 4 || nf == 5) {   // staged loads: pair (4), pair with directions (5)
         static int occ4 = 0, occ5 = 0;
         const size_t smem4 = fx_stage_bytes<2, fx_stages(false)>();
@@ -541,8 +572,10 @@ size_t persistent_stage_bytes() { return fx_stage_bytes<4, fx_stages(true)>(); }
 int persistent_grid(int n, int* gx, int* gy, int* slabs, int* kz_per) {
     static int occ_pt = 0, occ_mz = 0;
     if (!occ_pt) {
-        occ_pt = resident_per_sm(bicg_persistent_kernel<true>, FX_NT);
-        occ_mz = resident_per_sm(bicg_persistent_kernel<false>, FX_NT, persistent_stage_bytes());
+        occ_pt = resident_per_sm(bicg_persistent_kernel<true, false>, FX_NT);
+        occ_mz = resident_per_sm(bicg_persistent_kernel<false, false>, FX_NT, persistent_stage_bytes());
+        // the elided variants run on the same grids (same partial sums)
+        resident_per_sm(bicg_persistent_kernel<false, true>, FX_NT, persistent_stage_bytes());
         if (occ_pt > 2) occ_pt = 2;
         if (occ_mz > 2) occ_mz = 2;
     }
@@ -565,7 +598,7 @@ bool persistent_pointwise(int n) { return n <= kPointwiseMaxN; }
 
 cudaError_t launch_bicg_persistent(double* x, double* r, double* rs, double* p, double* ps, double* p2, double* ps2,
                                    double* q, double* qs, int n, int bc_kind, int iters, double* partials,
-                                   BicgState* st, unsigned int* barrier_words, cudaStream_t s) {
+                                   BicgState* st, unsigned int* barrier_words, cudaStream_t s, bool elide) {
     int gx, gy, slabs, kz_per;
     const int G = persistent_grid(n, &gx, &gy, &slabs, &kz_per);
     cudaError_t e = cudaMemsetAsync(barrier_words, 0, 3 * sizeof(unsigned int), s);
@@ -576,7 +609,10 @@ cudaError_t launch_bicg_persistent(double* x, double* r, double* rs, double* p, 
     GridBarrier gb{barrier_words, barrier_words + 1, (int*)(barrier_words + 2)};
     void* args[] = {&v, &len, &n, &sigma, &gx, &gy, &slabs, &kz_per, &iters, &partials, &st, &gb};
     const bool pw = persistent_pointwise(n);
-    const void* fn = pw ? (const void*)bicg_persistent_kernel<true> : (const void*)bicg_persistent_kernel<false>;
+    const void* fn = pw ? (elide ? (const void*)bicg_persistent_kernel<true, true>
+                                 : (const void*)bicg_persistent_kernel<true, false>)
+                        : (elide ? (const void*)bicg_persistent_kernel<false, true>
+                                 : (const void*)bicg_persistent_kernel<false, false>);
     return cudaLaunchCooperativeKernel(fn, dim3(G), dim3(FX_TX, FX_TY, 1), args, pw ? 0 : persistent_stage_bytes(),
                                        s);
 }
@@ -610,6 +646,38 @@ cudaError_t launch_bicg_stencil_pair(const double* p, double* q, const double* p
         const StencilGrid g = fx_grid(n, 2);
         stencil_fx_kernel<2, true><<<g.grid, g.block, 0, s>>>(fl, nullptr, n, sg, g.kz_per_cta, &st->done,
                                                               partials, st);
+    }
+    return cudaGetLastError();
+}
+
+cudaError_t launch_cg_stencil(const double* p, double* q, int n, int bc_kind, double* partials, BicgState* st,
+                              cudaStream_t s) {
+    FxFields fl{{p, nullptr}, {q, nullptr}, {nullptr, nullptr}, {nullptr, nullptr}, 0.0, nullptr, nullptr};
+    const int sg = bc_kind == 1 ? 1 : -1;
+    if (bulk_ok(n, {p})) {
+        const StencilGrid g = fx_grid(n, 6);
+        stencil_fx_kernel<1, true, false, true><<<g.grid, g.block, g.smem, s>>>(fl, nullptr, n, sg, g.kz_per_cta,
+                                                                                &st->done, partials, st);
+    } else {
+        const StencilGrid g = fx_grid(n, 2);
+        stencil_fx_kernel<1, true><<<g.grid, g.block, 0, s>>>(fl, nullptr, n, sg, g.kz_per_cta, &st->done,
+                                                              partials, st);
+    }
+    return cudaGetLastError();
+}
+
+cudaError_t launch_cg_stencil_dir(const double* r, const double* p_prev, double* p, double* q, int n, int bc_kind,
+                                  double* partials, BicgState* st, cudaStream_t s) {
+    FxFields fl{{p_prev, nullptr}, {q, nullptr}, {r, nullptr}, {p, nullptr}, 0.0, nullptr, nullptr};
+    const int sg = bc_kind == 1 ? 1 : -1;
+    if (bulk_ok(n, {r, p_prev})) {
+        const StencilGrid g = fx_grid(n, 7);
+        stencil_fx_kernel<1, true, true, true><<<g.grid, g.block, g.smem, s>>>(fl, nullptr, n, sg, g.kz_per_cta,
+                                                                               &st->done, partials, st);
+    } else {
+        const StencilGrid g = fx_grid(n, 3);
+        stencil_fx_kernel<1, true, true><<<g.grid, g.block, 0, s>>>(fl, nullptr, n, sg, g.kz_per_cta, &st->done,
+                                                                    partials, st);
     }
     return cudaGetLastError();
 }

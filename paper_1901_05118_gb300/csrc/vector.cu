@@ -209,7 +209,90 @@ bicg_pupdate_kernel(double* __restrict__ p, const double* __restrict__ r, double
     }
 }
 
+// Shadow-elided mode (not Alg. 2 as printed; r* = r and p* = p are not
+// stored).  p_0 = r_0, rho_0 = rr = (r_0, r_0): the sums of
+// bicg_init_kernel with r*_0 = r_0, in the same order.
+__global__ void __launch_bounds__(kVecThreads)
+cg_init_kernel(const double* __restrict__ r, double* __restrict__ p, size_t len, double* partials, BicgState* st) {
+    __shared__ double sh[32];
+    __shared__ bool am_last;
+    double vrr = 0.0;
+    for (size_t t = blockIdx.x * (size_t)blockDim.x + threadIdx.x; t < len;
+         t += (size_t)gridDim.x * blockDim.x) {
+        const double rv = r[t];
+        p[t] = rv;
+        vrr += rv * rv;
+    }
+    double s2[2];
+    s2[0] = block_sum(vrr, sh);
+    s2[1] = s2[0];
+    if (publish_partials(s2, 2, partials, &st->ticket, &am_last)) {
+        const double rr = gather_partials(partials, 1, sh);
+        if (thread0()) {
+            st->rho = rr;
+            st->rr = rr;
+            st->iter = 0;
+            st->alpha = st->beta = st->sigma = 0.0;
+            const bool conv = sqrt(rr) <= st->tol * st->bnorm;
+            st->done = (conv || st->max_iter <= 0) ? 1 : 0;
+            st->status = conv ? kConverged : (st->max_iter <= 0 ? kCapped : kRunning);
+            st->ticket = 0;
+        }
+    }
+}
+
+// Shadow-elided update: x += alpha p; r -= alpha A p; rho_{k+1} = rr =
+// (r, r); beta; stopping test.  Same arithmetic and summation order as
+// bicg_update_kernel on twin entries.
+__global__ void __launch_bounds__(kVecThreads)
+cg_update_kernel(double* __restrict__ x, const double* __restrict__ p, double* __restrict__ r,
+                 const double* __restrict__ q, size_t len, double* partials, BicgState* st) {
+    if (st->done) return;
+    __shared__ double sh[32];
+    __shared__ bool am_last;
+    const double alpha = st->alpha;
+    double vrr = 0.0;
+    for (size_t t = blockIdx.x * (size_t)blockDim.x + threadIdx.x; t < len;
+         t += (size_t)gridDim.x * blockDim.x) {
+        x[t] = x[t] + alpha * p[t];
+        const double rn = r[t] - alpha * q[t];
+        r[t] = rn;
+        vrr += rn * rn;
+    }
+    double s[2];
+    s[0] = block_sum(vrr, sh);
+    s[1] = s[0];
+    if (publish_partials(s, 2, partials, &st->ticket, &am_last)) {
+        const double rr = gather_partials(partials, 1, sh);
+        if (thread0()) {
+            st->beta = rr / st->rho;
+            st->rho = rr;
+            st->rr = rr;
+            st->iter += 1;
+            if (sqrt(rr) <= st->tol * st->bnorm) {
+                st->status = kConverged;
+                st->done = 1;
+            } else if (st->iter >= st->max_iter) {
+                st->status = kCapped;
+                st->done = 1;
+            }
+            st->ticket = 0;
+        }
+    }
+}
+
 }  // namespace
+
+cudaError_t launch_cg_init(const double* r, double* p, size_t len, double* partials, BicgState* st, cudaStream_t s) {
+    cg_init_kernel<<<kVecBlocks, kVecThreads, 0, s>>>(r, p, len, partials, st);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_cg_update(double* x, const double* p, double* r, const double* q, size_t len, double* partials,
+                             BicgState* st, cudaStream_t s) {
+    cg_update_kernel<<<kVecBlocks, kVecThreads, 0, s>>>(x, p, r, q, len, partials, st);
+    return cudaGetLastError();
+}
 
 cudaError_t launch_dot(const double* a, const double* b, size_t len, double* partials,
                        unsigned int* ticket, double* out, cudaStream_t s) {

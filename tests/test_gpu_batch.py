@@ -17,8 +17,21 @@ from paper_1901_05118_gb300 import binding as B  # noqa: E402
 DEV = torch.device("cuda", 0)
 
 # (n_finest, n_coarsest, bc_kind, problem)
-MIX = [(32, 4, 1, "sin_pi"), (48, 6, 2, "random_sines:3"), (64, 8, 1, "random_sines:4"),
+# first-kind random sines on 64^3 need ~1100 oracle Bi-CG iterations on the
+# finest level (minutes of CPU time): the 64^3 instance has second-kind data
+MIX = [(32, 4, 1, "sin_pi"), (48, 6, 2, "random_sines:3"), (64, 8, 2, "random_sines:4"),
        (24, 6, 2, "exp_sum"), (40, 5, 1, "sin2pi_plus_poly")]
+
+_ORACLE = {}
+
+
+def oracle_solution(n, nc, bc, name, tol):
+    """u~ of the oracle for one MIX entry (computed once per session)."""
+    key = (n, nc, bc, name, tol)
+    if key not in _ORACLE:
+        fr, g1r, g2r = P.by_name(name).data(n, bc)
+        _ORACLE[key] = oracle.excmg(n, nc, bc, fr, g1r, g2r, tol)[1]
+    return _ORACLE[key]
 
 
 def data(n, bc, name):
@@ -40,13 +53,12 @@ def test_batch_matches_single_solves_and_oracle(precision):
         ident, u = batch.submit(n, nc, bc, f, g1, g2, tol, precision=precision)
         subs.append((ident, u, n, nc, bc, prob, f, g1, g2))
     batch.run()
-    for ident, u, n, nc, bc, prob, f, g1, g2 in subs:
+    for (ident, u, n, nc, bc, prob, f, g1, g2), (_, _, _, name) in zip(subs, MIX):
         q = batch.query(ident)
         assert q["done"] and q["status"] == 0
         for s in q["stats"][2:]:
             assert s["relres"] <= tol
-        fr, g1r, g2r = prob.data(n, bc)
-        _, ref_t, _ = oracle.excmg(n, nc, bc, fr, g1r, g2r, tol)
+        ref_t = oracle_solution(n, nc, bc, name, tol)
         got = u.cpu().numpy()
         scale = np.abs(ref_t).max()
         if precision == "fp64":
