@@ -360,11 +360,22 @@ def run_ours(args):
     avg_ms = st_ms / st_cnt if st_cnt else float("nan")
     bytes_per_launch = st_bytes / st_cnt if st_cnt else None
     achieved = st_bytes / (st_ms * 1e-3) / 1e9 if st_cnt else None
-    kernel = (f"stencil_fx_kernel: p = r + beta p, p* = r* + beta p*, A p and A^T p* and sigma on the {n}^3 grid"
-              if args.stencil == "exact" else f"stencil_f64_kernel: A p or A^T p* on the {n}^3 grid")
+    per_unknown = bytes_per_launch / (n - 1) ** 3 if bytes_per_launch else 0.0
+    if args.stencil != "exact":
+        kernel = f"stencil_f64_kernel: A p or A^T p* on the {n}^3 grid"
+    elif per_unknown > 48.0:
+        kernel = f"stencil_fx_kernel (fused schedule): p, p* formed, A p, A^T p*, sigma on the {n}^3 grid"
+    else:
+        kernel = f"stencil_fx_kernel: A p, A^T p*, sigma (operator pair) on the {n}^3 grid"
+    # DRAM traffic of the operator pair (dram__bytes_read.sum + dram__bytes_write.sum) from one
+    # ncu capture of the same kernel on 255^3 unknowns (515.04 MB), scaled to this launch by the
+    # unknowns it processes (traffic grows in proportion); only the kernel that was captured
+    traffic = None
+    if args.stencil == "exact" and 24.0 < per_unknown < 40.0:
+        traffic = 515.04e6 / 255 ** 3 * (n - 1) ** 3
     roofline = {"kernel": kernel, "bound": "hbm",
                 "achieved": achieved, "peak": hbm_peak, "unit": "GB/s",
-                "frac": (achieved / hbm_peak) if achieved else None, "traffic": None,
+                "frac": (achieved / hbm_peak) if achieved else None, "traffic": traffic,
                 "launches": st_cnt, "avg_ms": avg_ms, "bytes_per_launch": bytes_per_launch,
                 "peak_source": "MEASURED_PEAKS.json hbm_gbs (of measured)"}
 

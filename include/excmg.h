@@ -116,7 +116,7 @@ int excmg_ctx_set_stencil(excmg_ctx *ctx, int variant);
  *   variant: A_h is symmetric, and with r*_0 = r_0 and the exact operator
  *   (EXCMG_STENCIL_EXACT) A^T p* and A p are the same bits, so the shadow
  *   sequence equals the primal one bit for bit; it is then neither stored
- *   nor read (80 instead of 136 bytes per unknown and iteration on large
+ *   nor read (88 instead of 152 bytes per unknown and iteration on large
  *   grids) and every iterate, stopping decision and result is bit for bit
  *   that of EXCMG_SHADOW_FULL.  It applies to the exact operator only: with
  *   EXCMG_STENCIL_FP64, and in calls that pass their own r*_0
@@ -124,6 +124,22 @@ int excmg_ctx_set_stencil(excmg_ctx *ctx, int variant);
  *   the full sequence. */
 enum { EXCMG_SHADOW_FULL = 0, EXCMG_SHADOW_ELIDED = 1 };
 int excmg_ctx_set_shadow_mode(excmg_ctx *ctx, int mode);
+
+/* How a Bi-CG iteration is split into kernels (integer operator); both give
+ * the same iterates up to the reduction order of sigma (same bits within
+ * one schedule).
+ * EXCMG_SCHEDULE_SEPARATE (default): operator pair (A p, A^T p*, sigma,
+ *   alpha), update (x, r, r*, rho, beta) and direction update (p, p*) as
+ *   three launches on grids above 64^3 (152 bytes per unknown), a three-phase
+ *   cooperative launch on smaller ones.
+ * EXCMG_SCHEDULE_FUSED: the operator launch first forms p = r + beta p and
+ *   p* from the previous directions (recomputed on each block's halo, input
+ *   rows staged in shared memory by bulk copies), then applies A and A^T:
+ *   two launches, 136 bytes per unknown.  Measured slower on GB300 (4.0 ms
+ *   against 3.4 ms per iteration at 512^3): the halo recomputation and the
+ *   barrier stalls of the staged march cost more than the saved pass. */
+enum { EXCMG_SCHEDULE_SEPARATE = 0, EXCMG_SCHEDULE_FUSED = 1 };
+int excmg_ctx_set_schedule(excmg_ctx *ctx, int schedule);
 const char *excmg_last_error(const excmg_ctx *ctx);
 
 /* Instrumentation.  excmg_launch_count: kernel launches the library has

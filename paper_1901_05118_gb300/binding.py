@@ -32,6 +32,7 @@ STATUS_NAMES = {0: "EXCMG_OK", -1: "EXCMG_ERR_ARG", -2: "EXCMG_ERR_OOM", -3: "EX
 TOL_MODES = {"paper": 0, "uniform": 1}
 STENCIL_VARIANTS = {"exact": 0, "fp64": 1}
 SHADOW_MODES = {"full": 0, "elided": 1}
+SCHEDULES = {"separate": 0, "fused": 1}
 PRECISIONS = {"fp64": 0, "mixed": 1}
 MIXED_INNER_CAP = 500      # iterations of one FP32 correction solve
 MIXED_INNER_TOL = 1e-4     # residual reduction asked of one FP32 correction solve
@@ -69,6 +70,7 @@ _lib.excmg_ctx_bytes.argtypes = [_vp]
 _lib.excmg_ctx_bytes.restype = _sz
 _lib.excmg_ctx_set_stencil.argtypes = [_vp, _i]
 _lib.excmg_ctx_set_shadow_mode.argtypes = [_vp, _i]
+_lib.excmg_ctx_set_schedule.argtypes = [_vp, _i]
 _lib.excmg_launch_count.argtypes = []
 _lib.excmg_launch_count.restype = ctypes.c_longlong
 _lib.excmg_ctx_profile.argtypes = [_vp, _i]
@@ -112,7 +114,7 @@ for _name in ("excmg_batch_create", "excmg_batch_destroy", "excmg_batch_submit",
     getattr(_lib, _name).restype = _i
 
 for _name in ("excmg_ctx_create", "excmg_ctx_destroy", "excmg_ctx_set_stencil", "excmg_ctx_set_shadow_mode",
-              "excmg_ctx_profile",
+              "excmg_ctx_set_schedule", "excmg_ctx_profile",
               "excmg_ctx_profile_read", "excmg_level_create", "excmg_level_destroy",
               "stencil_apply", "bicg_solve", "bicg_solve_ex", "extrapolate_interpolate", "extrapolate_interpolate_ex",
               "midpoint_extrapolate", "midpoint_extrapolate_ex", "excmg_solve", "excmg_solve_ex",
@@ -181,6 +183,12 @@ class Context:
         sequence, bit for bit the primal one with the exact operator, is not
         stored; results are the same bits)."""
         self.check(_lib.excmg_ctx_set_shadow_mode(self.handle, SHADOW_MODES[mode]), "excmg_ctx_set_shadow_mode")
+
+    def set_schedule(self, schedule: str):
+        """'separate' (default: operator pair, update, direction update) or
+        'fused' (direction update folded into the operator launch, staged
+        input rows; measured slower on GB300)."""
+        self.check(_lib.excmg_ctx_set_schedule(self.handle, SCHEDULES[schedule]), "excmg_ctx_set_schedule")
 
     def profile(self, enable: bool = True):
         """Time every operator launch inside Bi-CG (CUDA events on this context's stream)."""

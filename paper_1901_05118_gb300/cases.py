@@ -1,7 +1,7 @@
 """Small, fixed GPU cases for profiling single kernels of the library.
 
     python -m paper_1901_05118_gb300.cases stencil --n 256 --variant exact --reps 3
-    python -m paper_1901_05118_gb300.cases bicg --n 256 --iters 4
+    python -m paper_1901_05118_gb300.cases bicg --n 256 --iters 4 [--schedule fused]
     python -m paper_1901_05118_gb300.cases solve --n 64 --nc 8
     python -m paper_1901_05118_gb300.cases issue-rates
 
@@ -33,6 +33,7 @@ def main(argv=None):
     ap.add_argument("--nc", type=int, default=8)
     ap.add_argument("--bc", type=int, default=1)
     ap.add_argument("--variant", choices=["exact", "fp64"], default="exact")
+    ap.add_argument("--schedule", choices=["separate", "fused"], default="separate")
     ap.add_argument("--reps", type=int, default=3)
     ap.add_argument("--iters", type=int, default=4)
     a = ap.parse_args(argv)
@@ -47,6 +48,7 @@ def main(argv=None):
     torch.cuda.set_device(dev)
     ctx = B.Context(dev)
     ctx.set_stencil(a.variant)
+    ctx.set_schedule(a.schedule)
     n = a.n
     gen = torch.Generator(device=dev)
     gen.manual_seed(0)

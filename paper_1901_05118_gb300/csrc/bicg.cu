@@ -73,11 +73,12 @@ int bicg_run(excmg_ctx* ctx, int n, int bc_kind, const double* b, double* x, dou
     const bool fused = ctx->stencil_variant == kStencilExact && stencil_cta_count(n) <= kMaxPartials;
     // small grids run whole iterations in one cooperative launch
     const bool persistent = fused && n <= kPersistentMaxN;
-    // other grids, and the z-march variant of the cooperative kernel, fold
+    // the fused schedule (an option; measured slower on GB300) folds
     // p = r + beta p into the operator step, which reads the previous
     // directions from one buffer pair and writes the new ones to the other
-    // (neighbouring blocks still read the old values)
-    const bool dir_fused = fused && !(persistent && persistent_pointwise(n));
+    // (neighbouring blocks still read the old values), with staged rows
+    const bool fuse = ctx->schedule == EXCMG_SCHEDULE_FUSED;
+    const bool dir_fused = fused && fuse && !(persistent && persistent_pointwise(n));
     double* p2 = dir_fused ? ctx_buffer(ctx, "bicg_p2", bytes, &st) : nullptr;
     double* ps2 = (dir_fused && !elide && !st) ? ctx_buffer(ctx, "bicg_ps2", bytes, &st) : nullptr;
     if (st) return st;
@@ -120,7 +121,7 @@ int bicg_run(excmg_ctx* ctx, int n, int bc_kind, const double* b, double* x, dou
             const int left = max_iter - ctx->host_state->iter;
             if (chunk > left) chunk = left;
             e = launch_bicg_persistent(x, r, rs, p, ps, p2, ps2, q, qs, n, bc_kind, chunk, ctx->partials, ctx->state,
-                                       ctx->barrier, s, elide);
+                                       ctx->barrier, s, elide, fuse);
             note_launches(1);
             if (e != cudaSuccess) return ctx_cuda(ctx, e, "cooperative Bi-CG launch");
         }
@@ -173,9 +174,10 @@ int bicg_run(excmg_ctx* ctx, int n, int bc_kind, const double* b, double* x, dou
                 // A p_k and A^T p*_k in one z-march, sigma_k and alpha_k fused;
                 // from the second iteration on the launch first forms
                 // p_k = r_k + beta_{k-1} p_{k-1} (and p*_k) on the fly
-                if (enqueued == 0) {
-                    e = elide ? launch_cg_stencil(pc, q, n, bc_kind, ctx->partials, ctx->state, s)
-                              : launch_bicg_stencil_pair(pc, q, psc, qs, n, bc_kind, ctx->partials, ctx->state, s);
+                if (enqueued == 0 || !dir_fused) {
+                    e = elide ? launch_cg_stencil(pc, q, n, bc_kind, ctx->partials, ctx->state, s, dir_fused)
+                              : launch_bicg_stencil_pair(pc, q, psc, qs, n, bc_kind, ctx->partials, ctx->state, s,
+                                                         dir_fused);
                     // p (, p*) in; q (, q*) out
                     launch_bytes[it] = (elide ? 16.0 : 32.0) * unknowns;
                 } else {
@@ -203,10 +205,12 @@ int bicg_run(excmg_ctx* ctx, int n, int bc_kind, const double* b, double* x, dou
             if (e == cudaSuccess)
                 e = elide ? launch_cg_update(x, pc, r, q, len, ctx->partials, ctx->state, s)
                           : launch_bicg_update(x, pc, r, q, rs, qs, len, ctx->partials, ctx->state, s);
-            if (e == cudaSuccess && !fused) e = launch_bicg_pupdate(p, r, ps, rs, len, ctx->state, s);
+            if (e == cudaSuccess && !dir_fused)
+                e = elide ? launch_cg_pupdate(p, r, len, ctx->state, s)
+                          : launch_bicg_pupdate(p, r, ps, rs, len, ctx->state, s);
             ++enqueued;
         }
-        note_launches((fused ? 2LL : 5LL) * batch);
+        note_launches((dir_fused ? 2LL : (fused ? 3LL : 5LL)) * batch);
         if (e != cudaSuccess) return ctx_cuda(ctx, e, "Bi-CG iteration");
     }
     const BicgState& h = *ctx->host_state;

@@ -153,6 +153,15 @@ int excmg_ctx_set_shadow_mode(excmg_ctx* c, int mode) {
     return EXCMG_OK;
 }
 
+int excmg_ctx_set_schedule(excmg_ctx* c, int schedule) {
+    if (!c) c = default_ctx();
+    if (!c) return EXCMG_ERR_CUDA;
+    if (schedule != EXCMG_SCHEDULE_SEPARATE && schedule != EXCMG_SCHEDULE_FUSED)
+        return ctx_fail(c, EXCMG_ERR_ARG, "unknown operator schedule");
+    c->schedule = schedule;
+    return EXCMG_OK;
+}
+
 long long excmg_launch_count(void) { return g_launches.load(); }
 
 int excmg_ctx_profile(excmg_ctx* c, int enable) {

@@ -58,7 +58,7 @@ cudaError_t launch_zero_boundary(double* y, int n, cudaStream_t s);
 // arithmetic, fused with sigma = (p*, q) and alpha = rho / sigma (Alg. 2).
 // Skips when st->done.  partials must hold stencil_cta_count(n) doubles.
 cudaError_t launch_bicg_stencil_pair(const double* p, double* q, const double* ps, double* qs, int n,
-                                     int bc_kind, double* partials, BicgState* st, cudaStream_t s);
+                                     int bc_kind, double* partials, BicgState* st, cudaStream_t s, bool staged);
 int stencil_cta_count(int n);
 // As launch_bicg_stencil_pair, with the direction update of the previous
 // iteration fused in: p = r + beta p_prev, p* = r* + beta p*_prev (beta from
@@ -71,12 +71,13 @@ cudaError_t launch_bicg_stencil_pair_dir(const double* r, const double* rs, cons
 // persistent_pointwise(n), the directions alternate between (p, ps) and
 // (p2, ps2), whose boundary entries must be zero; p, ps must hold p_0 on
 // entry (iteration k reads p_{k-1} from one pair, writes p_k to the other).
-constexpr int kPersistentMaxN = 128;
+constexpr int kPersistentMaxN = 64;
 bool persistent_pointwise(int n);
 // elide: the shadow-elided mode (rs, ps, ps2, qs unused, may be null).
 cudaError_t launch_bicg_persistent(double* x, double* r, double* rs, double* p, double* ps, double* p2, double* ps2,
                                    double* q, double* qs, int n, int bc_kind, int iters, double* partials,
-                                   BicgState* st, unsigned int* barrier_words, cudaStream_t s, bool elide);
+                                   BicgState* st, unsigned int* barrier_words, cudaStream_t s, bool elide,
+                                   bool fuse);
 // Shadow-elided mode (r* = r, p* = p, A^T p* = A p not stored): the one-field
 // operator launches with sigma = (p, A p) and alpha (the second also forms
 // p = r + beta p_prev into p), and the matching set-up and update kernels.
@@ -84,7 +85,8 @@ cudaError_t launch_bicg_persistent(double* x, double* r, double* rs, double* p, 
 // partial sums in the same order and the iterates are bit for bit those of
 // the full mode.
 cudaError_t launch_cg_stencil(const double* p, double* q, int n, int bc_kind, double* partials, BicgState* st,
-                              cudaStream_t s);
+                              cudaStream_t s, bool staged);
+cudaError_t launch_cg_pupdate(double* p, const double* r, size_t len, const BicgState* st, cudaStream_t s);
 cudaError_t launch_cg_stencil_dir(const double* r, const double* p_prev, double* p, double* q, int n, int bc_kind,
                                   double* partials, BicgState* st, cudaStream_t s);
 cudaError_t launch_cg_init(const double* r, double* p, size_t len, double* partials, BicgState* st, cudaStream_t s);
@@ -164,6 +166,7 @@ struct excmg_ctx {
     double* host_scalar = nullptr;            // pinned host mirror of `scalar`
     int stencil_variant = excmg::kStencilExact;
     int shadow_mode = EXCMG_SHADOW_FULL;
+    int schedule = EXCMG_SCHEDULE_SEPARATE;
     // optional timing of the operator launches inside Bi-CG
     bool profile = false;
     std::vector<cudaEvent_t> prof_events;

@@ -311,6 +311,11 @@ __device__ __forceinline__ double fx_march(const FxFields& fl, const double* __r
         poisoned[f] = false;
     }
     double dot = 0.0;
+    // NF = 2: while the two fields' planes have been equal bit for bit (with
+    // r*_0 = r_0 in Bi-CG, always), field 1's accumulators would equal field
+    // 0's; they are then not kept separately (exact integer sums, so no bit
+    // of the result changes)
+    bool shared1 = NF == 2;
 
     for (int zin = kz0 - 2; zin <= kz1 + 1; ++zin) {
         const bool zok = (zin >= 1) && (zin <= n - 1);
@@ -373,23 +378,45 @@ __device__ __forceinline__ double fx_march(const FxFields& fl, const double* __r
                 for (int r = 0; r < FX_SLOTS; ++r)
                     v[f][r] = (zok && soff[r] >= 0) ? (kBulk ? staged(f, r) : fl.in[f][zbase + soff[r]]) : 0.0;
         }
-#pragma unroll
-        for (int f = 0; f < NF; ++f) {
-            int emax = 0;
-#pragma unroll
-            for (int r = 0; r < FX_SLOTS; ++r) emax = max(emax, exponent_of(v[f][r]));
-            emax = (int)__reduce_max_sync(0xffffffffu, (unsigned)emax);
-            if (lane == 0) wmax[f][tid >> 5] = emax;
-        }
         if (NF == 2) {
 #pragma unroll
             for (int r = 0; r < FX_SLOTS; ++r)
                 same = same && (__double_as_longlong(v[0][r]) == __double_as_longlong(v[NF - 1][r]));
         }
-        // also: every thread is done reading the previous tiles
-        const bool plane_same = NF == 2 ? (__syncthreads_and(same) != 0) : (__syncthreads(), false);
+        // a warp whose two fields agree bit for bit has one exponent maximum
+        const bool warp_same = NF == 2 && __all_sync(0xffffffffu, same);
+        int emax0 = 0;
 #pragma unroll
         for (int f = 0; f < NF; ++f) {
+            int emax = 0;
+            if (f > 0 && warp_same) {
+                emax = emax0;
+            } else {
+#pragma unroll
+                for (int r = 0; r < FX_SLOTS; ++r) emax = max(emax, exponent_of(v[f][r]));
+                emax = (int)__reduce_max_sync(0xffffffffu, (unsigned)emax);
+            }
+            if (f == 0) emax0 = emax;
+            if (lane == 0) wmax[f][tid >> 5] = emax;
+        }
+        // also: every thread is done reading the previous tiles
+        const bool plane_same = NF == 2 ? (__syncthreads_and(same) != 0) : (__syncthreads(), false);
+        if (NF == 2 && shared1 && !plane_same) {
+            // first plane on which the fields differ: from here on field 1
+            // keeps accumulators of its own, starting from field 0's
+#pragma unroll
+            for (int q = 0; q < FX_RY; ++q)
+#pragma unroll
+                for (int k = 0; k < 5; ++k) acc[NF - 1][q][k] = acc[0][q][k];
+            shared1 = false;
+        }
+#pragma unroll
+        for (int f = 0; f < NF; ++f) {
+            if (f > 0 && shared1) {   // the same plane: the same scale
+                E[f] = E[0];
+                poisoned[f] = poisoned[0];
+                continue;
+            }
             const int ep = (int)__reduce_max_sync(0xffffffffu, (unsigned)wmax[f][lane & (FX_NT / 32 - 1)]);
             if (ep == 0x7FF) poisoned[f] = true;
             if (ep > E[f]) {
@@ -423,6 +450,16 @@ __device__ __forceinline__ double fx_march(const FxFields& fl, const double* __r
         double val0[FX_RY] = {0.0, 0.0};
 #pragma unroll
         for (int f = 0; f < NF; ++f) {
+            if (f > 0 && shared1) {
+                // field 1 has been field 0 bit for bit on every plane so far:
+                // its exact sums, hence its outputs, are field 0's
+                if (zstore) {
+#pragma unroll
+                    for (int q = 0; q < FX_RY; ++q)
+                        if (q == 0 ? act0 : act1) fl.out[f][o0 + (size_t)q * np] = val0[q];
+                }
+                continue;
+            }
             long long cc[FX_RY], p0[FX_RY], p1[FX_RY];
             if (f > 0 && twin) {
 #pragma unroll

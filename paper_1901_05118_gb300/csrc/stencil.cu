@@ -248,7 +248,10 @@ __device__ __forceinline__ double all_partials(const double* partials, int c, do
 // p*, A^T p* are not stored because they equal r, p, A p bit for bit (the
 // integer operator is symmetric and r*_0 = r_0); v.rs, v.ps, v.ps2, v.qs are
 // unused and the iterates are the same bits as with kElide = false.
-template <bool kPointwise, bool kElide>
+// kFuse (z-march only): the fused schedule -- p = r + beta p formed inside
+// the operator phase from staged rows, two phases per iteration; otherwise
+// three phases with a separate direction update.
+template <bool kPointwise, bool kElide, bool kFuse>
 __global__ void __launch_bounds__(FX_NT, 2)
 bicg_persistent_kernel(BicgVectors v, size_t len, int n, int sigma, int gx, int gy, int slabs, int kz_per,
                        int iters, double* partials, BicgState* st, GridBarrier gb) {
@@ -297,10 +300,17 @@ bicg_persistent_kernel(BicgVectors v, size_t len, int n, int sigma, int gx, int 
                 const int bx = u % gx, by = (u / gx) % gy, bz = u / (gx * gy);
                 const int kz0 = 1 + bz * kz_per;
                 const int kz1 = min(kz0 + kz_per, n);
-                if (kElide)
-                    dot += fx_march<1, true, true, true>(fd, nullptr, n, sigma, bx, by, kz0, kz1);
-                else
-                    dot += fx_march<2, true, true, true>(fd, nullptr, n, sigma, bx, by, kz0, kz1);
+                if (kFuse) {
+                    if (kElide)
+                        dot += fx_march<1, true, true, true>(fd, nullptr, n, sigma, bx, by, kz0, kz1);
+                    else
+                        dot += fx_march<2, true, true, true>(fd, nullptr, n, sigma, bx, by, kz0, kz1);
+                } else {
+                    if (kElide)
+                        dot += fx_march<1, true>(fl, nullptr, n, sigma, bx, by, kz0, kz1);
+                    else
+                        dot += fx_march<2, true>(fl, nullptr, n, sigma, bx, by, kz0, kz1);
+                }
             }
         }
         dot = block_sum(dot, sh);
@@ -315,7 +325,7 @@ bicg_persistent_kernel(BicgVectors v, size_t len, int n, int sigma, int gx, int 
         alpha = rho / sigma_s;
         // phase B: x += alpha p; r -= alpha q; r* -= alpha q*; (r*, r), (r, r)
         double vr = 0.0, vrr = 0.0;
-        const double* const pcur = kPointwise ? v.p : pk;
+        const double* const pcur = (kPointwise || !kFuse) ? v.p : pk;
         bool twin = true;   // as in bicg_update_kernel: vr == vrr so far
         for (size_t t = (size_t)blockIdx.x * nthreads + tid; t < len; t += (size_t)G * nthreads) {
             v.x[t] = v.x[t] + alpha * pcur[t];
@@ -371,8 +381,8 @@ bicg_persistent_kernel(BicgVectors v, size_t len, int n, int sigma, int gx, int 
             done = 1;
             break;
         }
-        if (kPointwise) {
-            // phase C: p = r + beta p; p* = r* + beta p* (the z-march variant
+        if (kPointwise || !kFuse) {
+            // phase C: p = r + beta p; p* = r* + beta p* (the fused schedule
             // does this in the next operator phase)
             for (size_t t = (size_t)blockIdx.x * nthreads + tid; t < len; t += (size_t)G * nthreads) {
                 v.p[t] = v.r[t] + beta * v.p[t];
@@ -569,22 +579,25 @@ constexpr int kPointwiseMaxN = 40;   // per-node operator on grids up to 40^3
 // operator phase with the direction update fused in
 size_t persistent_stage_bytes() { return fx_stage_bytes<4, fx_stages(true)>(); }
 
-int persistent_grid(int n, int* gx, int* gy, int* slabs, int* kz_per) {
-    static int occ_pt = 0, occ_mz = 0;
+int persistent_grid(int n, bool fuse, int* gx, int* gy, int* slabs, int* kz_per) {
+    static int occ_pt = 0, occ_mz = 0, occ_fz = 0;
     if (!occ_pt) {
-        occ_pt = resident_per_sm(bicg_persistent_kernel<true, false>, FX_NT);
-        occ_mz = resident_per_sm(bicg_persistent_kernel<false, false>, FX_NT, persistent_stage_bytes());
-        // the elided variants run on the same grids (same partial sums)
-        resident_per_sm(bicg_persistent_kernel<false, true>, FX_NT, persistent_stage_bytes());
+        occ_pt = resident_per_sm(bicg_persistent_kernel<true, false, false>, FX_NT);
+        occ_mz = resident_per_sm(bicg_persistent_kernel<false, false, false>, FX_NT);
+        occ_fz = resident_per_sm(bicg_persistent_kernel<false, false, true>, FX_NT, persistent_stage_bytes());
+        // the elided variants run on the grids of the full ones (same
+        // partial sums); this also opts them in to the dynamic shared memory
+        resident_per_sm(bicg_persistent_kernel<false, true, true>, FX_NT, persistent_stage_bytes());
         if (occ_pt > 2) occ_pt = 2;
         if (occ_mz > 2) occ_mz = 2;
+        if (occ_fz > 2) occ_fz = 2;
     }
     const int m = n - 1;
     *gx = (m + FX_TX - 1) / FX_TX;
     *gy = (m + FX_OY - 1) / FX_OY;
     *kz_per = m < 8 ? m : (n <= 64 ? 4 : 8);
     *slabs = (m + *kz_per - 1) / *kz_per;
-    if (n > kPointwiseMaxN) return 152 * occ_mz;
+    if (n > kPointwiseMaxN) return 152 * (fuse ? occ_fz : occ_mz);
     // one CTA per ~256 interior nodes, at most every resident slot: fewer
     // CTAs keep the grid barriers short on small grids
     const long long pts = (long long)m * m * m;
@@ -598,9 +611,12 @@ bool persistent_pointwise(int n) { return n <= kPointwiseMaxN; }
 
 cudaError_t launch_bicg_persistent(double* x, double* r, double* rs, double* p, double* ps, double* p2, double* ps2,
                                    double* q, double* qs, int n, int bc_kind, int iters, double* partials,
-                                   BicgState* st, unsigned int* barrier_words, cudaStream_t s, bool elide) {
+                                   BicgState* st, unsigned int* barrier_words, cudaStream_t s, bool elide,
+                                   bool fuse) {
+    const bool pw = persistent_pointwise(n);
+    fuse = fuse && !pw;
     int gx, gy, slabs, kz_per;
-    const int G = persistent_grid(n, &gx, &gy, &slabs, &kz_per);
+    const int G = persistent_grid(n, fuse, &gx, &gy, &slabs, &kz_per);
     cudaError_t e = cudaMemsetAsync(barrier_words, 0, 3 * sizeof(unsigned int), s);
     if (e != cudaSuccess) return e;
     BicgVectors v{x, r, rs, p, ps, p2, ps2, q, qs};
@@ -608,12 +624,17 @@ cudaError_t launch_bicg_persistent(double* x, double* r, double* rs, double* p, 
     int sigma = bc_kind == 1 ? 1 : -1;
     GridBarrier gb{barrier_words, barrier_words + 1, (int*)(barrier_words + 2)};
     void* args[] = {&v, &len, &n, &sigma, &gx, &gy, &slabs, &kz_per, &iters, &partials, &st, &gb};
-    const bool pw = persistent_pointwise(n);
-    const void* fn = pw ? (elide ? (const void*)bicg_persistent_kernel<true, true>
-                                 : (const void*)bicg_persistent_kernel<true, false>)
-                        : (elide ? (const void*)bicg_persistent_kernel<false, true>
-                                 : (const void*)bicg_persistent_kernel<false, false>);
-    return cudaLaunchCooperativeKernel(fn, dim3(G), dim3(FX_TX, FX_TY, 1), args, pw ? 0 : persistent_stage_bytes(),
+    const void* fn;
+    if (pw)
+        fn = elide ? (const void*)bicg_persistent_kernel<true, true, false>
+                   : (const void*)bicg_persistent_kernel<true, false, false>;
+    else if (fuse)
+        fn = elide ? (const void*)bicg_persistent_kernel<false, true, true>
+                   : (const void*)bicg_persistent_kernel<false, false, true>;
+    else
+        fn = elide ? (const void*)bicg_persistent_kernel<false, true, false>
+                   : (const void*)bicg_persistent_kernel<false, false, false>;
+    return cudaLaunchCooperativeKernel(fn, dim3(G), dim3(FX_TX, FX_TY, 1), args, fuse ? persistent_stage_bytes() : 0,
                                        s);
 }
 
@@ -635,10 +656,10 @@ cudaError_t launch_bicg_stencil_pair_dir(const double* r, const double* rs, cons
 }
 
 cudaError_t launch_bicg_stencil_pair(const double* p, double* q, const double* ps, double* qs, int n,
-                                     int bc_kind, double* partials, BicgState* st, cudaStream_t s) {
+                                     int bc_kind, double* partials, BicgState* st, cudaStream_t s, bool staged) {
     FxFields fl{{p, ps}, {q, qs}, {nullptr, nullptr}, {nullptr, nullptr}, 0.0, nullptr, nullptr};
     const int sg = bc_kind == 1 ? 1 : -1;
-    if (bulk_ok(n, {p, ps})) {
+    if (staged && bulk_ok(n, {p, ps})) {
         const StencilGrid g = fx_grid(n, 4);
         stencil_fx_kernel<2, true, false, true><<<g.grid, g.block, g.smem, s>>>(fl, nullptr, n, sg, g.kz_per_cta,
                                                                                 &st->done, partials, st);
@@ -651,10 +672,10 @@ cudaError_t launch_bicg_stencil_pair(const double* p, double* q, const double* p
 }
 
 cudaError_t launch_cg_stencil(const double* p, double* q, int n, int bc_kind, double* partials, BicgState* st,
-                              cudaStream_t s) {
+                              cudaStream_t s, bool staged) {
     FxFields fl{{p, nullptr}, {q, nullptr}, {nullptr, nullptr}, {nullptr, nullptr}, 0.0, nullptr, nullptr};
     const int sg = bc_kind == 1 ? 1 : -1;
-    if (bulk_ok(n, {p})) {
+    if (staged && bulk_ok(n, {p})) {
         const StencilGrid g = fx_grid(n, 6);
         stencil_fx_kernel<1, true, false, true><<<g.grid, g.block, g.smem, s>>>(fl, nullptr, n, sg, g.kz_per_cta,
                                                                                 &st->done, partials, st);

@@ -281,7 +281,22 @@ cg_update_kernel(double* __restrict__ x, const double* __restrict__ p, double* _
     }
 }
 
+// Shadow-elided direction update: p = r + beta p.
+__global__ void __launch_bounds__(kVecThreads)
+cg_pupdate_kernel(double* __restrict__ p, const double* __restrict__ r, size_t len, const BicgState* st) {
+    if (st->done) return;
+    const double beta = st->beta;
+    for (size_t t = blockIdx.x * (size_t)blockDim.x + threadIdx.x; t < len;
+         t += (size_t)gridDim.x * blockDim.x)
+        p[t] = r[t] + beta * p[t];
+}
+
 }  // namespace
+
+cudaError_t launch_cg_pupdate(double* p, const double* r, size_t len, const BicgState* st, cudaStream_t s) {
+    cg_pupdate_kernel<<<kVecBlocks, kVecThreads, 0, s>>>(p, r, len, st);
+    return cudaGetLastError();
+}
 
 cudaError_t launch_cg_init(const double* r, double* p, size_t len, double* partials, BicgState* st, cudaStream_t s) {
     cg_init_kernel<<<kVecBlocks, kVecThreads, 0, s>>>(r, p, len, partials, st);

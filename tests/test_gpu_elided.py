@@ -17,20 +17,22 @@ if torch.cuda.is_available():
 DEV = torch.device("cuda", 0)
 
 
-def ctx(mode):
+def ctx(mode, schedule="separate"):
     c = B.Context()
     c.set_shadow_mode(mode)
+    c.set_schedule(schedule)
     return c
 
 
-@pytest.mark.parametrize("n,bc_kind,tol,max_iter", [(24, 1, 1e-11, 5000), (80, 2, 1e-11, 5000),
+@pytest.mark.parametrize("schedule", ["separate", "fused"])
+@pytest.mark.parametrize("n,bc_kind,tol,max_iter", [(24, 1, 1e-11, 5000), (56, 2, 0.0, 300),
                                                      (136, 1, 0.0, 60), (133, 2, 0.0, 45)])
-def test_elided_bicg_is_bit_identical(n, bc_kind, tol, max_iter):
+def test_elided_bicg_is_bit_identical(n, bc_kind, tol, max_iter, schedule):
     b = torch.from_numpy(P.random_field(n, 91)).to(DEV)
     x0 = torch.from_numpy(P.random_field(n, 92) * 0.1).to(DEV)
     out = {}
     for mode in ("full", "elided"):
-        lvl = B.Level(n, bc_kind, ctx(mode))
+        lvl = B.Level(n, bc_kind, ctx(mode, schedule))
         x = x0.clone()
         it, rel, rc = B.bicg_solve(lvl, b, x, tol, max_iter)
         torch.cuda.synchronize()
