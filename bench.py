@@ -59,6 +59,8 @@ def parse():
     ap.add_argument("--no-serve", action="store_true", help="skip the request-stream leg")
     ap.add_argument("--serve-requests", type=int, default=120)
     ap.add_argument("--no-elided", action="store_true", help="skip the shadow-elided variant leg")
+    ap.add_argument("--schedule", choices=["separate", "fused"], default="separate",
+                    help="Bi-CG operator schedule of the timed solves")
     ap.add_argument("--serve-precision", choices=["fp64", "mixed"], default="fp64")
     ap.add_argument("--oracle-report", action="store_true",
                     help="time the CPU oracle on the small workload and one 512^3 operator application, then exit")
@@ -205,7 +207,7 @@ def config(args):
     return {"workload": (f"EXCMG FP64, {args.n}^3 intervals ({args.n - 1}^3 unknowns), coarsest {args.nc}^3, "
                          f"u=exp(x+y+z), first- and second-kind data, Bi-CG tol {args.tol:g} per level"),
             "n_finest": args.n, "n_coarsest": args.nc, "levels": int(np.log2(args.n // args.nc)) + 1,
-            "solves_per_step": 2, "tol": args.tol, "stencil": args.stencil,
+            "solves_per_step": 2, "tol": args.tol, "stencil": args.stencil, "schedule": args.schedule,
             "l2_flush": "inputs larger than L2 (each node array 1.08 GB)", "parallelism": "replicas"}
 
 
@@ -272,6 +274,7 @@ def run_ours(args):
     u_host = torch.empty((n + 1,) * 3, dtype=torch.float64).pin_memory()
     ctx = B.Context(dev)
     ctx.set_stencil(args.stencil)
+    ctx.set_schedule(args.schedule)
     stream = torch.cuda.current_stream(dev)
 
     def solve(bc, stats=False):
