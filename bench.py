@@ -41,7 +41,7 @@ METRIC = "EXCMG solve s @512³ FP64 vs FP32+refine; stencil HBM GB/s % peak; p99
 WU_DEFAULT = {1: 44.1, 2: 20.1}
 
 
-def parse():
+def parse(argv=None):
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
     ap.add_argument("--steps", type=int, default=3)
@@ -64,7 +64,7 @@ def parse():
     ap.add_argument("--serve-precision", choices=["fp64", "mixed"], default="fp64")
     ap.add_argument("--oracle-report", action="store_true",
                     help="time the CPU oracle on the small workload and one 512^3 operator application, then exit")
-    return ap.parse_args()
+    return ap.parse_args(argv)
 
 
 def dist_env():
