@@ -95,8 +95,12 @@ stencil_f64_kernel(const double* __restrict__ u, double* __restrict__ y, const d
     }
 }
 
+// Three CTAs per SM (at most 85 registers): the march waits on each plane's
+// loads, and 24 resident warps hide more of that latency than 16 (measured
+// 1.83 ms against 2.11 ms per operator pair at 512^3, despite a few bytes of
+// spilled state).
 template <int NF, bool kDot, bool kDir = false, bool kBulk = false>
-__global__ void __launch_bounds__(FX_NT)
+__global__ void __launch_bounds__(FX_NT, 3)
 stencil_fx_kernel(FxFields fl, const double* __restrict__ b, int n, int sigma, int kz_per_cta,
                   const int* __restrict__ skip, double* partials, BicgState* st) {
     extern __shared__ __align__(128) unsigned char fx_stage_smem[];
