@@ -371,11 +371,11 @@ def run_ours(args):
     else:
         kernel = f"stencil_fx_kernel: A p, A^T p*, sigma (operator pair) on the {n}^3 grid"
     # DRAM traffic of the operator pair (dram__bytes_read.sum + dram__bytes_write.sum) from one
-    # ncu capture of the same kernel on 255^3 unknowns (515.04 MB), scaled to this launch by the
+    # ncu capture of the same kernel on 255^3 unknowns (526.77 MB), scaled to this launch by the
     # unknowns it processes (traffic grows in proportion); only the kernel that was captured
     traffic = None
     if args.stencil == "exact" and 24.0 < per_unknown < 40.0:
-        traffic = 515.04e6 / 255 ** 3 * (n - 1) ** 3
+        traffic = 526.77e6 / 255 ** 3 * (n - 1) ** 3
     roofline = {"kernel": kernel, "bound": "hbm",
                 "achieved": achieved, "peak": hbm_peak, "unit": "GB/s",
                 "frac": (achieved / hbm_peak) if achieved else None, "traffic": traffic,
