@@ -136,8 +136,10 @@ int excmg_ctx_set_shadow_mode(excmg_ctx *ctx, int mode);
  *   p* from the previous directions (recomputed on each block's halo, input
  *   rows staged in shared memory by bulk copies), then applies A and A^T:
  *   two launches, 136 bytes per unknown.  Measured slower on GB300 (4.0 ms
- *   against 3.4 ms per iteration at 512^3): the halo recomputation and the
- *   barrier stalls of the staged march cost more than the saved pass. */
+ *   per fused launch against 2.8 ms for the separate operator pair and
+ *   direction update at 512^3; 0.254 s against 0.203 s per 512^3 solve):
+ *   the halo recomputation and the barrier stalls of the staged march cost
+ *   more than the saved pass. */
 enum { EXCMG_SCHEDULE_SEPARATE = 0, EXCMG_SCHEDULE_FUSED = 1 };
 int excmg_ctx_set_schedule(excmg_ctx *ctx, int schedule);
 const char *excmg_last_error(const excmg_ctx *ctx);
