@@ -79,49 +79,137 @@ __device__ __forceinline__ int quad_weights(int v, int n0, int* idx, double* w) 
     return 3;
 }
 
-__global__ void exp_finite_interp_kernel(double* __restrict__ w, const double* __restrict__ W, int nf) {
-    const int i = blockIdx.x * blockDim.x + threadIdx.x;
-    const int j = blockIdx.y * blockDim.y + threadIdx.y;
-    const int k = blockIdx.z;
+// Tiled, separable forms of the two fine-grid passes.  A CTA of 32 x 8
+// threads owns a tile of TX x TY x TZ fine nodes; the coarse values its
+// nodes need are staged in shared memory and interpolated along x, then y,
+// then z, so each intermediate value is formed once instead of once per
+// fine node that uses it (about 4 instead of 14 FP64 operations per node for
+// Step 5; FP64 issue is scarce on GB300).
+constexpr int TT_X = 32, TT_Y = 8, TT_Z = 8;
+constexpr int TT_THREADS = 256;
+constexpr int TM_X = TT_X / 2 + 1, TM_Y = TT_Y / 2 + 1, TM_Z = TT_Z / 2 + 1;   // coarse extents (17, 5, 5)
+
+// Middle-grid cell of fine index v (Step 5 uses cells of 4 fine intervals).
+__device__ __forceinline__ int quad_cell(int v, int n0) { return min(v >> 2, n0 - 1); }
+
+// Step 5 at every fine node of the tile: per fine node the same products and
+// sums, in the same order, as the direct tri-quadratic sum with x innermost,
+// then y, then z.
+__global__ void __launch_bounds__(TT_THREADS)
+exp_finite_interp_tiled_kernel(double* __restrict__ w, const double* __restrict__ W, int nf) {
+    __shared__ double Ws[TM_Z][TM_Y][TM_X];
+    __shared__ double Tx[TM_Z][TM_Y][TT_X];
+    __shared__ double Txy[TM_Z][TT_Y][TT_X];
+    const int tid = threadIdx.x;
     const int np = nf + 1, n0 = nf / 4, np1 = nf / 2 + 1;
-    if (i >= np || j >= np || k >= np) return;
-    int xi[3], yi[3], zi[3];
-    double xw[3], yw[3], zw[3];
-    const int nx = quad_weights(i, n0, xi, xw);
-    const int ny = quad_weights(j, n0, yi, yw);
-    const int nz = quad_weights(k, n0, zi, zw);
-    double v = 0.0;
-    for (int c = 0; c < nz; ++c) {
-        double vy = 0.0;
-        for (int b = 0; b < ny; ++b) {
-            double vx = 0.0;
-            for (int a = 0; a < nx; ++a) vx += xw[a] * W[nidx(np1, xi[a], yi[b], zi[c])];
-            vy += yw[b] * vx;
-        }
-        v += zw[c] * vy;
+    const int xa = blockIdx.x * TT_X, ya = blockIdx.y * TT_Y, za = blockIdx.z * TT_Z;
+    const int xb = min(xa + TT_X, np), yb = min(ya + TT_Y, np), zb = min(za + TT_Z, np);
+    // middle-grid nodes used by the tile: from the first node of the first
+    // cell to the last node of the last cell (tiles start on cell bounds)
+    const int mx0 = 2 * quad_cell(xa, n0), my0 = 2 * quad_cell(ya, n0), mz0 = 2 * quad_cell(za, n0);
+    const int nmx = 2 * quad_cell(xb - 1, n0) + 3 - mx0;
+    const int nmy = 2 * quad_cell(yb - 1, n0) + 3 - my0;
+    const int nmz = 2 * quad_cell(zb - 1, n0) + 3 - mz0;
+    for (int e = tid; e < nmz * nmy * nmx; e += TT_THREADS) {
+        const int ex = e % nmx, ey = (e / nmx) % nmy, ez = e / (nmx * nmy);
+        Ws[ez][ey][ex] = W[nidx(np1, mx0 + ex, my0 + ey, mz0 + ez)];
     }
-    w[nidx(np, i, j, k)] = v;
+    __syncthreads();
+    // along x: vx at (fine x, middle y, middle z)
+    for (int e = tid; e < nmz * nmy * TT_X; e += TT_THREADS) {
+        const int fx = e % TT_X, ey = (e / TT_X) % nmy, ez = e / (TT_X * nmy);
+        const int i = xa + fx;
+        if (i >= xb) continue;
+        int xi[3];
+        double xw[3];
+        const int nx = quad_weights(i, n0, xi, xw);
+        double vx = 0.0;
+        for (int a = 0; a < nx; ++a) vx += xw[a] * Ws[ez][ey][xi[a] - mx0];
+        Tx[ez][ey][fx] = vx;
+    }
+    __syncthreads();
+    // along y: vy at (fine x, fine y, middle z)
+    for (int e = tid; e < nmz * TT_Y * TT_X; e += TT_THREADS) {
+        const int fx = e % TT_X, fy = (e / TT_X) % TT_Y, ez = e / (TT_X * TT_Y);
+        const int i = xa + fx, j = ya + fy;
+        if (i >= xb || j >= yb) continue;
+        int yi[3];
+        double yw[3];
+        const int ny = quad_weights(j, n0, yi, yw);
+        double vy = 0.0;
+        for (int b = 0; b < ny; ++b) vy += yw[b] * Tx[ez][yi[b] - my0][fx];
+        Txy[ez][fy][fx] = vy;
+    }
+    __syncthreads();
+    // along z: the fine values
+    for (int e = tid; e < TT_Z * TT_Y * TT_X; e += TT_THREADS) {
+        const int fx = e % TT_X, fy = (e / TT_X) % TT_Y, fz = e / (TT_X * TT_Y);
+        const int i = xa + fx, j = ya + fy, k = za + fz;
+        if (i >= xb || j >= yb || k >= zb) continue;
+        int zi[3];
+        double zw[3];
+        const int nz = quad_weights(k, n0, zi, zw);
+        double v = 0.0;
+        for (int c = 0; c < nz; ++c) v += zw[c] * Txy[zi[c] - mz0][fy][fx];
+        w[nidx(np, i, j, k)] = v;
+    }
 }
 
-__global__ void exp_true_kernel(double* __restrict__ ut, const double* __restrict__ uh,
-                                const double* __restrict__ u2h, int nf) {
-    const int i = blockIdx.x * blockDim.x + threadIdx.x;
-    const int j = blockIdx.y * blockDim.y + threadIdx.y;
-    const int k = blockIdx.z;
+// EXP_true at every fine node of the tile: d = u_h - u_2h at the coarse
+// nodes, then its sums over the 1, 2, 4 or 8 coarse nodes around each fine
+// node, formed along x, then y, then z.
+__global__ void __launch_bounds__(TT_THREADS)
+exp_true_tiled_kernel(double* __restrict__ ut, const double* __restrict__ uh, const double* __restrict__ u2h,
+                      int nf) {
+    __shared__ double Ds[TM_Z][TM_Y][TM_X];
+    __shared__ double Sx[TM_Z][TM_Y][TT_X];
+    __shared__ double Sxy[TM_Z][TT_Y][TT_X];
+    const int tid = threadIdx.x;
     const int np = nf + 1, npc = nf / 2 + 1;
-    if (i >= np || j >= np || k >= np) return;
-    int ci[2], cj[2], ck[2];
-    const int ni = around(i, ci), nj = around(j, cj), nk = around(k, ck);
-    double sum = 0.0;
-    for (int c = 0; c < nk; ++c)
-        for (int b = 0; b < nj; ++b)
-            for (int a = 0; a < ni; ++a)
-                sum += uh[nidx(np, 2 * ci[a], 2 * cj[b], 2 * ck[c])] - u2h[nidx(npc, ci[a], cj[b], ck[c])];
-    // weight 1/(3 * 2^m), m = number of odd coordinates (one table load
-    // instead of an FP64 division per node)
-    const int m = (i & 1) + (j & 1) + (k & 1);
-    const double w = m == 0 ? 1.0 / 3.0 : (m == 1 ? 1.0 / 6.0 : (m == 2 ? 1.0 / 12.0 : 1.0 / 24.0));
-    ut[nidx(np, i, j, k)] = uh[nidx(np, i, j, k)] + sum * w;
+    const int xa = blockIdx.x * TT_X, ya = blockIdx.y * TT_Y, za = blockIdx.z * TT_Z;
+    const int xb = min(xa + TT_X, np), yb = min(ya + TT_Y, np), zb = min(za + TT_Z, np);
+    // coarse nodes around the tile's fine nodes: floor(v/2) .. ceil(v/2)
+    const int cx0 = xa >> 1, cy0 = ya >> 1, cz0 = za >> 1;
+    const int ncx = (xb >> 1) + 1 - cx0, ncy = (yb >> 1) + 1 - cy0, ncz = (zb >> 1) + 1 - cz0;
+    for (int e = tid; e < ncz * ncy * ncx; e += TT_THREADS) {
+        const int ex = e % ncx, ey = (e / ncx) % ncy, ez = e / (ncx * ncy);
+        const int ci = cx0 + ex, cj = cy0 + ey, ck = cz0 + ez;
+        if (ci < npc && cj < npc && ck < npc)
+            Ds[ez][ey][ex] = uh[nidx(np, 2 * ci, 2 * cj, 2 * ck)] - u2h[nidx(npc, ci, cj, ck)];
+    }
+    __syncthreads();
+    for (int e = tid; e < ncz * ncy * TT_X; e += TT_THREADS) {
+        const int fx = e % TT_X, ey = (e / TT_X) % ncy, ez = e / (TT_X * ncy);
+        const int i = xa + fx;
+        if (i >= xb || cy0 + ey >= npc || cz0 + ez >= npc) continue;
+        const int c = (i >> 1) - cx0;
+        Sx[ez][ey][fx] = (i & 1) ? Ds[ez][ey][c] + Ds[ez][ey][c + 1] : Ds[ez][ey][c];
+    }
+    __syncthreads();
+    for (int e = tid; e < ncz * TT_Y * TT_X; e += TT_THREADS) {
+        const int fx = e % TT_X, fy = (e / TT_X) % TT_Y, ez = e / (TT_X * TT_Y);
+        const int i = xa + fx, j = ya + fy;
+        if (i >= xb || j >= yb || cz0 + ez >= npc) continue;
+        const int c = (j >> 1) - cy0;
+        Sxy[ez][fy][fx] = (j & 1) ? Sx[ez][c][fx] + Sx[ez][c + 1][fx] : Sx[ez][c][fx];
+    }
+    __syncthreads();
+    for (int e = tid; e < TT_Z * TT_Y * TT_X; e += TT_THREADS) {
+        const int fx = e % TT_X, fy = (e / TT_X) % TT_Y, fz = e / (TT_X * TT_Y);
+        const int i = xa + fx, j = ya + fy, k = za + fz;
+        if (i >= xb || j >= yb || k >= zb) continue;
+        const int c = (k >> 1) - cz0;
+        const double sum = (k & 1) ? Sxy[c][fy][fx] + Sxy[c + 1][fy][fx] : Sxy[c][fy][fx];
+        const int m = (i & 1) + (j & 1) + (k & 1);
+        const double wt = m == 0 ? 1.0 / 3.0 : (m == 1 ? 1.0 / 6.0 : (m == 2 ? 1.0 / 12.0 : 1.0 / 24.0));
+        const size_t o = nidx(np, i, j, k);
+        ut[o] = uh[o] + sum * wt;
+    }
+}
+
+dim3 tiled_grid(int nf) {
+    const int np = nf + 1;
+    return dim3((np + TT_X - 1) / TT_X, (np + TT_Y - 1) / TT_Y, (np + TT_Z - 1) / TT_Z);
 }
 
 }  // namespace
@@ -134,16 +222,13 @@ cudaError_t launch_exp_finite(double* w, const double* u1, const double* u0, dou
     exp_finite_w_kernel<<<g1, block, 0, s>>>(W_scratch, u1, u0, n1);
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return e;
-    dim3 g2((n_fine + 1 + 31) / 32, (n_fine + 1 + 3) / 4, n_fine + 1);
-    exp_finite_interp_kernel<<<g2, block, 0, s>>>(w, W_scratch, n_fine);
+    exp_finite_interp_tiled_kernel<<<tiled_grid(n_fine), TT_THREADS, 0, s>>>(w, W_scratch, n_fine);
     return cudaGetLastError();
 }
 
 cudaError_t launch_exp_true(double* ut, const double* uh, const double* u2h, int n_fine,
                             cudaStream_t s) {
-    dim3 block(32, 4, 1);
-    dim3 g((n_fine + 1 + 31) / 32, (n_fine + 1 + 3) / 4, n_fine + 1);
-    exp_true_kernel<<<g, block, 0, s>>>(ut, uh, u2h, n_fine);
+    exp_true_tiled_kernel<<<tiled_grid(n_fine), TT_THREADS, 0, s>>>(ut, uh, u2h, n_fine);
     return cudaGetLastError();
 }
 
