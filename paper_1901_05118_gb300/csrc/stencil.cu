@@ -22,6 +22,9 @@
 // diagonal, so this is the same arithmetic; the flag is kept so that A^T is
 // applied as Alg. 2 asks (its shadow recurrence multiplies by A^T).
 #include <initializer_list>
+#include <mutex>
+#include <set>
+#include <utility>
 
 #include "excmg_internal.cuh"
 #include "march_fx.cuh"
@@ -483,6 +486,27 @@ int resident_per_sm(K kernel, int threads, size_t smem = 0) {
     return v > 0 ? v : 1;
 }
 
+// Opt a kernel in to `smem` bytes of dynamic shared memory on the current
+// device.  Function attributes belong to each device's context, so this is
+// done once per (kernel, device) and checked before every staged launch.
+template <typename K>
+void opt_in_smem(K kernel, size_t smem) {
+    static std::mutex mu;
+    static std::set<std::pair<const void*, int>> done;
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess) {
+        cudaGetLastError();
+        return;
+    }
+    const std::pair<const void*, int> key{(const void*)kernel, dev};
+    std::lock_guard<std::mutex> lock(mu);
+    if (done.count(key)) return;
+    if (cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) == cudaSuccess)
+        done.insert(key);
+    else
+        cudaGetLastError();   // the launch then reports the error
+}
+
 // The staged (bulk-copy) march needs n >= 16 (all copied rows then lie in
 // the array) and 16-byte aligned arrays (the copies start on 16-byte
 // boundaries of the array).
@@ -632,9 +656,15 @@ cudaError_t launch_bicg_persistent(double* x, double* r, double* rs, double* p, 
     if (pw)
         fn = elide ? (const void*)bicg_persistent_kernel<true, true, false>
                    : (const void*)bicg_persistent_kernel<true, false, false>;
-    else if (fuse)
-        fn = elide ? (const void*)bicg_persistent_kernel<false, true, true>
-                   : (const void*)bicg_persistent_kernel<false, false, true>;
+    else if (fuse) {
+        if (elide) {
+            opt_in_smem(bicg_persistent_kernel<false, true, true>, persistent_stage_bytes());
+            fn = (const void*)bicg_persistent_kernel<false, true, true>;
+        } else {
+            opt_in_smem(bicg_persistent_kernel<false, false, true>, persistent_stage_bytes());
+            fn = (const void*)bicg_persistent_kernel<false, false, true>;
+        }
+    }
     else
         fn = elide ? (const void*)bicg_persistent_kernel<false, true, false>
                    : (const void*)bicg_persistent_kernel<false, false, false>;
@@ -649,6 +679,7 @@ cudaError_t launch_bicg_stencil_pair_dir(const double* r, const double* rs, cons
     const int sg = bc_kind == 1 ? 1 : -1;
     if (bulk_ok(n, {r, rs, p_prev, ps_prev})) {
         const StencilGrid g = fx_grid(n, 5);
+        opt_in_smem(stencil_fx_kernel<2, true, true, true>, g.smem);
         stencil_fx_kernel<2, true, true, true><<<g.grid, g.block, g.smem, s>>>(fl, nullptr, n, sg, g.kz_per_cta,
                                                                                &st->done, partials, st);
     } else {
@@ -665,6 +696,7 @@ cudaError_t launch_bicg_stencil_pair(const double* p, double* q, const double* p
     const int sg = bc_kind == 1 ? 1 : -1;
     if (staged && bulk_ok(n, {p, ps})) {
         const StencilGrid g = fx_grid(n, 4);
+        opt_in_smem(stencil_fx_kernel<2, true, false, true>, g.smem);
         stencil_fx_kernel<2, true, false, true><<<g.grid, g.block, g.smem, s>>>(fl, nullptr, n, sg, g.kz_per_cta,
                                                                                 &st->done, partials, st);
     } else {
@@ -681,6 +713,7 @@ cudaError_t launch_cg_stencil(const double* p, double* q, int n, int bc_kind, do
     const int sg = bc_kind == 1 ? 1 : -1;
     if (staged && bulk_ok(n, {p})) {
         const StencilGrid g = fx_grid(n, 6);
+        opt_in_smem(stencil_fx_kernel<1, true, false, true>, g.smem);
         stencil_fx_kernel<1, true, false, true><<<g.grid, g.block, g.smem, s>>>(fl, nullptr, n, sg, g.kz_per_cta,
                                                                                 &st->done, partials, st);
     } else {
@@ -697,6 +730,7 @@ cudaError_t launch_cg_stencil_dir(const double* r, const double* p_prev, double*
     const int sg = bc_kind == 1 ? 1 : -1;
     if (bulk_ok(n, {r, p_prev})) {
         const StencilGrid g = fx_grid(n, 7);
+        opt_in_smem(stencil_fx_kernel<1, true, true, true>, g.smem);
         stencil_fx_kernel<1, true, true, true><<<g.grid, g.block, g.smem, s>>>(fl, nullptr, n, sg, g.kz_per_cta,
                                                                                &st->done, partials, st);
     } else {
