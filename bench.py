@@ -64,6 +64,11 @@ def parse(argv=None):
     ap.add_argument("--serve-precision", choices=["fp64", "mixed"], default="fp64")
     ap.add_argument("--oracle-report", action="store_true",
                     help="time the CPU oracle on the small workload and one 512^3 operator application, then exit")
+    ap.add_argument("--case", choices=["stencil", "bicg", "solve"],
+                    help="run one small fixed case for a profiler capture (sizes from --n / --nc) and exit")
+    ap.add_argument("--bc", type=int, default=1, help="--case: kind of boundary data")
+    ap.add_argument("--iters", type=int, default=4, help="--case bicg: Bi-CG iterations")
+    ap.add_argument("--reps", type=int, default=3, help="--case stencil: operator applications")
     return ap.parse_args(argv)
 
 
@@ -613,8 +618,47 @@ def oracle_report():
                       "cores": 1, "host_cpus": os.cpu_count()}), flush=True)
 
 
+def profile_case(args):
+    """A small, fixed GPU case for profiling single kernels: `stencil` (reps
+    operator applications), `bicg` (iters Bi-CG iterations from x = 0 on a
+    random right-hand side) or `solve` (one EXCMG solve of u = e^(x+y+z)).
+    At n = 256 the inputs are still larger than L2 and a capture of a few
+    launches ends quickly."""
+    import torch
+
+    from paper_1901_05118_gb300 import binding as B, problems
+
+    dev = torch.device("cuda", 0)
+    torch.cuda.set_device(dev)
+    ctx = B.Context(dev)
+    ctx.set_stencil(args.stencil)
+    ctx.set_schedule(args.schedule)
+    n = args.n
+    gen = torch.Generator(device=dev)
+    gen.manual_seed(0)
+    if args.case == "stencil":
+        u = torch.rand((n + 1,) * 3, dtype=torch.float64, device=dev, generator=gen)
+        y = torch.empty_like(u)
+        lvl = B.Level(n, args.bc, ctx)
+        for _ in range(args.reps):
+            B.stencil_apply(lvl, u, y)
+    elif args.case == "bicg":
+        b = torch.rand((n + 1,) * 3, dtype=torch.float64, device=dev, generator=gen)
+        x = torch.zeros_like(b)
+        lvl = B.Level(n, args.bc, ctx)
+        B.bicg_solve(lvl, b, x, 0.0, args.iters)
+    else:
+        f, g1, g2 = (torch.from_numpy(v).to(dev) for v in problems.exp_sum().data(n, args.bc))
+        B.excmg_solve(n, args.nc, args.bc, f, g1, g2, args.tol, ctx=ctx)
+    torch.cuda.synchronize()
+    print(json.dumps({"case": args.case, "n": n, "ok": True}), flush=True)
+
+
 def main():
     args = parse()
+    if args.case:
+        profile_case(args)
+        return
     if args.oracle_report:
         oracle_report()
         return

@@ -19,11 +19,19 @@
  * never frees or keeps it beyond the call.  The library allocates its own
  * workspace (cudaMalloc) inside a context and frees it in excmg_ctx_destroy.
  *
- * Streams: a context is bound to one CUDA stream.  Calls enqueue work on
- * that stream and return after the results are complete on it (the solver
- * reads a few scalars back to steer its loops); the caller's inputs must be
- * ready on that stream.  Calls without a context use a per-device default
- * context on the legacy default stream (stream 0).
+ * Streams and synchronisation: a context is bound to one CUDA stream.
+ * Calls enqueue their kernels on that stream; the caller's inputs must be
+ * ready on it.  Every call is synchronous with respect to the host: it
+ * returns once its results are complete on the stream, and its status
+ * covers the device-side outcome of its own kernels (a Bi-CG breakdown, a
+ * non-finite residual, a bounded device wait that gave up).  This differs
+ * from an asynchronous convention with errors latched on the device and
+ * reported at a later call, for two reasons: the WHILE loop of Alg. 1 and
+ * the stopping test of Alg. 2 are steered by scalars the host reads back
+ * between batches of Bi-CG iterations, so a solve cannot run ahead of the
+ * host anyway; and a synchronous status names the call that failed.  Calls
+ * without a context use a per-device default context on the legacy default
+ * stream (stream 0).
  *
  * Errors: every call returns an excmg_status; nothing throws across the ABI.
  * excmg_last_error() gives a message for the last failing call on a context
@@ -49,7 +57,8 @@ typedef enum {
     EXCMG_ERR_CUDA = -6,       /* a CUDA runtime call or kernel launch failed                */
     EXCMG_ERR_TIMEOUT = -7,    /* a bounded device-side wait gave up                         */
     EXCMG_ERR_BUDGET = -9,     /* the context's HBM budget is too small for the request      */
-    EXCMG_ERR_SIZE = -10       /* a size beyond the fixed maximum of an allocation-free call */
+    EXCMG_ERR_SIZE = -10,      /* a size beyond the fixed maximum of an allocation-free call */
+    EXCMG_ERR_TOO_LARGE = -11  /* one batch instance needs more than the batch's whole budget */
 } excmg_status;
 
 typedef struct excmg_ctx excmg_ctx;      /* device, stream, workspace, DSOLVE factor cache */
@@ -194,14 +203,20 @@ int bicg_solve(const excmg_level *level, const double *b, double *x_inout, doubl
 int bicg_solve_ex(const excmg_level *level, const double *b, double *x_inout, const double *shadow_r0,
                   double tol, int max_iter, int *iters_out, double *relres_out);
 
-/* EXP_finite (Sec. 4.2.2-4.2.3, Steps 1-5): third-order approximation w_h on
- * the grid with n_fine intervals (n_fine divisible by 4, >= 8) of the FD
- * solution, from the FD solutions u_2h (n_fine/2 intervals) and u_4h
- * (n_fine/4 intervals).  Every node of w_h is written, boundary nodes
- * included (interpolated values). */
-int extrapolate_interpolate(int n_fine, const double *u_2h, const double *u_4h, double *w_h);
+/* EXP_finite (Sec. 4.2.2-4.2.3, Steps 1-5; Alg. 1 line 6): third-order
+ * approximation w_h on the grid with n_fine intervals (n_fine divisible by
+ * 4, >= 8) of the FD solution, from the FD solutions u_2h (n_fine/2
+ * intervals) and u_4h (n_fine/4 intervals), all node arrays.  Steps 1-5 give
+ * every node of w_h, boundary nodes included.  g1_fine: a node array on the
+ * fine grid whose boundary entries (the Dirichlet data u = g1) then
+ * overwrite w_h's boundary nodes, as Alg. 1 does before Bi-CG; NULL keeps the
+ * interpolated boundary values (the distances ||w_h - u_h|| printed in the
+ * paper's tables are those of the interpolated values).  Interior nodes do
+ * not depend on g1_fine. */
+int extrapolate_interpolate(int n_fine, const double *u_2h, const double *u_4h, const double *g1_fine,
+                            double *w_h);
 
-/* EXP_finite as above, allocating nothing (the paper has no counterpart: it
+/* EXP_finite as above with g1_fine = NULL, allocating nothing (the paper has no counterpart: it
  * is a service for callers that cannot allocate device memory at this point
  * -- memory owned entirely by an arena or planner, a hard device-memory
  * budget, or a path where entering the CUDA allocator, which may synchronise
@@ -210,8 +225,10 @@ int extrapolate_interpolate(int n_fine, const double *u_2h, const double *u_4h, 
  * process exits), so n_fine is limited to 128; larger sizes return
  * EXCMG_ERR_SIZE.  The caller passes inputs and output as for
  * extrapolate_interpolate.  Runs on the legacy default stream and returns
- * when the result is complete.  The first call on a device looks up the
- * array's device address; make that first call before any stream capture.
+ * when the result is complete.  Every call looks up the array's device
+ * address on the current device; the first call on a device also loads the
+ * library's device code there, so make that first call before any stream
+ * capture.
  * All calls share the one array: calls that overlap on the GPU (other host
  * threads, other streams) race and must be serialised by the caller. */
 int extrapolate_interpolate_noalloc(int n_fine, const double *u_2h, const double *u_4h, double *w_h);
@@ -241,7 +258,7 @@ int excmg_solve_ex(excmg_ctx *ctx, int n_finest, int n_coarsest, int bc_kind, co
 
 /* Context forms of the two transfer steps (same semantics, ctx's stream). */
 int extrapolate_interpolate_ex(excmg_ctx *ctx, int n_fine, const double *u_2h, const double *u_4h,
-                               double *w_h);
+                               const double *g1_fine, double *w_h);
 int midpoint_extrapolate_ex(excmg_ctx *ctx, int n_fine, const double *u_h, const double *u_2h,
                             double *u_tilde);
 
@@ -255,7 +272,8 @@ int excmg_assemble_rhs(const excmg_level *level, int n_src, const double *f, con
 
 /* DSOLVE (Alg. 1, lines 1-2): u = A_h^{-1} fh on the level's interior nodes
  * (u's boundary entries left unchanged).  The first call on a (N, bc_kind)
- * factorises A_h (dense Gauss-Jordan inverse, kept in the context); N <= 32. */
+ * factorises A_h (dense Gauss-Jordan inverse, kept in the context); 4 <= N <= 16
+ * (at most 15^3 = 3375 unknowns, a 91 MB inverse), else EXCMG_ERR_ARG. */
 int excmg_dsolve(const excmg_level *level, const double *fh, double *u);
 
 /* ------------------------------------------------------ many solves at once */
@@ -283,7 +301,9 @@ size_t excmg_batch_instance_bytes(int n_finest, int n_coarsest, int precision);
  * FP64 or mixed; max_iter caps one Bi-CG call, inner_tol is used in mixed
  * mode).  f, g1, g2 and u_out must stay valid until the instance is done;
  * u_out receives u_tilde.  Returns EXCMG_ERR_BUDGET (nothing admitted) when
- * the budget or the slot count is full -- submit again after a step. */
+ * the budget or the slot count is full right now -- submit again after a
+ * step -- and EXCMG_ERR_TOO_LARGE when the instance alone needs more than
+ * the whole budget, so that it can never be admitted. */
 int excmg_batch_submit(excmg_batch *batch, int n_finest, int n_coarsest, int bc_kind, const double *f,
                        const double *g1, const double *g2, const excmg_params *params, double *u_out,
                        int *id_out);
@@ -300,6 +320,22 @@ int excmg_batch_query(excmg_batch *batch, int id, int *done, int *status, excmg_
                       double *latency_s);
 /* Kernel launches made by the batch so far. */
 long long excmg_batch_launches(const excmg_batch *batch);
+
+/* ------------------------------------------------------------- diagnostics */
+
+/* Failure-path self-test (the paper has no counterpart): makes one of the
+ * library's bounded device-side waits run out on purpose -- without a fault,
+ * trap or hang -- so that the path that reports EXCMG_ERR_TIMEOUT can be
+ * tested.  which = 0: the grid barrier of the cooperative kernels; a
+ * cooperative launch of 8 CTAs waits for a ninth arrival that never comes,
+ * and each CTA gives up after `limit` polls (at least 32 ns each).
+ * which = 1: the mbarrier wait of the staged loads; one arrival of two, and
+ * the wait gives up after `limit` nanoseconds.  1 <= limit <= 10^8.
+ * Returns EXCMG_ERR_TIMEOUT when the wait gave up as designed, EXCMG_OK if it
+ * did not (the mechanism failed), EXCMG_ERR_ARG, or EXCMG_ERR_CUDA.  Uses
+ * fixed device memory (allocates nothing), runs on the legacy default stream
+ * and returns when done. */
+int excmg_selftest_wait_timeout(int which, long long limit);
 
 #ifdef __cplusplus
 }

@@ -28,7 +28,8 @@ _lib = ctypes.CDLL(LIB_PATH)
 EXCMG_OK = 0
 STATUS_NAMES = {0: "EXCMG_OK", -1: "EXCMG_ERR_ARG", -2: "EXCMG_ERR_OOM", -3: "EXCMG_ERR_BREAKDOWN",
                 -4: "EXCMG_ERR_NOCONV", -5: "EXCMG_ERR_NAN", -6: "EXCMG_ERR_CUDA",
-                -7: "EXCMG_ERR_TIMEOUT", -9: "EXCMG_ERR_BUDGET", -10: "EXCMG_ERR_SIZE"}
+                -7: "EXCMG_ERR_TIMEOUT", -9: "EXCMG_ERR_BUDGET", -10: "EXCMG_ERR_SIZE",
+                -11: "EXCMG_ERR_TOO_LARGE"}
 TOL_MODES = {"paper": 0, "uniform": 1}
 STENCIL_VARIANTS = {"exact": 0, "fp64": 1}
 SHADOW_MODES = {"full": 0, "elided": 1}
@@ -83,8 +84,8 @@ _lib.excmg_level_destroy.argtypes = [_vp]
 _lib.stencil_apply.argtypes = [_vp, _i, _vp, _vp]
 _lib.bicg_solve.argtypes = [_vp, _vp, _vp, _d, _i, ctypes.POINTER(_i), ctypes.POINTER(_d)]
 _lib.bicg_solve_ex.argtypes = [_vp, _vp, _vp, _vp, _d, _i, ctypes.POINTER(_i), ctypes.POINTER(_d)]
-_lib.extrapolate_interpolate.argtypes = [_i, _vp, _vp, _vp]
-_lib.extrapolate_interpolate_ex.argtypes = [_vp, _i, _vp, _vp, _vp]
+_lib.extrapolate_interpolate.argtypes = [_i, _vp, _vp, _vp, _vp]
+_lib.extrapolate_interpolate_ex.argtypes = [_vp, _i, _vp, _vp, _vp, _vp]
 _lib.midpoint_extrapolate.argtypes = [_i, _vp, _vp, _vp]
 _lib.midpoint_extrapolate_ex.argtypes = [_vp, _i, _vp, _vp, _vp]
 _lib.excmg_solve.argtypes = [_i, _i, _i, _vp, _vp, _vp, _d, _vp]
@@ -108,6 +109,8 @@ _lib.excmg_batch_query.argtypes = [_vp, _i, ctypes.POINTER(_i), ctypes.POINTER(_
                                    ctypes.POINTER(_d)]
 _lib.excmg_batch_launches.argtypes = [_vp]
 _lib.excmg_batch_launches.restype = ctypes.c_longlong
+_lib.excmg_selftest_wait_timeout.argtypes = [_i, ctypes.c_longlong]
+_lib.excmg_selftest_wait_timeout.restype = _i
 
 for _name in ("excmg_batch_create", "excmg_batch_destroy", "excmg_batch_submit", "excmg_batch_step",
               "excmg_batch_query"):
@@ -129,6 +132,13 @@ def lib():
 def launch_count() -> int:
     """Kernel launches the library has made in this process."""
     return int(_lib.excmg_launch_count())
+
+
+def selftest_wait_timeout(which: str, limit: int) -> int:
+    """Make a bounded device wait run out on purpose ('barrier': the grid
+    barrier, limit in polls; 'mbarrier': the staged-load wait, limit in ns).
+    Returns the library status (-7, EXCMG_ERR_TIMEOUT, when it gave up)."""
+    return int(_lib.excmg_selftest_wait_timeout({"barrier": 0, "mbarrier": 1}[which], int(limit)))
 
 
 # ----------------------------------------------------------------- checks
@@ -290,14 +300,18 @@ def bicg_solve(level: Level, b: torch.Tensor, x: torch.Tensor, tol: float, max_i
 
 
 def extrapolate_interpolate(n_fine: int, u_2h: torch.Tensor, u_4h: torch.Tensor,
-                            w_h: torch.Tensor | None = None, ctx: Context | None = None) -> torch.Tensor:
-    """EXP_finite: third-order guess on the n_fine grid from u_2h and u_4h."""
+                            w_h: torch.Tensor | None = None, ctx: Context | None = None,
+                            g1_fine: torch.Tensor | None = None) -> torch.Tensor:
+    """EXP_finite: third-order guess on the n_fine grid from u_2h and u_4h.
+    With g1_fine (a fine-grid node array) its boundary entries overwrite
+    w_h's boundary nodes; without it they keep the interpolated values."""
     ctx = ctx or default_context(u_2h.device)
     p2 = _node(u_2h, n_fine // 2, "u_2h")
     p4 = _node(u_4h, n_fine // 4, "u_4h")
+    pg = _vp(_node(g1_fine, n_fine, "g1_fine")) if g1_fine is not None else _vp(0)
     if w_h is None:
         w_h = _new_node(n_fine, u_2h)
-    ctx.check(_lib.extrapolate_interpolate_ex(ctx.handle, int(n_fine), _vp(p2), _vp(p4),
+    ctx.check(_lib.extrapolate_interpolate_ex(ctx.handle, int(n_fine), _vp(p2), _vp(p4), pg,
                                               _vp(_node(w_h, n_fine, "w_h"))), "extrapolate_interpolate")
     return w_h
 
@@ -398,7 +412,8 @@ class Batch:
                precision: str = "mixed", inner_tol: float = MIXED_INNER_TOL, max_iter: int | None = None,
                max_total: int = 1000000):
         """Admit one solve; returns (id, u_out), or None when the budget or the
-        slots are full right now."""
+        slots are full right now.  Raises ExcmgError (EXCMG_ERR_TOO_LARGE) for
+        an instance that needs more than the whole budget."""
         n = int(n_finest)
         if u_out is None:
             u_out = _new_node(n, f)

@@ -22,6 +22,7 @@
 #include <vector>
 
 #include "excmg_internal.cuh"
+#include "grid_sync.cuh"
 #include "march_f32.cuh"
 #include "march_fx.cuh"
 #include "reduce.cuh"
@@ -60,40 +61,6 @@ struct BatchState {    // device, one per slot
     unsigned int ticket_a, ticket_b;
 };
 
-struct BatchBarrier {
-    unsigned int* count;
-    unsigned int* gen;
-    int* err;
-};
-
-__device__ bool batch_sync(const BatchBarrier& gb, unsigned int nblocks) {
-    __syncthreads();
-    if (thread0()) {
-        volatile unsigned int* gen = gb.gen;
-        volatile int* err = gb.err;
-        const unsigned int g = *gen;
-        __threadfence();
-        if (atomicAdd(gb.count, 1u) == nblocks - 1u) {
-            atomicExch(gb.count, 0u);
-            __threadfence();
-            atomicAdd(gb.gen, 1u);
-        } else {
-            long long spins = 0;
-            while (*gen == g) {
-                if (*err) break;
-                if (++spins > (1ll << 22)) {
-                    atomicExch(gb.err, 1);
-                    break;
-                }
-                __nanosleep(32);
-            }
-        }
-        __threadfence();
-    }
-    __syncthreads();
-    return *(volatile int*)gb.err == 0;
-}
-
 // Instance owning global index g, given each instance's first index.
 __device__ __forceinline__ int owner(const int* begin, int ninst, int g) {
     int lo = 0, hi = ninst - 1;
@@ -130,7 +97,7 @@ __global__ void __launch_bounds__(S_NT)
 batch_bicg_kernel(const BatchInst<T>* __restrict__ inst, const int* __restrict__ unit_begin,
                     const int* __restrict__ chunk_begin, int ninst, int total_units, int total_chunks,
                     double* unit_part, double* chunk_part, BatchState* states, int iters, int* active,
-                    BatchBarrier gb) {
+                    GridBarrier gb) {
     __shared__ double sh[32];
     __shared__ T shf[32];
     __shared__ bool flag;
@@ -167,7 +134,7 @@ batch_bicg_kernel(const BatchInst<T>* __restrict__ inst, const int* __restrict__
                 }
             }
         }
-        if (!(ok = batch_sync(gb, G))) break;
+        if (!(ok = grid_sync(gb, G))) break;
         // phase B: x += alpha p; r -= alpha q; r* -= alpha q*; per-chunk
         // (r*, r), (r, r); the CTA finishing the last chunk forms beta and
         // tests convergence
@@ -216,7 +183,7 @@ batch_bicg_kernel(const BatchInst<T>* __restrict__ inst, const int* __restrict__
                 }
             }
         }
-        if (!(ok = batch_sync(gb, G))) break;
+        if (!(ok = grid_sync(gb, G))) break;
         // the counter changes only in phases A and B: between this barrier
         // and the next every CTA reads the same value
         if (*(volatile int*)active <= 0) break;
@@ -234,7 +201,7 @@ batch_bicg_kernel(const BatchInst<T>* __restrict__ inst, const int* __restrict__
                 in.ps[t] = in.rs[t] + beta * in.ps[t];
             }
         }
-        if (!(ok = batch_sync(gb, G))) break;
+        if (!(ok = grid_sync(gb, G))) break;
     }
     if (!ok && blockIdx.x == 0 && thread0()) *active = -1;   // barrier gave up
 }
@@ -283,18 +250,11 @@ batch_correct_kernel(double* __restrict__ u, const float* __restrict__ e, size_t
         u[t] = u[t] + s * (double)e[t];
 }
 
+// The cooperative grid: every SM of the current device, at most two CTAs each.
 template <typename T>
 int batch_resident_ctas() {
-    static int occ = 0;
-    if (!occ) {
-        if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, batch_bicg_kernel<T>, S_NT, 0) != cudaSuccess) {
-            cudaGetLastError();
-            occ = 1;
-        }
-        if (occ < 1) occ = 1;
-        if (occ > 2) occ = 2;
-    }
-    return 152 * occ;
+    const int occ = min(2, kernel_occupancy((const void*)batch_bicg_kernel<T>, S_NT, 0));
+    return device_sms() * occ;
 }
 
 }  // namespace
@@ -572,7 +532,7 @@ int run_batched(excmg_batch* b, const std::vector<Instance*>& list, BatchInst<T>
     double* cp = b->d_chunk_part;
     BatchState* sts = b->d_states;
     int* act = b->d_active;
-    BatchBarrier gb{b->d_barrier, b->d_barrier + 1, (int*)(b->d_barrier + 2)};
+    GridBarrier gb{b->d_barrier, b->d_barrier + 1, (int*)(b->d_barrier + 2), kBarrierSpinLimit};
     void* args[] = {(void*)&di, (void*)&d_ub, (void*)&d_cb, (void*)&ninst, (void*)&units, (void*)&chunks,
                     (void*)&up, (void*)&cp, (void*)&sts, (void*)&iters, (void*)&act, (void*)&gb};
     e = cudaLaunchCooperativeKernel((const void*)batch_bicg_kernel<T>, dim3(G), dim3(S_TX, S_TY, 1), args, 0, s);
@@ -677,9 +637,11 @@ int excmg_batch_submit(excmg_batch* b, int n_finest, int n_coarsest, int bc_kind
     if (!(params->tol > 0.0) || params->max_iter < 1 || params->max_total < 1 ||
         (params->precision == EXCMG_PRECISION_MIXED && !(params->inner_tol > 0.0 && params->inner_tol < 1.0)))
         return bfail(b, EXCMG_ERR_ARG, "bad parameters");
-    if ((int)b->live.size() >= b->max_instances) return bfail(b, EXCMG_ERR_BUDGET, "all instance slots are busy");
     const int prec = params->precision;
     const size_t need = instance_bytes(n_finest, n_coarsest, prec);
+    if (b->budget && need > b->budget)
+        return bfail(b, EXCMG_ERR_TOO_LARGE, "the instance needs more device memory than the batch's whole budget");
+    if ((int)b->live.size() >= b->max_instances) return bfail(b, EXCMG_ERR_BUDGET, "all instance slots are busy");
     if (b->budget && b->bytes + need > b->budget)
         return bfail(b, EXCMG_ERR_BUDGET, "device-memory budget of the batch is full");
     Instance* in = new (std::nothrow) Instance();

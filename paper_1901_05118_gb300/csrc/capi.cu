@@ -4,7 +4,9 @@
 #include <cstdio>
 #include <cstring>
 #include <atomic>
+#include <map>
 #include <mutex>
+#include <tuple>
 
 #include "excmg_internal.cuh"
 
@@ -14,6 +16,55 @@ namespace excmg {
 
 static std::atomic<long long> g_launches{0};
 void note_launches(long long k) { g_launches.fetch_add(k, std::memory_order_relaxed); }
+
+namespace {
+std::mutex g_dev_mu;
+std::map<int, int> g_sms;
+std::map<std::tuple<const void*, int, int, size_t>, int> g_occ;
+}  // namespace
+
+int device_sms() {
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess) {
+        cudaGetLastError();
+        return 1;
+    }
+    std::lock_guard<std::mutex> lock(g_dev_mu);
+    auto it = g_sms.find(dev);
+    if (it != g_sms.end()) return it->second;
+    int v = 0;
+    if (cudaDeviceGetAttribute(&v, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess || v < 1) {
+        cudaGetLastError();
+        return 1;   // not cached: the next call asks again
+    }
+    g_sms[dev] = v;
+    return v;
+}
+
+int kernel_occupancy(const void* kernel, int threads, size_t smem) {
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess) {
+        cudaGetLastError();
+        return 1;
+    }
+    const auto key = std::make_tuple(kernel, dev, threads, smem);
+    std::lock_guard<std::mutex> lock(g_dev_mu);
+    auto it = g_occ.find(key);
+    if (it != g_occ.end()) return it->second;
+    if (smem > 48 * 1024 &&
+        cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) != cudaSuccess) {
+        cudaGetLastError();
+        return 1;   // not cached; the launch reports the error
+    }
+    int v = 0;
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&v, kernel, threads, smem) != cudaSuccess) {
+        cudaGetLastError();
+        return 1;
+    }
+    if (v < 1) v = 1;
+    g_occ[key] = v;
+    return v;
+}
 
 int ctx_fail(excmg_ctx* ctx, int status, const std::string& msg) {
     if (ctx) ctx->last_error = msg;
@@ -242,7 +293,7 @@ int bicg_solve_ex(const excmg_level* level, const double* b, double* x_inout, co
 }
 
 int extrapolate_interpolate_ex(excmg_ctx* ctx, int n_fine, const double* u_2h, const double* u_4h,
-                               double* w_h) {
+                               const double* g1_fine, double* w_h) {
     if (!ctx) ctx = default_ctx();
     if (!ctx) return EXCMG_ERR_CUDA;
     if (n_fine < 8 || n_fine % 4 || !u_2h || !u_4h || !w_h)
@@ -252,12 +303,18 @@ int extrapolate_interpolate_ex(excmg_ctx* ctx, int n_fine, const double* u_2h, c
     if (st) return st;
     cudaError_t e = launch_exp_finite(w_h, u_2h, u_4h, W, n_fine, ctx->stream);
     note_launches(2);
+    // Alg. 1: the boundary nodes of the next level carry the Dirichlet data
+    if (e == cudaSuccess && g1_fine) {
+        e = launch_set_boundary(w_h, n_fine, g1_fine, 1, ctx->stream);
+        note_launches(1);
+    }
     if (e == cudaSuccess) e = cudaStreamSynchronize(ctx->stream);
     return ctx_cuda(ctx, e, "extrapolate_interpolate");
 }
 
-int extrapolate_interpolate(int n_fine, const double* u_2h, const double* u_4h, double* w_h) {
-    return extrapolate_interpolate_ex(nullptr, n_fine, u_2h, u_4h, w_h);
+int extrapolate_interpolate(int n_fine, const double* u_2h, const double* u_4h, const double* g1_fine,
+                            double* w_h) {
+    return extrapolate_interpolate_ex(nullptr, n_fine, u_2h, u_4h, g1_fine, w_h);
 }
 
 int midpoint_extrapolate_ex(excmg_ctx* ctx, int n_fine, const double* u_h, const double* u_2h,
@@ -353,11 +410,19 @@ int excmg_solve_ex(excmg_ctx* ctx, int n_finest, int n_coarsest, int bc_kind, co
         note_launches(l >= 2 ? 4 : 2);
         if (e != cudaSuccess) { result = ctx_cuda(ctx, e, "level setup"); break; }
         if ((result = interior_norm(ctx, N, fh, &fnorm))) break;
+        if (!std::isfinite(fnorm)) {
+            result = ctx_fail(ctx, EXCMG_ERR_NAN, "right-hand side f_h is not finite");
+            break;
+        }
         if (l <= 1) {
             // Alg. 1, lines 1-2
             if ((result = dsolve_run(ctx, N, bc_kind, fh, u))) break;
             if ((result = true_residual_norm(ctx, N, bc_kind, fh, u, &rn))) break;
             rel = fnorm > 0.0 ? rn / fnorm : 0.0;
+            if (!std::isfinite(rel)) {
+                result = ctx_fail(ctx, EXCMG_ERR_NAN, "residual of the direct solve is not finite");
+                break;
+            }
         } else {
             const int i = l - 1;   // Alg. 1 loop counter 1..L
             const double eps = params->tol_mode == EXCMG_TOL_PAPER ? params->tol * std::pow(10.0, (double)(i - L))
@@ -370,6 +435,10 @@ int excmg_solve_ex(excmg_ctx* ctx, int n_finest, int n_coarsest, int bc_kind, co
             }
             if ((result = true_residual_norm(ctx, N, bc_kind, fh, u, &rn))) break;
             rel = fnorm > 0.0 ? rn / fnorm : 0.0;
+            if (!std::isfinite(rel)) {
+                result = ctx_fail(ctx, EXCMG_ERR_NAN, "residual of the initial guess is not finite");
+                break;
+            }
             // Alg. 1, lines 7-9
             while (rel > eps && iters < params->max_total) {
                 int it = 0;

@@ -182,6 +182,15 @@ struct excmg_level {
 namespace excmg {
 // Process-wide count of kernel launches made by the library (capi.cu).
 void note_launches(long long k);
+// Streaming multiprocessors of the current device (read once per device).
+int device_sms();
+// Resident CTAs per SM of `kernel` (a __global__ function) with `threads`
+// threads and `smem` bytes of dynamic shared memory on the current device,
+// at least 1.  Kernels that need more than 48 KB of dynamic shared memory are
+// opted in to it on the current device first.  Cached per (kernel, device,
+// threads, smem) under a lock: function attributes and occupancy belong to
+// each device's context.
+int kernel_occupancy(const void* kernel, int threads, size_t smem);
 // Workspace helpers (capi.cu).
 int ctx_fail(excmg_ctx* ctx, int status, const std::string& msg);
 int ctx_cuda(excmg_ctx* ctx, cudaError_t err, const char* what);

@@ -22,11 +22,10 @@
 // diagonal, so this is the same arithmetic; the flag is kept so that A^T is
 // applied as Alg. 2 asks (its shadow recurrence multiplies by A^T).
 #include <initializer_list>
-#include <mutex>
-#include <set>
 #include <utility>
 
 #include "excmg_internal.cuh"
+#include "grid_sync.cuh"
 #include "march_fx.cuh"
 #include "reduce.cuh"
 
@@ -198,42 +197,6 @@ struct BicgVectors {
     double* q;
     double* qs;
 };
-
-struct GridBarrier {
-    unsigned int* count;
-    unsigned int* gen;
-    int* err;
-};
-
-constexpr long long kBarrierSpinLimit = 1ll << 22;   // x >= 32 ns each: well over 0.1 s
-
-__device__ bool grid_sync(const GridBarrier& gb, unsigned int nblocks) {
-    __syncthreads();
-    if (thread0()) {
-        volatile unsigned int* gen = gb.gen;
-        volatile int* err = gb.err;
-        const unsigned int g = *gen;
-        __threadfence();
-        if (atomicAdd(gb.count, 1u) == nblocks - 1u) {
-            atomicExch(gb.count, 0u);
-            __threadfence();
-            atomicAdd(gb.gen, 1u);
-        } else {
-            long long spins = 0;
-            while (*gen == g) {
-                if (*err) break;
-                if (++spins > kBarrierSpinLimit) {
-                    atomicExch(gb.err, 1);
-                    break;
-                }
-                __nanosleep(32);
-            }
-        }
-        __threadfence();
-    }
-    __syncthreads();
-    return *(volatile int*)gb.err == 0;
-}
 
 // Sum of component c of the per-CTA partials, in CTA order (every CTA).
 __device__ __forceinline__ double all_partials(const double* partials, int c, double* sh) {
@@ -443,14 +406,14 @@ struct StencilGrid {
 };
 
 // Column tiles x z-slabs.  The slab count is chosen so that the CTAs fill
-// whole waves of the GPU's resident slots (152 SMs x CTAs per SM) while each
+// whole waves of the GPU's resident slots (SMs x CTAs per SM) while each
 // slab stays long enough that its 4 extra halo planes cost little.
 StencilGrid stencil_grid(int n, int tx, int rows, int per_sm) {
     const int m = n - 1;  // interior extent
     StencilGrid g;
     const int gx = (m + tx - 1) / tx, gy = (m + rows - 1) / rows;
     const int tiles = gx * gy;
-    const int slots = 152 * (per_sm > 0 ? per_sm : 1);
+    const int slots = device_sms() * (per_sm > 0 ? per_sm : 1);
     int best = 1;
     double best_eff = -1.0;
     for (int slabs = 1; slabs <= 64; ++slabs) {
@@ -471,40 +434,18 @@ StencilGrid stencil_grid(int n, int tx, int rows, int per_sm) {
     return g;
 }
 
+// Resident CTAs per SM of a kernel on the current device (cached per
+// kernel and device; opts the kernel in to `smem` bytes of dynamic shared
+// memory there first).  Function attributes belong to each device's
+// context, so the staged launches call this before every launch.
 template <typename K>
 int resident_per_sm(K kernel, int threads, size_t smem = 0) {
-    int v = 0;
-    if (smem > 0 &&
-        cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) != cudaSuccess) {
-        cudaGetLastError();
-        return 1;
-    }
-    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&v, kernel, threads, smem) != cudaSuccess) {
-        cudaGetLastError();
-        v = 1;
-    }
-    return v > 0 ? v : 1;
+    return kernel_occupancy((const void*)kernel, threads, smem);
 }
 
-// Opt a kernel in to `smem` bytes of dynamic shared memory on the current
-// device.  Function attributes belong to each device's context, so this is
-// done once per (kernel, device) and checked before every staged launch.
 template <typename K>
 void opt_in_smem(K kernel, size_t smem) {
-    static std::mutex mu;
-    static std::set<std::pair<const void*, int>> done;
-    int dev = 0;
-    if (cudaGetDevice(&dev) != cudaSuccess) {
-        cudaGetLastError();
-        return;
-    }
-    const std::pair<const void*, int> key{(const void*)kernel, dev};
-    std::lock_guard<std::mutex> lock(mu);
-    if (done.count(key)) return;
-    if (cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) == cudaSuccess)
-        done.insert(key);
-    else
-        cudaGetLastError();   // the launch then reports the error
+    (void)kernel_occupancy((const void*)kernel, FX_NT, smem);
 }
 
 // The staged (bulk-copy) march needs n >= 16 (all copied rows then lie in
@@ -518,16 +459,14 @@ bool bulk_ok(int n, std::initializer_list<const double*> arrays) {
 }
 
 StencilGrid fx_grid(int n, int nf) {
-    static int occ1 = 0, occ2 = 0;
     if (nf == 1) {
-        if (!occ1) occ1 = resident_per_sm(stencil_fx_kernel<1, false>, FX_NT);
+        const int occ1 = resident_per_sm(stencil_fx_kernel<1, false>, FX_NT);
         StencilGrid g = stencil_grid(n, FX_TX, FX_OY, occ1);
         g.block = dim3(FX_TX, FX_TY, 1);
         return g;
     }
     if (nf == 3) {
-        static int occ3 = 0;
-        if (!occ3) occ3 = resident_per_sm(stencil_fx_kernel<2, true, true>, FX_NT);
+        const int occ3 = resident_per_sm(stencil_fx_kernel<2, true, true>, FX_NT);
         StencilGrid g = stencil_grid(n, FX_TX, FX_OY, occ3);
         g.block = dim3(FX_TX, FX_TY, 1);
         return g;
@@ -536,35 +475,32 @@ StencilGrid fx_grid(int n, int nf) {
         // shadow-elided operator (one field, staged loads): the grid of the
         // pair kernel it replaces (4 / 5), so that sigma adds the same
         // per-CTA partial sums
-        static bool attr6 = false, attr7 = false;
         const size_t smem6 = fx_stage_bytes<1, fx_stages(false)>();
         const size_t smem7 = fx_stage_bytes<2, fx_stages(true)>();
-        if (nf == 6 && !attr6) attr6 = resident_per_sm(stencil_fx_kernel<1, true, false, true>, FX_NT, smem6) > 0;
-        if (nf == 7 && !attr7) attr7 = resident_per_sm(stencil_fx_kernel<1, true, true, true>, FX_NT, smem7) > 0;
+        if (nf == 6) opt_in_smem(stencil_fx_kernel<1, true, false, true>, smem6);
+        if (nf == 7) opt_in_smem(stencil_fx_kernel<1, true, true, true>, smem7);
         StencilGrid g = fx_grid(n, nf - 2);
         g.smem = nf == 6 ? smem6 : smem7;
         return g;
     }
     if (nf == 4 || nf == 5) {   // staged loads: pair (4), pair with directions (5)
-        static int occ4 = 0, occ5 = 0;
         const size_t smem4 = fx_stage_bytes<2, fx_stages(false)>();
         const size_t smem5 = fx_stage_bytes<4, fx_stages(true)>();
-        if (nf == 4 && !occ4) occ4 = resident_per_sm(stencil_fx_kernel<2, true, false, true>, FX_NT, smem4);
-        if (nf == 5 && !occ5) occ5 = resident_per_sm(stencil_fx_kernel<2, true, true, true>, FX_NT, smem5);
-        StencilGrid g = stencil_grid(n, FX_TX, FX_OY, nf == 4 ? occ4 : occ5);
+        const int occ = nf == 4 ? resident_per_sm(stencil_fx_kernel<2, true, false, true>, FX_NT, smem4)
+                                : resident_per_sm(stencil_fx_kernel<2, true, true, true>, FX_NT, smem5);
+        StencilGrid g = stencil_grid(n, FX_TX, FX_OY, occ);
         g.block = dim3(FX_TX, FX_TY, 1);
         g.smem = nf == 4 ? smem4 : smem5;
         return g;
     }
-    if (!occ2) occ2 = resident_per_sm(stencil_fx_kernel<2, true>, FX_NT);
+    const int occ2 = resident_per_sm(stencil_fx_kernel<2, true>, FX_NT);
     StencilGrid g = stencil_grid(n, FX_TX, FX_OY, occ2);
     g.block = dim3(FX_TX, FX_TY, 1);
     return g;
 }
 
 StencilGrid f64_grid(int n) {
-    static int occ = 0;
-    if (!occ) occ = resident_per_sm(stencil_f64_kernel<false>, TX * TY);
+    const int occ = resident_per_sm(stencil_f64_kernel<false>, TX * TY);
     StencilGrid g = stencil_grid(n, TX, TY, occ);
     g.block = dim3(TX, TY, 1);
     return g;
@@ -608,30 +544,25 @@ constexpr int kPointwiseMaxN = 40;   // per-node operator on grids up to 40^3
 size_t persistent_stage_bytes() { return fx_stage_bytes<4, fx_stages(true)>(); }
 
 int persistent_grid(int n, bool fuse, int* gx, int* gy, int* slabs, int* kz_per) {
-    static int occ_pt = 0, occ_mz = 0, occ_fz = 0;
-    if (!occ_pt) {
-        occ_pt = resident_per_sm(bicg_persistent_kernel<true, false, false>, FX_NT);
-        occ_mz = resident_per_sm(bicg_persistent_kernel<false, false, false>, FX_NT);
-        occ_fz = resident_per_sm(bicg_persistent_kernel<false, false, true>, FX_NT, persistent_stage_bytes());
-        // the elided variants run on the grids of the full ones (same
-        // partial sums); this also opts them in to the dynamic shared memory
-        resident_per_sm(bicg_persistent_kernel<false, true, true>, FX_NT, persistent_stage_bytes());
-        if (occ_pt > 2) occ_pt = 2;
-        if (occ_mz > 2) occ_mz = 2;
-        if (occ_fz > 2) occ_fz = 2;
-    }
+    // at most two CTAs per SM; the elided variants run on the grids of the
+    // full ones (same partial sums)
+    const int occ_pt = min(2, resident_per_sm(bicg_persistent_kernel<true, false, false>, FX_NT));
+    const int occ_mz = min(2, resident_per_sm(bicg_persistent_kernel<false, false, false>, FX_NT));
+    const int occ_fz = min(2, resident_per_sm(bicg_persistent_kernel<false, false, true>, FX_NT,
+                                              persistent_stage_bytes()));
+    const int sms = device_sms();
     const int m = n - 1;
     *gx = (m + FX_TX - 1) / FX_TX;
     *gy = (m + FX_OY - 1) / FX_OY;
     *kz_per = m < 8 ? m : (n <= 64 ? 4 : 8);
     *slabs = (m + *kz_per - 1) / *kz_per;
-    if (n > kPointwiseMaxN) return 152 * (fuse ? occ_fz : occ_mz);
+    if (n > kPointwiseMaxN) return sms * (fuse ? occ_fz : occ_mz);
     // one CTA per ~256 interior nodes, at most every resident slot: fewer
     // CTAs keep the grid barriers short on small grids
     const long long pts = (long long)m * m * m;
     long long want = (pts + 255) / 256;
     if (want < 8) want = 8;
-    if (want > 152LL * occ_pt) want = 152LL * occ_pt;
+    if (want > (long long)sms * occ_pt) want = (long long)sms * occ_pt;
     return (int)want;
 }
 
@@ -650,7 +581,7 @@ cudaError_t launch_bicg_persistent(double* x, double* r, double* rs, double* p, 
     BicgVectors v{x, r, rs, p, ps, p2, ps2, q, qs};
     size_t len = node_count(n);
     int sigma = bc_kind == 1 ? 1 : -1;
-    GridBarrier gb{barrier_words, barrier_words + 1, (int*)(barrier_words + 2)};
+    GridBarrier gb{barrier_words, barrier_words + 1, (int*)(barrier_words + 2), kBarrierSpinLimit};
     void* args[] = {&v, &len, &n, &sigma, &gx, &gy, &slabs, &kz_per, &iters, &partials, &st, &gb};
     const void* fn;
     if (pw)

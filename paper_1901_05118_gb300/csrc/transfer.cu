@@ -17,7 +17,6 @@
 //     u~ = u_h + (1/3) * (mean of u_h - u_2h over the 2^m coarse nodes
 //                         around the node),
 // which is (4 u_h - u_2h)/3 at coarse nodes and (chenlin) at 1D midpoints.
-#include <mutex>
 
 #include "excmg_internal.cuh"
 
@@ -254,28 +253,20 @@ constexpr size_t kNoAllocW =
 
 static __device__ __align__(256) double g_noalloc_W[kNoAllocW];
 
-std::mutex g_noalloc_mu;
-double* g_noalloc_addr[64] = {};   // device address of g_noalloc_W, per device
-
-// The array's device address on the current device, looked up once per
-// device (the name g_noalloc_W is only a host-side stand-in in host code).
+// The array's device address on the current device.  In host code the name
+// g_noalloc_W is only a host-side stand-in, so the address is looked up on
+// every call: a cached address would go stale if the device's context were
+// reset and the library's device code loaded again elsewhere.  The lookup
+// allocates nothing; on a device's first call it also loads the library's
+// device code there.
 int noalloc_scratch(double** out) {
-    int dev = 0;
-    if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= 64) {
+    void* p = nullptr;
+    const cudaError_t e = cudaGetSymbolAddress(&p, g_noalloc_W);
+    if (e != cudaSuccess || !p) {
         cudaGetLastError();
         return EXCMG_ERR_CUDA;
     }
-    std::lock_guard<std::mutex> lock(g_noalloc_mu);
-    if (!g_noalloc_addr[dev]) {
-        void* p = nullptr;
-        const cudaError_t e = cudaGetSymbolAddress(&p, g_noalloc_W);
-        if (e != cudaSuccess || !p) {
-            cudaGetLastError();
-            return EXCMG_ERR_CUDA;
-        }
-        g_noalloc_addr[dev] = (double*)p;
-    }
-    *out = g_noalloc_addr[dev];
+    *out = (double*)p;
     return EXCMG_OK;
 }
 

@@ -18,6 +18,7 @@ from dataclasses import dataclass, field
 import numpy as np
 
 SIZE_BASES = (4, 5, 6, 7)
+REJECTED = -9   # status recorded for a request the engine refuses while idle (EXCMG_ERR_BUDGET)
 
 
 def size_grid(lo: int = 32, hi: int = 256):
@@ -115,9 +116,20 @@ def serve(engine, requests, pool, tol: float, clock=time.perf_counter, new_outpu
             r = queued[0]
             f, g1, g2 = pool.get(r.n, r.bc, r.problem_seed)
             out = new_output(r.n) if new_output else None
-            sub = engine.submit(r.n, r.nc, r.bc, f, g1, g2, tol, out, **submit_kwargs)
-            if sub is None:
+            try:
+                sub = engine.submit(r.n, r.nc, r.bc, f, g1, g2, tol, out, **submit_kwargs)
+            except Exception as exc:          # e.g. larger than the whole budget
+                sub = exc
+            if sub is None and live:
                 break            # budget or slots full: wait for completions
+            if sub is None or isinstance(sub, Exception):
+                # refused with nothing running: it can never be admitted
+                status = getattr(sub, "status", REJECTED)
+                queued.popleft()
+                records.append({"rid": r.rid, "n": r.n, "bc": r.bc, "status": status, "latency_s": 0.0,
+                                "arrival_s": r.t_arrival, "engine_latency_s": None, "output": None,
+                                "rejected": True})
+                continue
             live[sub[0]] = (r, sub[1])
             queued.popleft()
         if live:
@@ -134,8 +146,10 @@ def serve(engine, requests, pool, tol: float, clock=time.perf_counter, new_outpu
         elif pending:
             sleep(max(0.0, min(0.01, pending[0].t_arrival - (clock() - t0))))
     wall = clock() - t0
-    lat = np.array([rec["latency_s"] for rec in records]) if records else np.zeros(1)
-    summary = {"requests": len(records), "wall_s": wall, "solves_per_s": len(records) / wall if wall > 0 else 0.0,
+    solved = [rec for rec in records if not rec.get("rejected")]
+    lat = np.array([rec["latency_s"] for rec in solved]) if solved else np.zeros(1)
+    summary = {"requests": len(records), "rejected": len(records) - len(solved), "wall_s": wall,
+               "solves_per_s": len(solved) / wall if wall > 0 else 0.0,
                "p50_s": float(np.percentile(lat, 50)), "p99_s": float(np.percentile(lat, 99)),
                "mean_s": float(lat.mean()), "steps": steps,
                "failed": sum(1 for rec in records if rec["status"] != 0)}

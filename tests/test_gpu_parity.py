@@ -150,6 +150,22 @@ def test_extrapolate_interpolate(nf):
     assert rel_max(w, ref) <= 1e-13
 
 
+@pytest.mark.parametrize("nf", [8, 40])
+def test_extrapolate_interpolate_takes_boundary_from_g1(nf):
+    """With g1_fine, w_h's boundary nodes hold g1's boundary values (Alg. 1
+    sets the Dirichlet data before Bi-CG); interior nodes are Steps 1-5."""
+    u1 = P.random_field(nf // 2, 11 + nf)
+    u0 = P.random_field(nf // 4, 12 + nf)
+    g1 = P.random_field(nf, 13 + nf)
+    w = host(B.extrapolate_interpolate(nf, dev(u1), dev(u0), g1_fine=dev(g1)))
+    ref = oracle.exp_finite(nf, u1, u0)
+    inner = (slice(1, nf), slice(1, nf), slice(1, nf))
+    assert rel_max(w[inner], ref[inner]) <= 1e-13
+    mask = np.ones_like(w, dtype=bool)
+    mask[inner] = False
+    np.testing.assert_array_equal(w[mask], g1[mask])
+
+
 @pytest.mark.parametrize("nf", [4, 10, 64])
 def test_midpoint_extrapolate(nf):
     uh = P.random_field(nf, 3 + nf)
@@ -254,6 +270,56 @@ def test_excmg_solve_matches_oracle(name, bc_kind, variant):
         # iteration counts are not pinned by the paper; rounding differences
         # shift them slightly over hundreds of iterations
         assert abs(s["iters"] - ref_stats[l, 0]) <= max(3, 0.05 * ref_stats[l, 0])
+
+
+_ORACLE_128 = {}
+# (tolerance schedule, tol, Bi-CG cap per call of the WHILE loop): the small
+# cap makes the loop restart Bi-CG several times per level and end levels on
+# the stagnation rule
+CASES_128 = [("uniform", 1e-6, 100000), ("paper", 1e-6, 100000), ("uniform", 1e-8, 8)]
+
+
+def _oracle_128(bc_kind, case):
+    """The oracle's solve of the 128^3 case, computed once per session."""
+    key = (bc_kind, case)
+    if key not in _ORACLE_128:
+        tol_mode, tol, max_iter = case
+        f, g1, g2 = P.exp_sum().data(128, bc_kind)
+        _ORACLE_128[key] = oracle.excmg(128, 8, bc_kind, f, g1, g2, tol, tol_mode=tol_mode, max_iter=max_iter,
+                                        max_total=400)
+    return _ORACLE_128[key]
+
+
+@pytest.mark.parametrize("schedule", SCHEDULES)
+@pytest.mark.parametrize("case", CASES_128)
+@pytest.mark.parametrize("bc_kind", [1, 2])
+def test_excmg_solve_128_matches_oracle(bc_kind, case, schedule):
+    """Alg. 1 on 8^3 .. 128^3 (u = e^(x+y+z)): the 32^3 and 64^3 levels run
+    the cooperative kernels and the 128^3 level the launched operator /
+    update / direction-update kernels (in both operator schedules), inside
+    the WHILE loop with its restarts, stagnation rule and EXP_finite
+    hand-offs, under both tolerance schedules of Alg. 1 line 5.  Every level
+    takes the oracle's Bi-CG iterations and calls and ends the same way; u_h
+    and u~ match the oracle's entry by entry."""
+    tol_mode, tol, max_iter = case
+    n, nc = 128, 8
+    f, g1, g2 = P.exp_sum().data(n, bc_kind)
+    ctx = B.Context()
+    ctx.set_schedule(schedule)
+    uh = torch.empty((n + 1,) * 3, dtype=torch.float64, device=DEV)
+    ut, stats = B.excmg_solve(n, nc, bc_kind, dev(f), dev(g1), dev(g2), tol, tol_mode=tol_mode, max_iter=max_iter,
+                              max_total=400, u_h_out=uh, return_stats=True, ctx=ctx)
+    ref_h, ref_t, ref_stats = _oracle_128(bc_kind, case)
+    assert [s["iters"] for s in stats] == [int(v) for v in ref_stats[:, 0]]
+    assert [s["calls"] for s in stats] == [int(v) for v in ref_stats[:, 2]]
+    assert [int(s["stagnated"]) for s in stats] == [int(v) for v in ref_stats[:, 3]]
+    assert rel_max(host(uh), ref_h) <= 1e-9
+    assert rel_max(host(ut), ref_t) <= 1e-9
+    L = len(stats) - 2
+    for l, st in enumerate(stats[2:], start=2):
+        eps_i = tol * (10.0 ** (l - 1 - L) if tol_mode == "paper" else 1.0)
+        assert st["relres"] <= eps_i or st["stagnated"]
+        assert st["relres"] == pytest.approx(ref_stats[l, 1], rel=1e-6)
 
 
 def test_excmg_exact_for_triquadratic():

@@ -467,3 +467,30 @@ def test_bicg_with_chosen_shadow_matches_direct_solve(bc_kind):
     x, it, rel, rc = oracle.bicg(N, bc_kind, fh, np.zeros_like(fh), 1e-13, shadow=P.random_field(N, 62))
     assert rc == 0 and rel <= 1e-13
     np.testing.assert_allclose(interior(x), interior(xd), rtol=0, atol=1e-9 * np.abs(xd).max())
+
+
+# -------------------------------------------- Alg. 1 line 5: the tolerances
+@pytest.mark.parametrize("bc_kind", [1, 2])
+def test_excmg_paper_tolerance_schedule(bc_kind):
+    """eps_i = eps * 10^(i - L): level i of L (i = L the finest) stops at a
+    true relative residual of at most eps * 10^(i-L), i.e. every coarser
+    Bi-CG grid is solved ten times tighter than the next finer one; with the
+    uniform schedule every level stops at eps.  A swapped exponent sign would
+    leave the coarse levels at 10 eps and fail the first assertion."""
+    prob = P.exp_sum()
+    n, nc, eps = 64, 4, 1e-5
+    f, g1, g2 = prob.data(n, bc_kind)
+    _, _, st_p = oracle.excmg(n, nc, bc_kind, f, g1, g2, eps, tol_mode="paper")
+    _, _, st_u = oracle.excmg(n, nc, bc_kind, f, g1, g2, eps, tol_mode="uniform")
+    levels = st_p.shape[0]                 # grids 4, 8 (direct), 16, 32, 64
+    L = levels - 2
+    for l in range(2, levels):
+        i = l - 1                          # Alg. 1 loop counter 1..L
+        eps_i = eps * 10.0 ** (i - L)
+        assert st_p[l, 1] <= eps_i, (l, st_p[l, 1], eps_i)
+        assert st_u[l, 1] <= eps
+        if i < L:   # the tighter coarse levels cost at least as many iterations
+            assert st_p[l, 0] >= st_u[l, 0]
+    assert st_p[2, 0] > st_u[2, 0]          # the coarsest Bi-CG grid: 100x tighter
+    # the uniform schedule does not meet the coarsest level's paper bound
+    assert st_u[2, 1] > eps * 10.0 ** (1 - L)

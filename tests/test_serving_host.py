@@ -80,6 +80,42 @@ def test_serve_admits_as_slots_free_and_reports_latency():
     assert sorted(r["rid"] for r in recs) == list(range(50))
 
 
+class PickyEngine(FakeEngine):
+    """Never admits grids of `never` intervals: returns None for them (as a
+    full engine does), or raises like excmg_batch_submit's
+    EXCMG_ERR_TOO_LARGE when `raise_status` is set."""
+
+    def __init__(self, slots, work, never, raise_status=None):
+        super().__init__(slots, work)
+        self.never, self.raise_status = never, raise_status
+
+    def submit(self, n, nc, bc, f, g1, g2, tol, out, **kw):
+        if n == self.never:
+            if self.raise_status is not None:
+                err = RuntimeError("instance larger than the whole budget")
+                err.status = self.raise_status
+                raise err
+            return None
+        return super().submit(n, nc, bc, f, g1, g2, tol, out, **kw)
+
+
+@pytest.mark.parametrize("raise_status", [None, -11])
+def test_serve_rejects_a_request_that_can_never_be_admitted(raise_status):
+    # the loop must end (it used to spin forever with nothing live), serve
+    # every other request and record the refused ones as rejected
+    reqs = S.make_requests(60, rate=2000.0, seed=3)
+    big = max(r.n for r in reqs)
+    n_big = sum(1 for r in reqs if r.n == big)
+    assert 0 < n_big < len(reqs)
+    eng = PickyEngine(slots=4, work=2, never=big, raise_status=raise_status)
+    recs, summ = S.serve(eng, reqs, FakePool(), 1e-8, clock=FakeClock(), sleep=lambda s: None)
+    assert summ["requests"] == 60 and summ["rejected"] == n_big
+    rejected = [r for r in recs if r.get("rejected")]
+    assert {r["n"] for r in rejected} == {big}
+    assert all(r["status"] == (raise_status if raise_status is not None else S.REJECTED) for r in rejected)
+    assert all(r["status"] == 0 for r in recs if not r.get("rejected"))
+
+
 def test_random_sines_torch_matches_numpy():
     torch = pytest.importorskip("torch")
     for bc in (1, 2):

@@ -11,6 +11,7 @@ import ctypes
 import numpy as np
 import pytest
 
+import oracle
 from paper_1901_05118_gb300 import problems as P
 
 torch = pytest.importorskip("torch")
@@ -39,10 +40,13 @@ def _dev(a):
 def test_noalloc_matches_extrapolate_interpolate_on_consecutive_calls():
     fn = _entry()
     # two calls in a row through the C ABI; the second one, at the largest
-    # allowed size, reuses the array the first one left behind
+    # allowed size, reuses the array the first one left behind.  Each result
+    # is checked against the allocating entry point and against the CPU
+    # oracle's Steps 1-5.
     for call, nf in enumerate((64, MAX_FINE)):
-        u1 = _dev(P.random_field(nf // 2, 500 + call))
-        u0 = _dev(P.random_field(nf // 4, 600 + call))
+        h1 = P.random_field(nf // 2, 500 + call)
+        h0 = P.random_field(nf // 4, 600 + call)
+        u1, u0 = _dev(h1), _dev(h0)
         ref = B.extrapolate_interpolate(nf, u1, u0)          # the allocating entry point
         w = torch.full((nf + 1,) * 3, float("nan"), dtype=torch.float64, device=DEV)
         torch.cuda.synchronize()
@@ -50,6 +54,8 @@ def test_noalloc_matches_extrapolate_interpolate_on_consecutive_calls():
         assert rc == 0
         got, want = w.cpu().numpy(), ref.cpu().numpy()
         assert np.abs(got - want).max() <= 1e-13 * np.abs(want).max()
+        orc = oracle.exp_finite(nf, h1, h0)
+        assert np.abs(got - orc).max() <= 1e-13 * np.abs(orc).max()
 
 
 def test_noalloc_rejects_sizes_beyond_its_array():
