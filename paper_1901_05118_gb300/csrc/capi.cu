@@ -51,7 +51,9 @@ int kernel_occupancy(const void* kernel, int threads, size_t smem) {
     std::lock_guard<std::mutex> lock(g_dev_mu);
     auto it = g_occ.find(key);
     if (it != g_occ.end()) return it->second;
-    if (smem > 48 * 1024 &&
+    // (static + dynamic shared memory above 48 KB needs the opt-in, so it is
+    // made whenever dynamic shared memory is asked for)
+    if (smem > 0 &&
         cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) != cudaSuccess) {
         cudaGetLastError();
         return 1;   // not cached; the launch reports the error

@@ -186,8 +186,8 @@ void note_launches(long long k);
 int device_sms();
 // Resident CTAs per SM of `kernel` (a __global__ function) with `threads`
 // threads and `smem` bytes of dynamic shared memory on the current device,
-// at least 1.  Kernels that need more than 48 KB of dynamic shared memory are
-// opted in to it on the current device first.  Cached per (kernel, device,
+// at least 1.  A kernel given dynamic shared memory is opted in to that much
+// on the current device first (cudaFuncAttributeMaxDynamicSharedMemorySize).  Cached per (kernel, device,
 // threads, smem) under a lock: function attributes and occupancy belong to
 // each device's context.
 int kernel_occupancy(const void* kernel, int threads, size_t smem);
