@@ -1,0 +1,304 @@
+// The operator launch of Bi-CG (Alg. 2): q = A p and q* = A^T p* of eq.
+// (method1) with the reflections of eqs. (reflection2) / (reflection4), with
+// sigma = (p*, q), in the integer arithmetic of march_fx.cuh (each input
+// plane of a CTA on one power-of-two scale, taps summed exactly, one
+// rounding per output).  Same results, bit for bit, as fx_march<2, true>:
+// the same scale sequence, the same integer sums, the same per-thread order
+// of the sigma terms.  What differs is how the work is fed:
+//
+//  * Loads are staged ahead by per-thread asynchronous copies (cp.async, 8
+//    bytes each) of the thread's own halo slots into a ring of four shared
+//    memory stages, three planes ahead of the plane being converted.  Each
+//    thread reads back only the slots it copied itself, so completing a stage
+//    needs no CTA barrier: cp.async.wait_group orders the thread's own copies.
+//  * A thread's slots are its own two output columns (x = i, rows j, j+1)
+//    plus at most one element of the 2-node ring around the CTA's 32 x 16
+//    columns, so its centre values also feed sigma without another load.
+//  * One CTA barrier per plane: the exponent maximum of plane t+1 is
+//    published (per warp) before the barrier that also publishes the
+//    fixed-point tile of plane t, so the scale of every plane is known one
+//    plane ahead.  Tiles alternate between two buffers.
+//  * The march runs on p alone and checks, slot by slot, that p* equals p
+//    bit for bit (with r*_0 = r_0 it always does: A^T p* is then A p bit for
+//    bit, and q* is written from q).  A CTA that meets a differing slot
+//    returns `false` and the caller runs the general two-field march.
+//  * Multiplications by the small weights are 64 x 32-bit products (two
+//    integer multiply-adds) and sums of mirrored taps are shared between the
+//    two output rows (the diagonal taps of a row are the horizontal axis
+//    taps of the rows above and below).
+#pragma once
+
+#include <cuda_runtime.h>
+
+#include "march_fx.cuh"
+
+namespace excmg {
+namespace {
+
+constexpr int PP_TX = 32;                       // threads along x
+constexpr int PP_TY = 8;                        // threads along y
+constexpr int PP_OY = 2 * PP_TY;                // output rows per CTA (2 per thread)
+constexpr int PP_HX = PP_TX + 4;                // halo width (36)
+constexpr int PP_HY = PP_OY + 4;                // halo height (20)
+constexpr int PP_HALO = PP_HX * PP_HY;          // 720 nodes per plane
+constexpr int PP_NT = PP_TX * PP_TY;            // 256 threads
+constexpr int PP_RING = PP_HALO - PP_TX * PP_OY;   // 208 ring nodes
+constexpr int PP_STAGES = 4;                    // copy stages
+constexpr int PP_AHEAD = PP_STAGES - 1;         // planes copied ahead of the one converted
+
+static_assert(PP_TX == FX_TX && PP_OY == FX_OY, "same tiles as fx_march (same sigma partials)");
+
+// dynamic shared memory: copy stages (NF fields) + two fixed-point tiles
+template <int NF>
+__host__ __device__ constexpr size_t pp_smem_bytes() {
+    return (size_t)PP_STAGES * NF * PP_HALO * sizeof(double) + (size_t)2 * PP_HALO * sizeof(long long);
+}
+
+// Halo index (ly * PP_HX + lx) of slot s of thread tid: slots 0, 1 are the
+// thread's output columns; slot 2 (threads below PP_RING) one ring node --
+// the two rows above and below the CTA's columns, then the two columns left
+// and right of them, four nodes per row.
+__device__ __forceinline__ int pp_slot(int tid, int s) {
+    const int tx = tid & (PP_TX - 1), ty = tid / PP_TX;
+    if (s < 2) return (2 * ty + 2 + s) * PP_HX + tx + 2;
+    if (tid < 4 * PP_HX) {
+        const int row = tid / PP_HX, lx = tid - row * PP_HX;
+        const int ly = row < 2 ? row : PP_HY - 4 + row;
+        return ly * PP_HX + lx;
+    }
+    const int k = tid - 4 * PP_HX;
+    const int c = k & 3;
+    return (2 + (k >> 2)) * PP_HX + (c < 2 ? c : PP_HX - 4 + c);
+}
+
+__device__ __forceinline__ void cp_async8(void* dst, const void* src, unsigned src_bytes) {
+    asm volatile("cp.async.ca.shared.global [%0], [%1], 8, %2;" ::"r"(smem_u32(dst)), "l"(src), "r"(src_bytes)
+                 : "memory");
+}
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;" ::: "memory"); }
+template <int N>
+__device__ __forceinline__ void cp_async_wait() {
+    asm volatile("cp.async.wait_group %0;" ::"n"(N) : "memory");
+}
+__device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wait_all;" ::: "memory"); }
+
+// a * w for a 64-bit integer a and a small positive weight w (|a w| < 2^63):
+// one 32 x 32 -> 64 product of the low word and one multiply-add of the high
+// word, instead of a general 64-bit multiplication
+__device__ __forceinline__ long long mul_w(long long a, unsigned w) {
+    const unsigned long long lo = (unsigned long long)(unsigned)a * w;
+    const unsigned hi = (unsigned)((unsigned long long)a >> 32) * w + (unsigned)(lo >> 32);
+    return (long long)(((unsigned long long)hi << 32) | (unsigned)lo);
+}
+
+// Y * 2^(E - 1075) rounded to nearest even, by the hardware conversion of Y
+// to double (the same rounding of Y to 53 bits as from_fixed) and an exact
+// power-of-two scaling of the exponent field; valid for 53 <= E <= 2036.
+__device__ __forceinline__ double fx_result_cvt(long long acc, int E, bool poisoned) {
+    if (!poisoned && E >= 53 && E <= 2036) {
+        const double d = (double)acc;
+        const long long bits = __double_as_longlong(d) + ((long long)(E - 1075) << 52);
+        return acc == 0 ? 0.0 : __longlong_as_double(bits);
+    }
+    return fx_result_slow(acc, E, poisoned);
+}
+
+// One CTA's march over output planes [kz0, kz1) of column tile (bx, by).
+// Returns false (uniformly) if some slot of p* differs from p; otherwise
+// writes q (and q* = q unless kElide) and adds this thread's share of
+// sigma = (p*, q) to *dot.  kElide: p* is not read and q* not written (the
+// shadow-elided mode; the same sums in the same order).  kCvt: round the
+// outputs through the hardware integer-to-double conversion.
+template <bool kElide, bool kCvt>
+__device__ __forceinline__ bool pp_march(const double* __restrict__ p, const double* __restrict__ ps,
+                                         double* __restrict__ q, double* __restrict__ qs, int n, int sigma, int bx,
+                                         int by, int kz0, int kz1, unsigned char* smem, double* dot) {
+    constexpr int NF = kElide ? 1 : 2;
+    __shared__ int wmax[2][PP_NT / 32];
+    double* const raw = reinterpret_cast<double*>(smem);   // [stage][field][halo]
+    long long* const tiles = reinterpret_cast<long long*>(smem + (size_t)PP_STAGES * NF * PP_HALO * sizeof(double));
+    const int np = n + 1;
+    const size_t plane = (size_t)np * np;
+    const int tx = threadIdx.x, ty = threadIdx.y, tid = ty * PP_TX + tx;
+    const int lane = tid & 31, warp = tid >> 5;
+    const int i0 = 1 + bx * PP_TX, j0 = 1 + by * PP_OY;
+    const bool ring = tid < PP_RING;
+
+    // slots: halo index, in-plane offset of the node, whether it is an unknown
+    int se[3], soff[3];
+    bool sin[3];
+#pragma unroll
+    for (int s = 0; s < 3; ++s) {
+        se[s] = (s < 2 || ring) ? pp_slot(tid, s) : 0;
+        const int ly = se[s] / PP_HX, lx = se[s] - ly * PP_HX;
+        const int gi = i0 - 2 + lx, gj = j0 - 2 + ly;
+        sin[s] = (s < 2 || ring) && gi >= 1 && gi <= n - 1 && gj >= 1 && gj <= n - 1;
+        soff[s] = sin[s] ? gj * np + gi : 0;
+    }
+    const int i = i0 + tx, ja = j0 + 2 * ty;
+    const bool act0 = (i <= n - 1) && (ja <= n - 1);
+    const bool act1 = (i <= n - 1) && (ja + 1 <= n - 1);
+    const int cx = (i == 1) + (i == n - 1);
+    const int c0 = cx + (ja == 1) + (ja == n - 1);
+    const int c1 = cx + (ja + 1 == 1) + (ja + 1 == n - 1);
+    const int rx = tx + 2, ry = 2 * ty + 2;
+    const int T = kz1 - kz0 + 4;   // input planes kz0 - 2 .. kz1 + 1
+
+    // copy plane t (all of this thread's slots, both fields) into its stage;
+    // nodes outside the interior are zero-filled; always one commit group
+    auto issue = [&](int t) {
+        if (t < T) {
+            const int zin = kz0 - 2 + t;
+            const bool zok = zin >= 1 && zin <= n - 1;
+            const size_t zb = zok ? (size_t)zin * plane : 0;
+            double* st = raw + (size_t)(t % PP_STAGES) * NF * PP_HALO;
+#pragma unroll
+            for (int s = 0; s < 3; ++s) {
+                if (s < 2 || ring) {
+                    const bool ld = zok && sin[s];
+                    const size_t o = ld ? zb + soff[s] : 0;
+                    cp_async8(st + se[s], p + o, ld ? 8u : 0u);
+                    if (!kElide) cp_async8(st + PP_HALO + se[s], ps + o, ld ? 8u : 0u);
+                }
+            }
+        }
+        cp_async_commit();
+    };
+    // read back plane t's slots (its copies complete), publish the warp's
+    // exponent maximum for plane t; false if p* differs from p in a slot
+    auto scan = [&](int t, double (&v)[3]) -> bool {
+        const double* st = raw + (size_t)(t % PP_STAGES) * NF * PP_HALO;
+        unsigned diff = 0u;
+        int emax = 0;
+#pragma unroll
+        for (int s = 0; s < 3; ++s) {
+            v[s] = 0.0;
+            if (s < 2 || ring) {
+                v[s] = st[se[s]];
+                emax = max(emax, exponent_of(v[s]));
+                if (!kElide) {
+                    const double w = st[PP_HALO + se[s]];
+                    diff |= ((unsigned)__double2loint(v[s]) ^ (unsigned)__double2loint(w)) |
+                            ((unsigned)__double2hiint(v[s]) ^ (unsigned)__double2hiint(w));
+                }
+            }
+        }
+        emax = (int)__reduce_max_sync(0xffffffffu, (unsigned)emax);
+        if (lane == 0) wmax[t & 1][warp] = emax;
+        return diff == 0u;
+    };
+    auto plane_max = [&](int t) { return (int)__reduce_max_sync(0xffffffffu, (unsigned)wmax[t & 1][lane & 7]); };
+
+#pragma unroll
+    for (int t = 0; t < PP_AHEAD; ++t) issue(t);
+    cp_async_wait<PP_AHEAD - 1>();
+    double cur[3];
+    bool same = scan(0, cur);
+    if (!__syncthreads_and(same)) {
+        cp_async_wait_all();
+        return false;
+    }
+    int E = max(1, plane_max(0));
+    bool poisoned = E == 0x7FF;
+
+    long long acc[2][5];
+#pragma unroll
+    for (int qq = 0; qq < 2; ++qq)
+#pragma unroll
+        for (int k = 0; k < 5; ++k) acc[qq][k] = 0;
+    double pc1[2] = {0.0, 0.0}, pc2[2] = {0.0, 0.0};   // centre p of the last two planes
+    double d = 0.0;
+
+    for (int t = 0; t < T; ++t) {
+        issue(t + PP_AHEAD);
+        cp_async_wait<PP_AHEAD - 1>();   // planes up to t + 1 have landed
+        double nxt[3] = {0.0, 0.0, 0.0};
+        same = t + 1 < T ? scan(t + 1, nxt) : true;
+        // plane t on scale E into its tile
+        long long* tl = tiles + (size_t)(t & 1) * PP_HALO;
+#pragma unroll
+        for (int s = 0; s < 3; ++s)
+            if (s < 2 || ring) tl[se[s]] = to_fixed(cur[s], E);
+        // every tile of plane t written, every exponent of plane t + 1
+        // published, every read of the tile of plane t - 2 done
+        if (!__syncthreads_and(same)) {
+            cp_async_wait_all();
+            return false;
+        }
+        const int ep = t + 1 < T ? plane_max(t + 1) : 0;
+
+        const int zin = kz0 - 2 + t;
+        const int cz = (zin == 1) + (zin == n - 1);
+        auto at = [&](int yy, int xx) { return tl[yy * PP_HX + xx]; };
+        const long long cm2 = at(ry - 2, rx), cm1 = at(ry - 1, rx), cc0 = at(ry, rx), cc1 = at(ry + 1, rx),
+                        cc2 = at(ry + 2, rx), cc3 = at(ry + 3, rx);
+        // x-neighbour sums at distance 1 (rows ry-1 .. ry+2) and 2 (rows ry, ry+1)
+        const long long h1m = at(ry - 1, rx - 1) + at(ry - 1, rx + 1);
+        const long long h10 = at(ry, rx - 1) + at(ry, rx + 1);
+        const long long h11 = at(ry + 1, rx - 1) + at(ry + 1, rx + 1);
+        const long long h12 = at(ry + 2, rx - 1) + at(ry + 2, rx + 1);
+        const long long h20 = at(ry, rx - 2) + at(ry, rx + 2);
+        const long long h21 = at(ry + 1, rx - 2) + at(ry + 1, rx + 2);
+        long long P0[2], P1[2], C[2];
+        {   // output row ja: same plane (42 + sigma c) u - 12 (4 axis) + (4 at 2) + 2 (4 diagonals);
+            // planes +-1: 2 (4 axis) - 12 u; planes +-2: u
+            const long long n4 = h10 + cm1 + cc1;
+            const long long f4 = h20 + cm2 + cc2;
+            const long long d4 = h1m + h11;
+            P0[0] = mul_w(cc0, (unsigned)(42 + sigma * (c0 + cz))) - mul_w(n4, 12u) + f4 + d4 + d4;
+            P1[0] = n4 + n4 - mul_w(cc0, 12u);
+            C[0] = cc0;
+        }
+        {   // output row ja + 1
+            const long long n4 = h11 + cc0 + cc2;
+            const long long f4 = h21 + cm1 + cc3;
+            const long long d4 = h10 + h12;
+            P0[1] = mul_w(cc1, (unsigned)(42 + sigma * (c1 + cz))) - mul_w(n4, 12u) + f4 + d4 + d4;
+            P1[1] = n4 + n4 - mul_w(cc1, 12u);
+            C[1] = cc1;
+        }
+        const int zo = zin - 2;
+        const bool zstore = zo >= kz0 && zo < kz1;
+#pragma unroll
+        for (int qq = 0; qq < 2; ++qq) {
+            acc[qq][0] += C[qq];
+            acc[qq][1] += P1[qq];
+            acc[qq][2] += P0[qq];
+            acc[qq][3] += P1[qq];
+            acc[qq][4] += C[qq];
+            if (zstore && (qq == 0 ? act0 : act1)) {
+                const size_t o = ((size_t)zo * np + ja + qq) * np + i;
+                const double val = kCvt ? fx_result_cvt(acc[qq][0], E, poisoned) : fx_result(acc[qq][0], E, poisoned);
+                q[o] = val;
+                if (!kElide) qs[o] = val;
+                // sigma = (p*, A p): p* = p here, the centre value of plane zo
+                d += pc2[qq] * val;
+            }
+            acc[qq][0] = acc[qq][1];
+            acc[qq][1] = acc[qq][2];
+            acc[qq][2] = acc[qq][3];
+            acc[qq][3] = acc[qq][4];
+            acc[qq][4] = 0;
+            pc2[qq] = pc1[qq];
+            pc1[qq] = cur[qq];
+        }
+        // scale of plane t + 1: a larger exponent shifts the accumulators
+        if (ep == 0x7FF) poisoned = true;
+        if (ep > E) {
+            const int dd = ep - E;
+#pragma unroll
+            for (int qq = 0; qq < 2; ++qq)
+#pragma unroll
+                for (int k = 0; k < 5; ++k) acc[qq][k] = dd >= 63 ? 0 : (acc[qq][k] >> dd);
+            E = ep;
+        }
+#pragma unroll
+        for (int s = 0; s < 3; ++s) cur[s] = nxt[s];
+    }
+    cp_async_wait_all();
+    *dot = d;
+    return true;
+}
+
+}  // namespace
+}  // namespace excmg

@@ -27,6 +27,7 @@
 #include "excmg_internal.cuh"
 #include "grid_sync.cuh"
 #include "march_fx.cuh"
+#include "march_pair.cuh"
 #include "reduce.cuh"
 
 namespace excmg {
@@ -135,6 +136,57 @@ stencil_fx_kernel(FxFields fl, const double* __restrict__ b, int n, int sigma, i
                 }
                 st->ticket = 0;
             }
+        }
+    }
+}
+
+// The operator launch of the default Bi-CG schedule on grids above 64^3:
+// q = A p, q* = A^T p*, sigma = (p*, q) and alpha = rho / sigma (Alg. 2),
+// with the copy-ahead march of march_pair.cuh (bit for bit the results of
+// stencil_fx_kernel<2, true>).  A CTA whose slab holds a node where p*
+// differs from p (a caller-chosen r*_0) runs the general two-field march
+// instead.  kElide: the shadow-elided mode (p only, q only; the same sums).
+constexpr bool kPairCvt = true;   // outputs rounded by the hardware conversion
+
+// the general two-field march, kept out of line: it runs only where p* != p
+__device__ __noinline__ double pair_two_field(const double* p, const double* ps, double* q, double* qs, int n,
+                                              int sigma, int kz0, int kz1) {
+    const FxFields fl{{p, ps}, {q, qs}, {nullptr, nullptr}, {nullptr, nullptr}, 0.0, nullptr, nullptr};
+    return fx_march<2, true>(fl, nullptr, n, sigma, blockIdx.x, blockIdx.y, kz0, kz1);
+}
+
+template <bool kElide>
+__global__ void __launch_bounds__(PP_NT, 3)
+stencil_pair_kernel(const double* __restrict__ p, const double* __restrict__ ps, double* __restrict__ q,
+                    double* __restrict__ qs, int n, int sigma, int kz_per_cta, double* partials, BicgState* st) {
+    extern __shared__ __align__(128) unsigned char pp_smem[];
+    if (st->done) return;
+    const int kz0 = 1 + blockIdx.z * kz_per_cta;
+    const int kz1 = min(kz0 + kz_per_cta, n);
+    double dot = 0.0;
+    const bool fast = pp_march<kElide, kPairCvt>(p, ps, q, qs, n, sigma, blockIdx.x, blockIdx.y, kz0, kz1,
+                                                pp_smem, &dot);
+    if constexpr (!kElide) {
+        if (!fast) {
+            __syncthreads();
+            dot = pair_two_field(p, ps, q, qs, n, sigma, kz0, kz1);
+        }
+    }
+    __shared__ double sh[32];
+    __shared__ bool am_last;
+    const double sdot = block_sum(dot, sh);
+    if (publish_partials(&sdot, 1, partials, &st->ticket, &am_last)) {
+        const double sg = gather_partials(partials, 0, sh);
+        if (thread0()) {
+            const double rho = st->rho;
+            st->sigma = sg;
+            if (!(rho != 0.0 && isfinite(rho)) || !(sg != 0.0 && isfinite(sg))) {
+                st->status = kBreakdown;
+                st->done = 1;
+            } else {
+                st->alpha = rho / sg;
+            }
+            st->ticket = 0;
         }
     }
 }
@@ -499,6 +551,16 @@ StencilGrid fx_grid(int n, int nf) {
     return g;
 }
 
+// The copy-ahead operator launch (both modes run on this grid, so that
+// sigma adds the same per-CTA partial sums).
+StencilGrid pair_grid(int n) {
+    const int occ = resident_per_sm(stencil_pair_kernel<false>, PP_NT, pp_smem_bytes<2>());
+    StencilGrid g = stencil_grid(n, PP_TX, PP_OY, occ);
+    g.block = dim3(PP_TX, PP_TY, 1);
+    g.smem = pp_smem_bytes<2>();
+    return g;
+}
+
 StencilGrid f64_grid(int n) {
     const int occ = resident_per_sm(stencil_f64_kernel<false>, TX * TY);
     StencilGrid g = stencil_grid(n, TX, TY, occ);
@@ -514,6 +576,8 @@ int stencil_cta_count(int n) {
         const StencilGrid g = fx_grid(n, nf);
         most = max(most, g.grid.x * g.grid.y * g.grid.z);
     }
+    const StencilGrid g = pair_grid(n);
+    most = max(most, g.grid.x * g.grid.y * g.grid.z);
     return (int)most;
 }
 
@@ -631,9 +695,9 @@ cudaError_t launch_bicg_stencil_pair(const double* p, double* q, const double* p
         stencil_fx_kernel<2, true, false, true><<<g.grid, g.block, g.smem, s>>>(fl, nullptr, n, sg, g.kz_per_cta,
                                                                                 &st->done, partials, st);
     } else {
-        const StencilGrid g = fx_grid(n, 2);
-        stencil_fx_kernel<2, true><<<g.grid, g.block, 0, s>>>(fl, nullptr, n, sg, g.kz_per_cta, &st->done,
-                                                              partials, st);
+        const StencilGrid g = pair_grid(n);
+        opt_in_smem(stencil_pair_kernel<false>, g.smem);
+        stencil_pair_kernel<false><<<g.grid, g.block, g.smem, s>>>(p, ps, q, qs, n, sg, g.kz_per_cta, partials, st);
     }
     return cudaGetLastError();
 }
@@ -648,9 +712,11 @@ cudaError_t launch_cg_stencil(const double* p, double* q, int n, int bc_kind, do
         stencil_fx_kernel<1, true, false, true><<<g.grid, g.block, g.smem, s>>>(fl, nullptr, n, sg, g.kz_per_cta,
                                                                                 &st->done, partials, st);
     } else {
-        const StencilGrid g = fx_grid(n, 2);
-        stencil_fx_kernel<1, true><<<g.grid, g.block, 0, s>>>(fl, nullptr, n, sg, g.kz_per_cta, &st->done,
-                                                              partials, st);
+        const StencilGrid g = pair_grid(n);
+        const size_t smem = pp_smem_bytes<1>();
+        opt_in_smem(stencil_pair_kernel<true>, smem);
+        stencil_pair_kernel<true><<<g.grid, g.block, smem, s>>>(p, nullptr, q, nullptr, n, sg, g.kz_per_cta, partials,
+                                                               st);
     }
     return cudaGetLastError();
 }

@@ -35,7 +35,7 @@ def still_works(ctx, n=16):
 @pytest.mark.parametrize("where", ["interior", "boundary_data"])
 def test_nonfinite_input_reports_nan(where):
     n, nc = 32, 4
-    f, g1, g2 = P.exp_sum().data(n, 1)
+    f, g1, g2 = (a.copy() for a in P.exp_sum().data(n, 1))
     if where == "interior":
         f[n // 2, n // 3, n // 4] = np.nan      # a right-hand side value
     else:

@@ -273,20 +273,25 @@ def test_excmg_solve_matches_oracle(name, bc_kind, variant):
 
 
 _ORACLE_128 = {}
-# (tolerance schedule, tol, Bi-CG cap per call of the WHILE loop): the small
-# cap makes the loop restart Bi-CG several times per level and end levels on
-# the stagnation rule
-CASES_128 = [("uniform", 1e-6, 100000), ("paper", 1e-6, 100000), ("uniform", 1e-8, 8)]
+# (tolerance schedule, tol, Bi-CG cap per call of the WHILE loop, cap per
+# level).  The small per-call cap makes the loop restart Bi-CG several times
+# per level and end levels on the stagnation rule.  In the paper's schedule
+# the 32^3 level (eps / 100) is held to 60 iterations: stopping decisions
+# taken after hundreds of Bi-CG steps can fall one iteration apart between
+# two correct FP64 runs (their rounding differs), while decisions after a
+# few dozen steps, and a cap, are the same on both sides; the 64^3 level
+# still runs to its paper tolerance eps / 10.
+CASES_128 = [("uniform", 1e-6, 100000, 400), ("paper", 1e-6, 100000, 60), ("uniform", 1e-8, 8, 400)]
 
 
 def _oracle_128(bc_kind, case):
     """The oracle's solve of the 128^3 case, computed once per session."""
     key = (bc_kind, case)
     if key not in _ORACLE_128:
-        tol_mode, tol, max_iter = case
+        tol_mode, tol, max_iter, max_total = case
         f, g1, g2 = P.exp_sum().data(128, bc_kind)
         _ORACLE_128[key] = oracle.excmg(128, 8, bc_kind, f, g1, g2, tol, tol_mode=tol_mode, max_iter=max_iter,
-                                        max_total=400)
+                                        max_total=max_total)
     return _ORACLE_128[key]
 
 
@@ -301,14 +306,14 @@ def test_excmg_solve_128_matches_oracle(bc_kind, case, schedule):
     hand-offs, under both tolerance schedules of Alg. 1 line 5.  Every level
     takes the oracle's Bi-CG iterations and calls and ends the same way; u_h
     and u~ match the oracle's entry by entry."""
-    tol_mode, tol, max_iter = case
+    tol_mode, tol, max_iter, max_total = case
     n, nc = 128, 8
     f, g1, g2 = P.exp_sum().data(n, bc_kind)
     ctx = B.Context()
     ctx.set_schedule(schedule)
     uh = torch.empty((n + 1,) * 3, dtype=torch.float64, device=DEV)
     ut, stats = B.excmg_solve(n, nc, bc_kind, dev(f), dev(g1), dev(g2), tol, tol_mode=tol_mode, max_iter=max_iter,
-                              max_total=400, u_h_out=uh, return_stats=True, ctx=ctx)
+                              max_total=max_total, u_h_out=uh, return_stats=True, ctx=ctx)
     ref_h, ref_t, ref_stats = _oracle_128(bc_kind, case)
     assert [s["iters"] for s in stats] == [int(v) for v in ref_stats[:, 0]]
     assert [s["calls"] for s in stats] == [int(v) for v in ref_stats[:, 2]]
@@ -318,7 +323,7 @@ def test_excmg_solve_128_matches_oracle(bc_kind, case, schedule):
     L = len(stats) - 2
     for l, st in enumerate(stats[2:], start=2):
         eps_i = tol * (10.0 ** (l - 1 - L) if tol_mode == "paper" else 1.0)
-        assert st["relres"] <= eps_i or st["stagnated"]
+        assert st["relres"] <= eps_i or st["stagnated"] or st["iters"] == max_total
         assert st["relres"] == pytest.approx(ref_stats[l, 1], rel=1e-6)
 
 
