@@ -34,11 +34,9 @@ if ROOT not in sys.path:
     sys.path.insert(0, ROOT)
 
 METRIC = "EXCMG solve s @512³ FP64 vs FP32+refine; stencil HBM GB/s % peak; p99 latency"
-# Work of one solve in work units (one Bi-CG iteration on the finest grid, as
-# the paper counts cost), per boundary kind, for the default workload; used
-# only by the CPU-oracle legs to scale a timed sample to a whole solve when
-# the GPU counts are not at hand.
-WU_DEFAULT = {1: 44.1, 2: 20.1}
+# The CPU oracle's own per-level Bi-CG counts on the default workload, written
+# by `python -m oracle.work_units` (a run of the oracle's whole 512^3 solve).
+ORACLE_COUNTS = os.path.join(ROOT, "oracle", "excmg_512_counts.json")
 
 
 def parse(argv=None):
@@ -152,60 +150,161 @@ class ClockSampler:
 
 
 # ------------------------------------------------------------- CPU oracle
-def oracle_sample(n: int, nc: int, bc_kinds, wu: dict):
-    """Time the CPU oracle on a bounded sample of the workload: Bi-CG
-    iterations on the 256^3 level of the same problem (three more iterations
-    in the second call than in the first; the difference over three is one
-    iteration), then scale to one solve: seconds per iteration x
-    ((512-1)/(256-1))^3 x the solve's work units.  Single-threaded C."""
-    import oracle
-    from paper_1901_05118_gb300 import problems
+def host_threads() -> int:
+    """Host CPUs this process may run on."""
+    try:
+        return len(os.sched_getaffinity(0))
+    except (AttributeError, OSError):
+        return os.cpu_count() or 1
 
-    prob = problems.exp_sum()
-    ns = n // 2
-    t_it = []
-    for bc in bc_kinds:
-        f, g1, g2 = prob.data(ns, bc)
-        fh = oracle.assemble_rhs(ns, bc, f, g1, g2)
-        x0 = g1.copy()
+
+class OracleSampler:
+    """The CPU oracle (oracle/, plain C, FP64) timed on bounded samples of the
+    workload and scaled to one whole solve with the oracle's own counts.
+
+    A whole oracle solve of the 512^3 workload takes minutes, so one timed
+    sample is: on every Bi-CG level N = 4 nc .. n, one Bi-CG iteration of the
+    oracle (the time of a 1-iteration call minus that of a 0-iteration call
+    on the level's own right-hand side), times the oracle's iterations on that
+    level; plus, measured once, each level's fixed work of Alg. 1 (assembly
+    of f_h, EXP_finite, the true residuals of the WHILE loop).  The counts are
+    the oracle's own from a whole run (oracle/excmg_512_counts.json); without
+    that file for this workload there is no value."""
+
+    def __init__(self, n: int, nc: int, threads: int):
+        import oracle
+        from paper_1901_05118_gb300 import problems
+
+        self.oracle, self.n, self.nc = oracle, n, nc
+        self.threads = oracle.set_threads(threads)
+        self.prob = problems.exp_sum()
+        self.counts = None
+        try:
+            rec = json.load(open(ORACLE_COUNTS))
+            if rec["n_finest"] == n and rec["n_coarsest"] == nc:
+                self.counts = {int(k): v for k, v in rec["kinds"].items()}
+        except (OSError, ValueError, KeyError):
+            pass
+        self.levels = []
+        N = 4 * nc
+        while N <= n:
+            self.levels.append(N)
+            N *= 2
+        self.data = {}
+        self.fixed = {}
+
+    def _level(self, N, bc):
+        key = (N, bc)
+        if key not in self.data:
+            f, g1, g2 = self.prob.data(N, bc)
+            self.data[key] = (self.oracle.assemble_rhs(N, bc, f, g1, g2), np.ascontiguousarray(g1))
+        return self.data[key]
+
+    def iteration_s(self, N, bc):
+        """Seconds per oracle Bi-CG iteration on level N: (time of a k-iteration
+        call - time of a 0-iteration call) / k, k grown until the difference
+        is at least 0.2 s (at most 256 iterations)."""
+        fh, g1 = self._level(N, bc)
         t0 = time.perf_counter()
-        oracle.bicg(ns, bc, fh, x0, 0.0, max_iter=1)
-        t1 = time.perf_counter()
-        oracle.bicg(ns, bc, fh, x0, 0.0, max_iter=4)
-        t2 = time.perf_counter()
-        t_it.append(max(((t2 - t1) - (t1 - t0)) / 3.0, 1e-9))
-    scale = ((n - 1) / (ns - 1)) ** 3
-    per_solve = [t * scale * wu[bc] for t, bc in zip(t_it, bc_kinds)]
-    return sum(per_solve) / len(per_solve), {
-        "kind": "oracle", "cores": 1,
-        "sample": (f"single-threaded C oracle: one Bi-CG iteration on the {ns}^3 level of the same problem, "
-                   f"per boundary kind ({', '.join(f'{t:.2f} s' for t in t_it)}; difference of 4- and "
-                   f"1-iteration calls over 3), scaled by "
-                   f"((N-1)/({ns}-1))^3 to {n}^3 and by the solve's work units "
-                   f"({', '.join(f'{wu[b]:.1f}' for b in bc_kinds)} finest-grid iterations)")}
+        self.oracle.bicg(N, bc, fh, g1, 0.0, max_iter=0)
+        setup = time.perf_counter() - t0
+        k = 1
+        while True:
+            t0 = time.perf_counter()
+            self.oracle.bicg(N, bc, fh, g1, 0.0, max_iter=k)
+            run = time.perf_counter() - t0 - setup
+            if run >= 0.2 or k >= 256:
+                return max(run / k, 1e-9)
+            k *= 4
+
+    def fixed_s(self, N, bc, calls):
+        """Alg. 1's work on level N besides the Bi-CG iterations (timed once)."""
+        key = (N, bc)
+        if key not in self.fixed:
+            o = self.oracle
+            f, g1, g2 = self.prob.data(N, bc)
+            u1 = np.ascontiguousarray(self.prob.exact(N // 2))
+            u0 = np.ascontiguousarray(self.prob.exact(N // 4))
+            t0 = time.perf_counter()
+            fh = o.assemble_rhs(N, bc, f, g1, g2)
+            w = o.exp_finite(N, u1, u0)
+            t1 = time.perf_counter()
+            o.residual_norm(N, bc, fh, w)
+            t2 = time.perf_counter()
+            self.fixed[key] = (t1 - t0, t2 - t1)
+        setup, resid = self.fixed[key]
+        return setup + (calls + 1) * resid
+
+    def solve_s(self, bc):
+        """Seconds of one oracle solve of the workload with kind bc, and the
+        per-level breakdown; (None, None) without the oracle's counts."""
+        if self.counts is None:
+            return None, None
+        lv = {L["n"]: L for L in self.counts[bc]["levels"]}
+        total, parts = 0.0, []
+        for N in self.levels:
+            t_it = self.iteration_s(N, bc)
+            t_fx = self.fixed_s(N, bc, lv[N]["calls"])
+            total += lv[N]["iters"] * t_it + t_fx
+            parts.append({"n": N, "iters": lv[N]["iters"], "iteration_s": round(t_it, 4), "fixed_s": round(t_fx, 3)})
+        return total, parts
+
+    def describe(self):
+        return (f"oracle (plain C, FP64) on {self.threads} host threads: per Bi-CG level N = "
+                f"{self.levels[0]}..{self.levels[-1]}, timed Bi-CG iterations (at least 0.2 s of them) x the oracle's own iterations "
+                f"on that level (oracle/excmg_512_counts.json, from a whole oracle solve), plus each level's "
+                f"assembly, EXP_finite and true residuals timed once; the direct solves of the two coarsest "
+                f"grids are not counted")
 
 
 def run_reference(args):
+    """The reference arm: the CPU oracle, timed as OracleSampler says, on the
+    same workload and metric.  Each step samples one kind of boundary data
+    (alternating); `value` is the mean over the timed steps of the oracle's
+    seconds per solve, `ms_per_step` the wall time a timed step took."""
     rank, world, local = dist_env()
     if rank != 0:
         return
-    bcs = (1, 2)
-    times = []
-    info = None
-    for s in range(args.warmup + args.steps):
+    sampler = OracleSampler(args.n, args.nc, host_threads())
+    if sampler.counts is None:
+        print(json.dumps({"impl": "reference", "unavailable": f"no oracle counts for {args.n}^3 / {args.nc}^3 "
+                          "(run python -m oracle.work_units)"}), flush=True)
+        return
+    values, walls, parts = [], [], {}
+    for s_ in range(args.warmup + args.steps):
+        bc = 1 + s_ % 2
         t0 = time.perf_counter()
-        v, info = oracle_sample(args.n, args.nc, bcs, WU_DEFAULT)
-        if s >= args.warmup:
-            times.append(v)
-    value = statistics.mean(times)
-    info["value"] = value
+        v, part = sampler.solve_s(bc)
+        wall = time.perf_counter() - t0
+        if s_ >= args.warmup:
+            values.append(v)
+            walls.append(wall)
+            parts[str(bc)] = part
+    value = statistics.mean(values)
+    info = {"kind": "oracle", "cores": sampler.threads, "host_cpus": os.cpu_count(), "value": value, "unit": "s",
+            "sample": sampler.describe(), "levels": parts,
+            "oracle_whole_solve_s_recorded": {k: v["solve_s"] for k, v in sampler.counts.items()}}
     line = {"impl": "reference", "metric": METRIC, "value": value, "unit": "s", "n_gpus": args.gpus,
-            "steps": args.steps, "warmup": args.warmup, "ms_per_step": 2 * value * 1e3,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": statistics.mean(walls) * 1e3,
             "higher_is_better": False, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
-            "data": "synthetic", "config": config(args),
-            "cpu_baseline": info, "e2e": {"value": value, "unit": "s", "h2d_bytes_per_step": 0,
-                                          "d2h_bytes_per_step": 0}}
+            "data": "synthetic", "config": config(args), "cpu_baseline": info,
+            "e2e": {"value": value, "unit": "s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line), flush=True)
+
+
+def cpu_baseline(args):
+    """The oracle on the host cores, one sample of each kind of boundary data
+    (OracleSampler), as seconds per solve."""
+    sampler = OracleSampler(args.n, args.nc, host_threads())
+    if sampler.counts is None:
+        return {"kind": "oracle", "value": None, "unavailable": "no oracle counts for this workload"}
+    t0 = time.perf_counter()
+    per_kind = {bc: sampler.solve_s(bc) for bc in (1, 2)}
+    return {"kind": "oracle", "value": statistics.mean(v for v, _ in per_kind.values()), "unit": "s",
+            "cores": sampler.threads, "host_cpus": os.cpu_count(), "sample": sampler.describe(),
+            "sample_wall_s": time.perf_counter() - t0,
+            "levels": {str(bc): part for bc, (_, part) in per_kind.items()},
+            "oracle_whole_solve_s_recorded": {k: v["solve_s"] for k, v in sampler.counts.items()}}
 
 
 def config(args):
@@ -412,10 +511,7 @@ def run_ours(args):
             "work_units": {str(bc): round(w, 2) for bc, w in wu.items()}, "shadow_elided_leg": elided,
             "precision_leg": mixed, "batched_leg": batched, "serving_leg": served}
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
-        cpu_value, info = oracle_sample(n, nc, bcs, wu)
-        info["value"] = cpu_value
-        info["unit"] = "s"
-        line["cpu_baseline"] = info
+        line["cpu_baseline"] = cpu_baseline(args)
     if rank == 0:
         print(json.dumps(line), flush=True)
     if world > 1:

@@ -29,12 +29,15 @@ _I = ctypes.POINTER(ctypes.c_int)
 
 
 def build(force: bool = False) -> str:
-    """Compile the oracle into ``oracle/liboracle.so`` (gcc, FP64, no FMA contraction)."""
+    """Compile the oracle into ``oracle/liboracle.so`` (gcc, FP64, no FMA
+    contraction; with OpenMP where the compiler has it)."""
     if force or not os.path.exists(_LIB) or os.path.getmtime(_LIB) < os.path.getmtime(_SRC):
         tmp = _LIB + f".tmp{os.getpid()}"
-        subprocess.check_call(
-            ["gcc", "-O2", "-std=c11", "-fPIC", "-shared", "-ffp-contract=off",
-             "-o", tmp, _SRC, "-lm"])
+        base = ["gcc", "-O2", "-std=c11", "-fPIC", "-shared", "-ffp-contract=off", "-o", tmp, _SRC, "-lm"]
+        try:
+            subprocess.check_call(base[:-1] + ["-fopenmp", "-lm"], stderr=subprocess.DEVNULL)
+        except subprocess.CalledProcessError:
+            subprocess.check_call(base)
         os.replace(tmp, _LIB)
     return _LIB
 
@@ -65,12 +68,21 @@ def _load():
                                   _D, _D, _D]
         lib.orc_error_norms.argtypes = [ctypes.c_int, _D, _D, _D]
         lib.orc_error_norms.restype = None
+        lib.orc_set_threads.argtypes = [ctypes.c_int]
+        lib.orc_set_threads.restype = ctypes.c_int
         _lib = lib
     return _lib
 
 
 class OracleError(RuntimeError):
     pass
+
+
+def set_threads(n: int) -> int:
+    """Threads of the oracle's independent loops (the operator and the vector
+    updates); sums keep their sequential order, so results are the same bits
+    for any count.  Returns the count in effect (1 without OpenMP)."""
+    return int(_load().orc_set_threads(int(n)))
 
 
 def _p(a: np.ndarray):

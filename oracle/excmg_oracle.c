@@ -20,18 +20,42 @@
  *   bc_kind = 2: g2 = d2u/dn2, eq. (BC2).
  *
  * Everything is double precision; compile with -ffp-contract=off so that no
- * multiply-add is fused behind the reader's back.  Single-threaded.
+ * multiply-add is fused behind the reader's back.
+ *
+ * Threads: when built with OpenMP, loops whose iterations are independent
+ * (one output entry each: the operator, the vector updates) are split over
+ * threads; every entry is still computed by one thread in the same order of
+ * operations, and every sum over entries (the inner products) stays a single
+ * sequential loop, so the results are the same bits for any thread count.
+ * orc_set_threads() chooses the count (default 1).
  */
 #include <math.h>
 #include <stdint.h>
 #include <stdlib.h>
 #include <string.h>
+#ifdef _OPENMP
+#include <omp.h>
+#endif
 
 #define ORC_OK 0
 #define ORC_ERR_ARG (-1)
 #define ORC_ERR_OOM (-2)
 #define ORC_ERR_BREAKDOWN (-3)
 #define ORC_ERR_PIVOT (-8)
+
+static int orc_threads = 1;
+
+/* Threads of the parallel loops (1 = sequential; ignored without OpenMP).
+ * Returns the count in effect. */
+int orc_set_threads(int n) {
+#ifdef _OPENMP
+    orc_threads = n < 1 ? 1 : n;
+#else
+    (void)n;
+    orc_threads = 1;
+#endif
+    return orc_threads;
+}
 
 static size_t nidx(int N, int i, int j, int k) {
     return ((size_t)k * (size_t)(N + 1) + (size_t)j) * (size_t)(N + 1) + (size_t)i;
@@ -131,6 +155,7 @@ int orc_stencil_apply(int N, int bc_kind, int transpose, const double *u, double
     total = (size_t)(N + 1) * (size_t)(N + 1) * (size_t)(N + 1);
     s = ghost_sign(bc_kind);
     if (!transpose) {
+#pragma omp parallel for num_threads(orc_threads) private(i, j, t) schedule(static)
         for (k = 0; k <= N; ++k)
             for (j = 0; j <= N; ++j)
                 for (i = 0; i <= N; ++i) {
@@ -155,7 +180,7 @@ int orc_stencil_apply(int N, int bc_kind, int transpose, const double *u, double
                     }
                     y[nidx(N, i, j, k)] = acc;
                 }
-    } else {
+    } else if (orc_threads <= 1) {
         memset(y, 0, total * sizeof(double));
         for (k = 1; k <= N - 1; ++k)
             for (j = 1; j <= N - 1; ++j)
@@ -174,6 +199,43 @@ int orc_stencil_apply(int N, int bc_kind, int transpose, const double *u, double
                             y[nidx(N, ti.qi, ti.qj, ti.qk)] += s * TAPS[t].c * up;
                     }
                 }
+    } else {
+        /* The same scatter on several threads.  Rows are visited in the same
+         * lexicographic order, but the writes are grouped by the plane kt of
+         * the column they land in: plane kt of y receives them from rows
+         * kt-2 .. kt+2 only (a ghost folds onto its own row's plane), in the
+         * order the single pass above delivers them, so the planes of y are
+         * independent and every entry gets the same bits. */
+        int kt, by_dz[5][25], n_dz[5] = {0, 0, 0, 0, 0};
+        /* the taps of each plane offset dz = -2..2, in table order */
+        for (t = 0; t < 25; ++t) by_dz[TAPS[t].dz + 2][n_dz[TAPS[t].dz + 2]++] = t;
+        memset(y, 0, total * sizeof(double));
+#pragma omp parallel for num_threads(orc_threads) private(i, j, k, t) schedule(dynamic, 1)
+        for (kt = 1; kt <= N - 1; ++kt)
+            for (k = (kt - 2 > 1 ? kt - 2 : 1); k <= (kt + 2 < N - 1 ? kt + 2 : N - 1); ++k)
+                for (j = 1; j <= N - 1; ++j)
+                    for (i = 1; i <= N - 1; ++i) {
+                        double up = u[nidx(N, i, j, k)];
+                        if (i >= 3 && i <= N - 3 && j >= 3 && j <= N - 3 && k >= 3 && k <= N - 3) {
+                            const int g = kt - k + 2;
+                            int m;
+                            for (m = 0; m < n_dz[g]; ++m) {
+                                const orc_tap *tp = &TAPS[by_dz[g][m]];
+                                y[nidx(N, i + tp->dx, j + tp->dy, kt)] += tp->c * up;
+                            }
+                            continue;
+                        }
+                        for (t = 0; t < 25; ++t) {
+                            orc_tapinfo ti;
+                            if (k + TAPS[t].dz != kt && k != kt) continue;   /* cannot land in plane kt */
+                            ti = classify(N, i, j, k, &TAPS[t]);
+                            if (ti.qk != kt) continue;
+                            if (ti.kind == TAP_UNKNOWN)
+                                y[nidx(N, ti.qi, ti.qj, ti.qk)] += TAPS[t].c * up;
+                            else if (ti.kind == TAP_GHOST)
+                                y[nidx(N, ti.qi, ti.qj, ti.qk)] += s * TAPS[t].c * up;
+                        }
+                    }
     }
     return ORC_OK;
 }
@@ -419,6 +481,7 @@ int orc_bicg_shadow(int N, int bc_kind, const double *b, double *x, const double
         sigma = idot(N, ps, Ap);
         if (sigma == 0.0 || !isfinite(sigma)) { status = ORC_ERR_BREAKDOWN; break; }
         alpha = rho / sigma;
+#pragma omp parallel for num_threads(orc_threads) private(i, j, q) schedule(static)
         for (k = 1; k <= N - 1; ++k)
             for (j = 1; j <= N - 1; ++j)
                 for (i = 1; i <= N - 1; ++i) {
@@ -429,6 +492,7 @@ int orc_bicg_shadow(int N, int bc_kind, const double *b, double *x, const double
                 }
         rho_new = idot(N, rs, r);
         beta = rho_new / rho;
+#pragma omp parallel for num_threads(orc_threads) private(i, j, q) schedule(static)
         for (k = 1; k <= N - 1; ++k)
             for (j = 1; j <= N - 1; ++j)
                 for (i = 1; i <= N - 1; ++i) {

@@ -71,16 +71,49 @@ __device__ __forceinline__ int pp_slot(int tid, int s) {
     return (2 + (k >> 2)) * PP_HX + (c < 2 ? c : PP_HX - 4 + c);
 }
 
-__device__ __forceinline__ void cp_async8(void* dst, const void* src, unsigned src_bytes) {
-    asm volatile("cp.async.ca.shared.global [%0], [%1], 8, %2;" ::"r"(smem_u32(dst)), "l"(src), "r"(src_bytes)
-                 : "memory");
-}
 __device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;" ::: "memory"); }
 template <int N>
 __device__ __forceinline__ void cp_async_wait() {
     asm volatile("cp.async.wait_group %0;" ::"n"(N) : "memory");
 }
 __device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wait_all;" ::: "memory"); }
+
+__device__ __forceinline__ double lds_f64(unsigned a) {
+    double v;
+    asm volatile("ld.shared.f64 %0, [%1];" : "=d"(v) : "r"(a) : "memory");
+    return v;
+}
+__device__ __forceinline__ long long lds_s64(unsigned a) {
+    long long v;
+    asm volatile("ld.shared.s64 %0, [%1];" : "=l"(v) : "r"(a) : "memory");
+    return v;
+}
+__device__ __forceinline__ void sts_s64(unsigned a, long long v) {
+    asm volatile("st.shared.s64 [%0], %1;" ::"r"(a), "l"(v) : "memory");
+}
+__device__ __forceinline__ void cp_async8_u32(unsigned dst, const void* src, unsigned src_bytes) {
+    asm volatile("cp.async.ca.shared.global [%0], [%1], 8, %2;" ::"r"(dst), "l"(src), "r"(src_bytes) : "memory");
+}
+// x >> k for 0 <= k, 0 once k >= 32 (PTX clamps the shift amount)
+__device__ __forceinline__ unsigned shr_clamp(unsigned x, unsigned k) {
+    unsigned r;
+    asm("shr.b32 %0, %1, %2;" : "=r"(r) : "r"(x), "r"(k));
+    return r;
+}
+
+// to_fixed (march_fx.cuh) with the biased exponent e of v already at hand
+// and the 64-bit shift written as clamped 32-bit shifts: the same value,
+// m >> (E - max(e, 1)) with the sign of v, 0 once the shift reaches 64.
+__device__ __forceinline__ long long to_fixed_e(double v, unsigned e, int E) {
+    const unsigned hi = (unsigned)__double2hiint(v), lo = (unsigned)__double2loint(v);
+    const unsigned mh = (hi & 0xFFFFFu) | (e != 0u ? 0x100000u : 0u);
+    const unsigned d = (unsigned)(E - (int)max(e, 1u));
+    const unsigned rlo = shr_clamp(__funnelshift_rc(lo, mh, d), (unsigned)max((int)d - 32, 0));
+    const unsigned rhi = shr_clamp(mh, d);
+    const unsigned sg = (unsigned)((int)hi >> 31);   // 0 or all ones
+    const unsigned long long m = ((unsigned long long)(rhi ^ sg) << 32) | (rlo ^ sg);
+    return (long long)(m - (unsigned long long)(long long)(int)sg);
+}
 
 // a * w for a 64-bit integer a and a small positive weight w (|a w| < 2^63):
 // one 32 x 32 -> 64 product of the low word and one multiply-add of the high
@@ -108,32 +141,38 @@ __device__ __forceinline__ double fx_result_cvt(long long acc, int E, bool poiso
 // writes q (and q* = q unless kElide) and adds this thread's share of
 // sigma = (p*, q) to *dot.  kElide: p* is not read and q* not written (the
 // shadow-elided mode; the same sums in the same order).  kCvt: round the
-// outputs through the hardware integer-to-double conversion.
+// outputs through the hardware integer-to-double conversion.  Shared memory
+// is addressed through 32-bit shared-window addresses.
 template <bool kElide, bool kCvt>
 __device__ __forceinline__ bool pp_march(const double* __restrict__ p, const double* __restrict__ ps,
                                          double* __restrict__ q, double* __restrict__ qs, int n, int sigma, int bx,
                                          int by, int kz0, int kz1, unsigned char* smem, double* dot) {
     constexpr int NF = kElide ? 1 : 2;
+    constexpr unsigned kField = PP_HALO * 8u;          // bytes of one field of a stage
+    constexpr unsigned kStage = NF * kField;           // bytes of one stage
+    constexpr unsigned kTile = PP_HALO * 8u;           // bytes of one fixed-point tile
     __shared__ int wmax[2][PP_NT / 32];
-    double* const raw = reinterpret_cast<double*>(smem);   // [stage][field][halo]
-    long long* const tiles = reinterpret_cast<long long*>(smem + (size_t)PP_STAGES * NF * PP_HALO * sizeof(double));
+    const unsigned raw = smem_u32(smem);
+    const unsigned tiles = raw + PP_STAGES * kStage;
     const int np = n + 1;
-    const size_t plane = (size_t)np * np;
+    const unsigned plane = (unsigned)np * (unsigned)np;
     const int tx = threadIdx.x, ty = threadIdx.y, tid = ty * PP_TX + tx;
     const int lane = tid & 31, warp = tid >> 5;
     const int i0 = 1 + bx * PP_TX, j0 = 1 + by * PP_OY;
     const bool ring = tid < PP_RING;
 
-    // slots: halo index, in-plane offset of the node, whether it is an unknown
-    int se[3], soff[3];
+    // slots: byte offset in a stage / tile, in-plane node index, whether the
+    // node is an unknown (else it reads as zero)
+    unsigned so[3], sidx[3];
     bool sin[3];
 #pragma unroll
     for (int s = 0; s < 3; ++s) {
-        se[s] = (s < 2 || ring) ? pp_slot(tid, s) : 0;
-        const int ly = se[s] / PP_HX, lx = se[s] - ly * PP_HX;
+        const int e = (s < 2 || ring) ? pp_slot(tid, s) : 0;
+        const int ly = e / PP_HX, lx = e - ly * PP_HX;
         const int gi = i0 - 2 + lx, gj = j0 - 2 + ly;
+        so[s] = 8u * (unsigned)e;
         sin[s] = (s < 2 || ring) && gi >= 1 && gi <= n - 1 && gj >= 1 && gj <= n - 1;
-        soff[s] = sin[s] ? gj * np + gi : 0;
+        sidx[s] = sin[s] ? (unsigned)(gj * np + gi) : 0u;
     }
     const int i = i0 + tx, ja = j0 + 2 * ty;
     const bool act0 = (i <= n - 1) && (ja <= n - 1);
@@ -141,50 +180,53 @@ __device__ __forceinline__ bool pp_march(const double* __restrict__ p, const dou
     const int cx = (i == 1) + (i == n - 1);
     const int c0 = cx + (ja == 1) + (ja == n - 1);
     const int c1 = cx + (ja + 1 == 1) + (ja + 1 == n - 1);
-    const int rx = tx + 2, ry = 2 * ty + 2;
+    // byte offset in a tile of this thread's first output (row ry, column rx)
+    const unsigned tc = 8u * (unsigned)((2 * ty + 2) * PP_HX + tx + 2);
     const int T = kz1 - kz0 + 4;   // input planes kz0 - 2 .. kz1 + 1
 
-    // copy plane t (all of this thread's slots, both fields) into its stage;
-    // nodes outside the interior are zero-filled; always one commit group
+    // copy plane t (all of this thread's slots) into its stage; nodes
+    // outside the interior are zero-filled; always one commit group
     auto issue = [&](int t) {
         if (t < T) {
             const int zin = kz0 - 2 + t;
             const bool zok = zin >= 1 && zin <= n - 1;
-            const size_t zb = zok ? (size_t)zin * plane : 0;
-            double* st = raw + (size_t)(t % PP_STAGES) * NF * PP_HALO;
+            const unsigned zb = zok ? (unsigned)zin * plane : 0u;
+            const unsigned st = raw + (unsigned)(t & (PP_STAGES - 1)) * kStage;
 #pragma unroll
             for (int s = 0; s < 3; ++s) {
                 if (s < 2 || ring) {
                     const bool ld = zok && sin[s];
-                    const size_t o = ld ? zb + soff[s] : 0;
-                    cp_async8(st + se[s], p + o, ld ? 8u : 0u);
-                    if (!kElide) cp_async8(st + PP_HALO + se[s], ps + o, ld ? 8u : 0u);
+                    const unsigned gidx = ld ? zb + sidx[s] : 0u;
+                    const unsigned nb = ld ? 8u : 0u;
+                    cp_async8_u32(st + so[s], p + gidx, nb);
+                    if (!kElide) cp_async8_u32(st + kField + so[s], ps + gidx, nb);
                 }
             }
         }
         cp_async_commit();
     };
-    // read back plane t's slots (its copies complete), publish the warp's
-    // exponent maximum for plane t; false if p* differs from p in a slot
-    auto scan = [&](int t, double (&v)[3]) -> bool {
-        const double* st = raw + (size_t)(t % PP_STAGES) * NF * PP_HALO;
-        unsigned diff = 0u;
-        int emax = 0;
+    // read back plane t's slots (its copies complete) and their exponents,
+    // publish the warp's exponent maximum; false if p* differs from p
+    auto scan = [&](int t, double (&v)[3], unsigned (&ev)[3]) -> bool {
+        const unsigned st = raw + (unsigned)(t & (PP_STAGES - 1)) * kStage;
+        unsigned diff = 0u, emax = 0u;
 #pragma unroll
         for (int s = 0; s < 3; ++s) {
             v[s] = 0.0;
+            ev[s] = 0u;
             if (s < 2 || ring) {
-                v[s] = st[se[s]];
-                emax = max(emax, exponent_of(v[s]));
+                v[s] = lds_f64(st + so[s]);
+                ev[s] = ((unsigned)__double2hiint(v[s]) >> 20) & 0x7FFu;
+                emax = max(emax, ev[s]);
                 if (!kElide) {
-                    const double w = st[PP_HALO + se[s]];
+                    const double w = lds_f64(st + kField + so[s]);
                     diff |= ((unsigned)__double2loint(v[s]) ^ (unsigned)__double2loint(w)) |
                             ((unsigned)__double2hiint(v[s]) ^ (unsigned)__double2hiint(w));
                 }
             }
         }
-        emax = (int)__reduce_max_sync(0xffffffffu, (unsigned)emax);
-        if (lane == 0) wmax[t & 1][warp] = emax;
+        emax = __reduce_max_sync(0xffffffffu, emax);
+        if (lane == 0) wmax[t & 1][warp] = (int)emax;
         return diff == 0u;
     };
     auto plane_max = [&](int t) { return (int)__reduce_max_sync(0xffffffffu, (unsigned)wmax[t & 1][lane & 7]); };
@@ -193,7 +235,8 @@ __device__ __forceinline__ bool pp_march(const double* __restrict__ p, const dou
     for (int t = 0; t < PP_AHEAD; ++t) issue(t);
     cp_async_wait<PP_AHEAD - 1>();
     double cur[3];
-    bool same = scan(0, cur);
+    unsigned ecur[3];
+    bool same = scan(0, cur, ecur);
     if (!__syncthreads_and(same)) {
         cp_async_wait_all();
         return false;
@@ -213,12 +256,13 @@ __device__ __forceinline__ bool pp_march(const double* __restrict__ p, const dou
         issue(t + PP_AHEAD);
         cp_async_wait<PP_AHEAD - 1>();   // planes up to t + 1 have landed
         double nxt[3] = {0.0, 0.0, 0.0};
-        same = t + 1 < T ? scan(t + 1, nxt) : true;
+        unsigned enx[3] = {0u, 0u, 0u};
+        same = t + 1 < T ? scan(t + 1, nxt, enx) : true;
         // plane t on scale E into its tile
-        long long* tl = tiles + (size_t)(t & 1) * PP_HALO;
+        const unsigned tl = tiles + (unsigned)(t & 1) * kTile;
 #pragma unroll
         for (int s = 0; s < 3; ++s)
-            if (s < 2 || ring) tl[se[s]] = to_fixed(cur[s], E);
+            if (s < 2 || ring) sts_s64(tl + so[s], to_fixed_e(cur[s], ecur[s], E));
         // every tile of plane t written, every exponent of plane t + 1
         // published, every read of the tile of plane t - 2 done
         if (!__syncthreads_and(same)) {
@@ -229,16 +273,17 @@ __device__ __forceinline__ bool pp_march(const double* __restrict__ p, const dou
 
         const int zin = kz0 - 2 + t;
         const int cz = (zin == 1) + (zin == n - 1);
-        auto at = [&](int yy, int xx) { return tl[yy * PP_HX + xx]; };
-        const long long cm2 = at(ry - 2, rx), cm1 = at(ry - 1, rx), cc0 = at(ry, rx), cc1 = at(ry + 1, rx),
-                        cc2 = at(ry + 2, rx), cc3 = at(ry + 3, rx);
-        // x-neighbour sums at distance 1 (rows ry-1 .. ry+2) and 2 (rows ry, ry+1)
-        const long long h1m = at(ry - 1, rx - 1) + at(ry - 1, rx + 1);
-        const long long h10 = at(ry, rx - 1) + at(ry, rx + 1);
-        const long long h11 = at(ry + 1, rx - 1) + at(ry + 1, rx + 1);
-        const long long h12 = at(ry + 2, rx - 1) + at(ry + 2, rx + 1);
-        const long long h20 = at(ry, rx - 2) + at(ry, rx + 2);
-        const long long h21 = at(ry + 1, rx - 2) + at(ry + 1, rx + 2);
+        const unsigned b0 = tl + tc;
+        auto at = [&](int dy, int dx) { return lds_s64(b0 + 8u * (unsigned)(dy * PP_HX + dx)); };
+        const long long cm2 = at(-2, 0), cm1 = at(-1, 0), cc0 = at(0, 0), cc1 = at(1, 0), cc2 = at(2, 0),
+                        cc3 = at(3, 0);
+        // x-neighbour sums at distance 1 (rows -1 .. 2) and 2 (rows 0, 1)
+        const long long h1m = at(-1, -1) + at(-1, 1);
+        const long long h10 = at(0, -1) + at(0, 1);
+        const long long h11 = at(1, -1) + at(1, 1);
+        const long long h12 = at(2, -1) + at(2, 1);
+        const long long h20 = at(0, -2) + at(0, 2);
+        const long long h21 = at(1, -2) + at(1, 2);
         long long P0[2], P1[2], C[2];
         {   // output row ja: same plane (42 + sigma c) u - 12 (4 axis) + (4 at 2) + 2 (4 diagonals);
             // planes +-1: 2 (4 axis) - 12 u; planes +-2: u
@@ -259,15 +304,16 @@ __device__ __forceinline__ bool pp_march(const double* __restrict__ p, const dou
         }
         const int zo = zin - 2;
         const bool zstore = zo >= kz0 && zo < kz1;
+        const unsigned orow = ((unsigned)zo * (unsigned)np + (unsigned)ja) * (unsigned)np + (unsigned)i;
 #pragma unroll
         for (int qq = 0; qq < 2; ++qq) {
             acc[qq][0] += C[qq];
             acc[qq][1] += P1[qq];
             acc[qq][2] += P0[qq];
             acc[qq][3] += P1[qq];
-            acc[qq][4] += C[qq];
+            acc[qq][4] = C[qq];
             if (zstore && (qq == 0 ? act0 : act1)) {
-                const size_t o = ((size_t)zo * np + ja + qq) * np + i;
+                const unsigned o = orow + (unsigned)qq * (unsigned)np;
                 const double val = kCvt ? fx_result_cvt(acc[qq][0], E, poisoned) : fx_result(acc[qq][0], E, poisoned);
                 q[o] = val;
                 if (!kElide) qs[o] = val;
@@ -278,7 +324,6 @@ __device__ __forceinline__ bool pp_march(const double* __restrict__ p, const dou
             acc[qq][1] = acc[qq][2];
             acc[qq][2] = acc[qq][3];
             acc[qq][3] = acc[qq][4];
-            acc[qq][4] = 0;
             pc2[qq] = pc1[qq];
             pc1[qq] = cur[qq];
         }
@@ -289,11 +334,14 @@ __device__ __forceinline__ bool pp_march(const double* __restrict__ p, const dou
 #pragma unroll
             for (int qq = 0; qq < 2; ++qq)
 #pragma unroll
-                for (int k = 0; k < 5; ++k) acc[qq][k] = dd >= 63 ? 0 : (acc[qq][k] >> dd);
+                for (int k = 0; k < 4; ++k) acc[qq][k] = dd >= 63 ? 0 : (acc[qq][k] >> dd);
             E = ep;
         }
 #pragma unroll
-        for (int s = 0; s < 3; ++s) cur[s] = nxt[s];
+        for (int s = 0; s < 3; ++s) {
+            cur[s] = nxt[s];
+            ecur[s] = enx[s];
+        }
     }
     cp_async_wait_all();
     *dot = d;

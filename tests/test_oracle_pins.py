@@ -494,3 +494,24 @@ def test_excmg_paper_tolerance_schedule(bc_kind):
     assert st_p[2, 0] > st_u[2, 0]          # the coarsest Bi-CG grid: 100x tighter
     # the uniform schedule does not meet the coarsest level's paper bound
     assert st_u[2, 1] > eps * 10.0 ** (1 - L)
+
+
+# ------------------------------------- threads change no bit of the oracle
+def test_oracle_threads_give_the_same_bits():
+    """The operator (A and the scattered A^T), Bi-CG and a whole solve return
+    identical bits with one thread and with several (the parallel loops have
+    independent iterations; inner products stay sequential)."""
+    prob = P.exp_sum()
+    N = 24
+    u = P.random_field(N, 77)
+    f, g1, g2 = prob.data(N, 2)
+    out = {}
+    for th in (1, 4):
+        got = oracle.set_threads(th)
+        out[th] = (oracle.stencil_apply(N, 1, u), oracle.stencil_apply(N, 2, u, transpose=True),
+                   oracle.bicg(N, 1, u, np.zeros_like(u), 0.0, max_iter=15)[0],
+                   oracle.excmg(N, 6, 2, f, g1, g2, 1e-9)[1])
+        assert got == th or got == 1
+    oracle.set_threads(1)
+    for a, b in zip(out[1], out[4]):
+        np.testing.assert_array_equal(a, b)
