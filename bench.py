@@ -67,6 +67,7 @@ def parse(argv=None):
     ap.add_argument("--bc", type=int, default=1, help="--case: kind of boundary data")
     ap.add_argument("--iters", type=int, default=4, help="--case bicg: Bi-CG iterations")
     ap.add_argument("--reps", type=int, default=3, help="--case stencil: operator applications")
+    ap.add_argument("--shadow", choices=["full", "elided"], default="full", help="--case bicg: shadow mode")
     return ap.parse_args(argv)
 
 
@@ -729,6 +730,7 @@ def profile_case(args):
     ctx = B.Context(dev)
     ctx.set_stencil(args.stencil)
     ctx.set_schedule(args.schedule)
+    ctx.set_shadow_mode(args.shadow)
     n = args.n
     gen = torch.Generator(device=dev)
     gen.manual_seed(0)

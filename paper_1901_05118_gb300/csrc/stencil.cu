@@ -150,9 +150,9 @@ constexpr bool kPairCvt = true;   // outputs rounded by the hardware conversion
 
 // the general two-field march, kept out of line: it runs only where p* != p
 __device__ __noinline__ double pair_two_field(const double* p, const double* ps, double* q, double* qs, int n,
-                                              int sigma, int kz0, int kz1) {
+                                              int sigma, int bx, int by, int kz0, int kz1) {
     const FxFields fl{{p, ps}, {q, qs}, {nullptr, nullptr}, {nullptr, nullptr}, 0.0, nullptr, nullptr};
-    return fx_march<2, true>(fl, nullptr, n, sigma, blockIdx.x, blockIdx.y, kz0, kz1);
+    return fx_march<2, true>(fl, nullptr, n, sigma, bx, by, kz0, kz1);
 }
 
 template <bool kElide>
@@ -169,7 +169,7 @@ stencil_pair_kernel(const double* __restrict__ p, const double* __restrict__ ps,
     if constexpr (!kElide) {
         if (!fast) {
             __syncthreads();
-            dot = pair_two_field(p, ps, q, qs, n, sigma, kz0, kz1);
+            dot = pair_two_field(p, ps, q, qs, n, sigma, blockIdx.x, blockIdx.y, kz0, kz1);
         }
     }
     __shared__ double sh[32];
@@ -328,10 +328,17 @@ bicg_persistent_kernel(BicgVectors v, size_t len, int n, int sigma, int gx, int 
                     else
                         dot += fx_march<2, true, true, true>(fd, nullptr, n, sigma, bx, by, kz0, kz1);
                 } else {
-                    if (kElide)
-                        dot += fx_march<1, true>(fl, nullptr, n, sigma, bx, by, kz0, kz1);
-                    else
-                        dot += fx_march<2, true>(fl, nullptr, n, sigma, bx, by, kz0, kz1);
+                    // the copy-ahead march (same sums as fx_march<2, true>);
+                    // the CTA's previous unit is done with the shared buffers
+                    __syncthreads();
+                    double dd = 0.0;
+                    if (pp_march<kElide, kPairCvt>(v.p, v.ps, v.q, v.qs, n, sigma, bx, by, kz0, kz1,
+                                                   persistent_stage_smem, &dd)) {
+                        dot += dd;
+                    } else if constexpr (!kElide) {
+                        __syncthreads();
+                        dot += pair_two_field(v.p, v.ps, v.q, v.qs, n, sigma, bx, by, kz0, kz1);
+                    }
                 }
             }
         }
@@ -346,38 +353,59 @@ bicg_persistent_kernel(BicgVectors v, size_t len, int n, int sigma, int gx, int 
         }
         alpha = rho / sigma_s;
         // phase B: x += alpha p; r -= alpha q; r* -= alpha q*; (r*, r), (r, r)
+        // (entries t, t + S of this thread loaded together,
+        // then updated and summed in index order)
         double vr = 0.0, vrr = 0.0;
         const double* const pcur = (kPointwise || !kFuse) ? v.p : pk;
         bool twin = true;   // as in bicg_update_kernel: vr == vrr so far
-        for (size_t t = (size_t)blockIdx.x * nthreads + tid; t < len; t += (size_t)G * nthreads) {
-            v.x[t] = v.x[t] + alpha * pcur[t];
-            if (kElide) {
-                const double rn = v.r[t] - alpha * v.q[t];
-                v.r[t] = rn;
-                vrr += rn * rn;
-                continue;
+        const size_t S = (size_t)G * nthreads;
+        constexpr int kB = (kPointwise || kFuse) ? 1 : 2;   // entries per thread loaded together
+        for (size_t t0 = (size_t)blockIdx.x * nthreads + tid; t0 < len; t0 += kB * S) {
+            double xv[kB], pv[kB], rv[kB], qv[kB], rsv[kB], qsv[kB];
+#pragma unroll
+            for (int k = 0; k < kB; ++k) {
+                const size_t t = t0 + k * S;
+                if (t < len) {
+                    xv[k] = v.x[t];
+                    pv[k] = pcur[t];
+                    rv[k] = v.r[t];
+                    qv[k] = v.q[t];
+                    if (!kElide) {
+                        rsv[k] = v.rs[t];
+                        qsv[k] = v.qs[t];
+                    }
+                }
             }
-            const double rv = v.r[t], qv = v.q[t], rsv = v.rs[t], qsv = v.qs[t];
-            const double rn = rv - alpha * qv;
-            v.r[t] = rn;
-            if (__double_as_longlong(rsv) == __double_as_longlong(rv) &&
-                __double_as_longlong(qsv) == __double_as_longlong(qv)) {
-                v.rs[t] = rn;
-                if (twin) {
+#pragma unroll
+            for (int k = 0; k < kB; ++k) {
+                const size_t t = t0 + k * S;
+                if (t >= len) break;
+                v.x[t] = xv[k] + alpha * pv[k];
+                const double rn = rv[k] - alpha * qv[k];
+                v.r[t] = rn;
+                if (kElide) {
                     vrr += rn * rn;
+                    continue;
+                }
+                if (__double_as_longlong(rsv[k]) == __double_as_longlong(rv[k]) &&
+                    __double_as_longlong(qsv[k]) == __double_as_longlong(qv[k])) {
+                    v.rs[t] = rn;
+                    if (twin) {
+                        vrr += rn * rn;
+                    } else {
+                        vr += rn * rn;
+                        vrr += rn * rn;
+                    }
                 } else {
-                    vr += rn * rn;
+                    if (twin) {
+                        vr = vrr;
+                        twin = false;
+                    }
+                    const double rsn = rsv[k] - alpha * qsv[k];
+                    v.rs[t] = rsn;
+                    vr += rsn * rn;
                     vrr += rn * rn;
                 }
-            } else {
-                if (twin) {
-                    vr = vrr;
-                    twin = false;
-                }
-                const double rsn = rsv - alpha * qsv;
-                v.rs[t] = rsn;
-                vr += rsn * rn;
-                vrr += rn * rn;
             }
         }
         if (twin) vr = vrr;
@@ -406,9 +434,27 @@ bicg_persistent_kernel(BicgVectors v, size_t len, int n, int sigma, int gx, int 
         if (kPointwise || !kFuse) {
             // phase C: p = r + beta p; p* = r* + beta p* (the fused schedule
             // does this in the next operator phase)
-            for (size_t t = (size_t)blockIdx.x * nthreads + tid; t < len; t += (size_t)G * nthreads) {
-                v.p[t] = v.r[t] + beta * v.p[t];
-                if (!kElide) v.ps[t] = v.rs[t] + beta * v.ps[t];
+            for (size_t t0 = (size_t)blockIdx.x * nthreads + tid; t0 < len; t0 += kB * S) {
+                double rv[kB], pv[kB], rsv[kB], psv[kB];
+#pragma unroll
+                for (int k = 0; k < kB; ++k) {
+                    const size_t t = t0 + k * S;
+                    if (t < len) {
+                        rv[k] = v.r[t];
+                        pv[k] = v.p[t];
+                        if (!kElide) {
+                            rsv[k] = v.rs[t];
+                            psv[k] = v.ps[t];
+                        }
+                    }
+                }
+#pragma unroll
+                for (int k = 0; k < kB; ++k) {
+                    const size_t t = t0 + k * S;
+                    if (t >= len) break;
+                    v.p[t] = rv[k] + beta * pv[k];
+                    if (!kElide) v.ps[t] = rsv[k] + beta * psv[k];
+                }
             }
             if (!(ok = grid_sync(gb, G))) break;
         }
@@ -607,11 +653,18 @@ constexpr int kPointwiseMaxN = 40;   // per-node operator on grids up to 40^3
 // operator phase with the direction update fused in
 size_t persistent_stage_bytes() { return fx_stage_bytes<4, fx_stages(true)>(); }
 
+// dynamic shared memory of a cooperative launch: none for the per-node
+// operator, the copy stages and tiles of pp_march for the plain z-march
+size_t persistent_smem(bool pointwise, bool fuse) {
+    if (pointwise) return 0;
+    return fuse ? persistent_stage_bytes() : pp_smem_bytes<2>();
+}
+
 int persistent_grid(int n, bool fuse, int* gx, int* gy, int* slabs, int* kz_per) {
     // at most two CTAs per SM; the elided variants run on the grids of the
     // full ones (same partial sums)
     const int occ_pt = min(2, resident_per_sm(bicg_persistent_kernel<true, false, false>, FX_NT));
-    const int occ_mz = min(2, resident_per_sm(bicg_persistent_kernel<false, false, false>, FX_NT));
+    const int occ_mz = min(2, resident_per_sm(bicg_persistent_kernel<false, false, false>, FX_NT, pp_smem_bytes<2>()));
     const int occ_fz = min(2, resident_per_sm(bicg_persistent_kernel<false, false, true>, FX_NT,
                                               persistent_stage_bytes()));
     const int sms = device_sms();
@@ -661,10 +714,13 @@ cudaError_t launch_bicg_persistent(double* x, double* r, double* rs, double* p, 
         }
     }
     else
+    {
+        opt_in_smem(bicg_persistent_kernel<false, true, false>, pp_smem_bytes<2>());
+        opt_in_smem(bicg_persistent_kernel<false, false, false>, pp_smem_bytes<2>());
         fn = elide ? (const void*)bicg_persistent_kernel<false, true, false>
                    : (const void*)bicg_persistent_kernel<false, false, false>;
-    return cudaLaunchCooperativeKernel(fn, dim3(G), dim3(FX_TX, FX_TY, 1), args, fuse ? persistent_stage_bytes() : 0,
-                                       s);
+    }
+    return cudaLaunchCooperativeKernel(fn, dim3(G), dim3(FX_TX, FX_TY, 1), args, persistent_smem(pw, fuse), s);
 }
 
 cudaError_t launch_bicg_stencil_pair_dir(const double* r, const double* rs, const double* p_prev,
