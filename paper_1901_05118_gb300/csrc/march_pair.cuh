@@ -88,6 +88,14 @@ __device__ __forceinline__ long long lds_s64(unsigned a) {
     asm volatile("ld.shared.s64 %0, [%1];" : "=l"(v) : "r"(a) : "memory");
     return v;
 }
+// ld.shared.s64 at a + OFF (OFF a non-negative constant folded into the
+// instruction's immediate offset)
+template <int OFF>
+__device__ __forceinline__ long long lds_s64_at(unsigned a) {
+    long long v;
+    asm volatile("ld.shared.s64 %0, [%1+%2];" : "=l"(v) : "r"(a), "n"(OFF));
+    return v;
+}
 __device__ __forceinline__ void sts_s64(unsigned a, long long v) {
     asm volatile("st.shared.s64 [%0], %1;" ::"r"(a), "l"(v) : "memory");
 }
@@ -180,8 +188,9 @@ __device__ __forceinline__ bool pp_march(const double* __restrict__ p, const dou
     const int cx = (i == 1) + (i == n - 1);
     const int c0 = cx + (ja == 1) + (ja == n - 1);
     const int c1 = cx + (ja + 1 == 1) + (ja + 1 == n - 1);
-    // byte offset in a tile of this thread's first output (row ry, column rx)
-    const unsigned tc = 8u * (unsigned)((2 * ty + 2) * PP_HX + tx + 2);
+    // byte offset in a tile of the top-left corner (row ry - 2, column
+    // rx - 2) of this thread's 5 x 6 stencil window
+    const unsigned tc = 8u * (unsigned)((2 * ty) * PP_HX + tx);
     const int T = kz1 - kz0 + 4;   // input planes kz0 - 2 .. kz1 + 1
 
     // copy plane t (all of this thread's slots) into its stage; nodes
@@ -274,16 +283,17 @@ __device__ __forceinline__ bool pp_march(const double* __restrict__ p, const dou
         const int zin = kz0 - 2 + t;
         const int cz = (zin == 1) + (zin == n - 1);
         const unsigned b0 = tl + tc;
-        auto at = [&](int dy, int dx) { return lds_s64(b0 + 8u * (unsigned)(dy * PP_HX + dx)); };
-        const long long cm2 = at(-2, 0), cm1 = at(-1, 0), cc0 = at(0, 0), cc1 = at(1, 0), cc2 = at(2, 0),
-                        cc3 = at(3, 0);
+#define PP_AT(dy, dx) lds_s64_at<8 * (((dy) + 2) * PP_HX + (dx) + 2)>(b0)
+        const long long cm2 = PP_AT(-2, 0), cm1 = PP_AT(-1, 0), cc0 = PP_AT(0, 0), cc1 = PP_AT(1, 0),
+                        cc2 = PP_AT(2, 0), cc3 = PP_AT(3, 0);
         // x-neighbour sums at distance 1 (rows -1 .. 2) and 2 (rows 0, 1)
-        const long long h1m = at(-1, -1) + at(-1, 1);
-        const long long h10 = at(0, -1) + at(0, 1);
-        const long long h11 = at(1, -1) + at(1, 1);
-        const long long h12 = at(2, -1) + at(2, 1);
-        const long long h20 = at(0, -2) + at(0, 2);
-        const long long h21 = at(1, -2) + at(1, 2);
+        const long long h1m = PP_AT(-1, -1) + PP_AT(-1, 1);
+        const long long h10 = PP_AT(0, -1) + PP_AT(0, 1);
+        const long long h11 = PP_AT(1, -1) + PP_AT(1, 1);
+        const long long h12 = PP_AT(2, -1) + PP_AT(2, 1);
+        const long long h20 = PP_AT(0, -2) + PP_AT(0, 2);
+        const long long h21 = PP_AT(1, -2) + PP_AT(1, 2);
+#undef PP_AT
         long long P0[2], P1[2], C[2];
         {   // output row ja: same plane (42 + sigma c) u - 12 (4 axis) + (4 at 2) + 2 (4 diagonals);
             // planes +-1: 2 (4 axis) - 12 u; planes +-2: u
