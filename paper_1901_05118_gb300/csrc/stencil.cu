@@ -155,8 +155,12 @@ __device__ __noinline__ double pair_two_field(const double* p, const double* ps,
     return fx_march<2, true>(fl, nullptr, n, sigma, bx, by, kz0, kz1);
 }
 
+// Launch bounds: the two-field kernel at two CTAs per SM (up to 128
+// registers: measured 1.27 ms against 1.41 ms per 512^3 launch at three CTAs
+// and 80 registers, where the compiler recomputes values it cannot keep),
+// the elided one at three (1.02 against 1.06 ms).
 template <bool kElide>
-__global__ void __launch_bounds__(PP_NT, 3)
+__global__ void __launch_bounds__(PP_NT, kElide ? 3 : 2)
 stencil_pair_kernel(const double* __restrict__ p, const double* __restrict__ ps, double* __restrict__ q,
                     double* __restrict__ qs, int n, int sigma, int kz_per_cta, double* partials, BicgState* st) {
     extern __shared__ __align__(128) unsigned char pp_smem[];
