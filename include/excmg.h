@@ -151,6 +151,15 @@ int excmg_ctx_set_shadow_mode(excmg_ctx *ctx, int mode);
  *   more than the saved pass. */
 enum { EXCMG_SCHEDULE_SEPARATE = 0, EXCMG_SCHEDULE_FUSED = 1 };
 int excmg_ctx_set_schedule(excmg_ctx *ctx, int schedule);
+
+/* CUDA graphs (default on): on grids solved by launched kernels (above
+ * 64^3), every full batch of Bi-CG iterations after the first -- the same
+ * sequence of launches each time, all of them reading their scalars and
+ * their stop flag from the device -- is captured once into a CUDA graph (on
+ * a private stream of the context) and replayed, cached per grid size,
+ * variant and buffer set.  Results are the same bits with graphs on or off.
+ * Graphs are not used while operator timing (excmg_ctx_profile) is on. */
+int excmg_ctx_set_graphs(excmg_ctx *ctx, int enable);
 const char *excmg_last_error(const excmg_ctx *ctx);
 
 /* Instrumentation.  excmg_launch_count: kernel launches the library has

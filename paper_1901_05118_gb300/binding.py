@@ -72,6 +72,7 @@ _lib.excmg_ctx_bytes.restype = _sz
 _lib.excmg_ctx_set_stencil.argtypes = [_vp, _i]
 _lib.excmg_ctx_set_shadow_mode.argtypes = [_vp, _i]
 _lib.excmg_ctx_set_schedule.argtypes = [_vp, _i]
+_lib.excmg_ctx_set_graphs.argtypes = [_vp, _i]
 _lib.excmg_launch_count.argtypes = []
 _lib.excmg_launch_count.restype = ctypes.c_longlong
 _lib.excmg_ctx_profile.argtypes = [_vp, _i]
@@ -117,7 +118,7 @@ for _name in ("excmg_batch_create", "excmg_batch_destroy", "excmg_batch_submit",
     getattr(_lib, _name).restype = _i
 
 for _name in ("excmg_ctx_create", "excmg_ctx_destroy", "excmg_ctx_set_stencil", "excmg_ctx_set_shadow_mode",
-              "excmg_ctx_set_schedule", "excmg_ctx_profile",
+              "excmg_ctx_set_schedule", "excmg_ctx_set_graphs", "excmg_ctx_profile",
               "excmg_ctx_profile_read", "excmg_level_create", "excmg_level_destroy",
               "stencil_apply", "bicg_solve", "bicg_solve_ex", "extrapolate_interpolate", "extrapolate_interpolate_ex",
               "midpoint_extrapolate", "midpoint_extrapolate_ex", "excmg_solve", "excmg_solve_ex",
@@ -199,6 +200,11 @@ class Context:
         'fused' (direction update folded into the operator launch, staged
         input rows; measured slower on GB300)."""
         self.check(_lib.excmg_ctx_set_schedule(self.handle, SCHEDULES[schedule]), "excmg_ctx_set_schedule")
+
+    def set_graphs(self, enable: bool):
+        """Replay full batches of launched Bi-CG iterations from CUDA graphs
+        (default on; the same bits either way)."""
+        self.check(_lib.excmg_ctx_set_graphs(self.handle, int(bool(enable))), "excmg_ctx_set_graphs")
 
     def profile(self, enable: bool = True):
         """Time every operator launch inside Bi-CG (CUDA events on this context's stream)."""

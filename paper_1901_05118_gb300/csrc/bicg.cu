@@ -168,47 +168,95 @@ int bicg_run(excmg_ctx* ctx, int n, int bc_kind, const double* b, double* x, dou
             }
         }
         launch_bytes.assign(batch, 0.0);
-        for (int it = 0; it < batch && e == cudaSuccess; ++it) {
-            if (ctx->profile) cudaEventRecord(ctx->prof_events[3 * it], s);
-            if (fused) {
-                // A p_k and A^T p*_k in one z-march, sigma_k and alpha_k fused;
-                // from the second iteration on the launch first forms
-                // p_k = r_k + beta_{k-1} p_{k-1} (and p*_k) on the fly
-                if (enqueued == 0 || !dir_fused) {
-                    e = elide ? launch_cg_stencil(pc, q, n, bc_kind, ctx->partials, ctx->state, s, dir_fused)
-                              : launch_bicg_stencil_pair(pc, q, psc, qs, n, bc_kind, ctx->partials, ctx->state, s,
-                                                         dir_fused);
-                    // p (, p*) in; q (, q*) out
-                    launch_bytes[it] = (elide ? 16.0 : 32.0) * unknowns;
+        // the iterations of one batch, enqueued on stream `ss`
+        auto enqueue = [&](cudaStream_t ss) -> cudaError_t {
+            cudaError_t ee = cudaSuccess;
+            for (int it = 0; it < batch && ee == cudaSuccess; ++it) {
+                if (ctx->profile) cudaEventRecord(ctx->prof_events[3 * it], ss);
+                if (fused) {
+                    // A p_k and A^T p*_k in one z-march, sigma_k and alpha_k fused;
+                    // from the second iteration on the launch first forms
+                    // p_k = r_k + beta_{k-1} p_{k-1} (and p*_k) on the fly
+                    if (enqueued == 0 || !dir_fused) {
+                        ee = elide ? launch_cg_stencil(pc, q, n, bc_kind, ctx->partials, ctx->state, ss, dir_fused)
+                                   : launch_bicg_stencil_pair(pc, q, psc, qs, n, bc_kind, ctx->partials, ctx->state,
+                                                              ss, dir_fused);
+                        // p (, p*) in; q (, q*) out
+                        launch_bytes[it] = (elide ? 16.0 : 32.0) * unknowns;
+                    } else {
+                        ee = elide ? launch_cg_stencil_dir(r, pc, pn, q, n, bc_kind, ctx->partials, ctx->state, ss)
+                                   : launch_bicg_stencil_pair_dir(r, rs, pc, psc, pn, psn, q, qs, n, bc_kind,
+                                                                  ctx->partials, ctx->state, ss);
+                        std::swap(pc, pn);
+                        std::swap(psc, psn);
+                        // r (, r*), p_old (, p*_old) in; p (, p*), q (, q*) out
+                        launch_bytes[it] = (elide ? 32.0 : 64.0) * unknowns;
+                    }
+                    if (ctx->profile) {
+                        cudaEventRecord(ctx->prof_events[3 * it + 1], ss);
+                        cudaEventRecord(ctx->prof_events[3 * it + 2], ss);
+                    }
                 } else {
-                    e = elide ? launch_cg_stencil_dir(r, pc, pn, q, n, bc_kind, ctx->partials, ctx->state, s)
-                              : launch_bicg_stencil_pair_dir(r, rs, pc, psc, pn, psn, q, qs, n, bc_kind,
-                                                             ctx->partials, ctx->state, s);
-                    std::swap(pc, pn);
-                    std::swap(psc, psn);
-                    // r (, r*), p_old (, p*_old) in; p (, p*), q (, q*) out
-                    launch_bytes[it] = (elide ? 32.0 : 64.0) * unknowns;
+                    launch_bytes[it] = 32.0 * unknowns;       // two launches of u in, y out
+                    ee = launch_stencil(p, q, nullptr, n, bc_kind, false, done, ss, ctx->stencil_variant);  // A p_k
+                    if (ctx->profile) cudaEventRecord(ctx->prof_events[3 * it + 1], ss);
+                    if (ee == cudaSuccess)
+                        ee = launch_stencil(ps, qs, nullptr, n, bc_kind, true, done, ss,
+                                            ctx->stencil_variant);  // A^T p*_k
+                    if (ctx->profile) cudaEventRecord(ctx->prof_events[3 * it + 2], ss);
+                    if (ee == cudaSuccess) ee = launch_bicg_sigma(ps, q, len, ctx->partials, ctx->state, ss);
                 }
-                if (ctx->profile) {
-                    cudaEventRecord(ctx->prof_events[3 * it + 1], s);
-                    cudaEventRecord(ctx->prof_events[3 * it + 2], s);
-                }
-            } else {
-                launch_bytes[it] = 32.0 * unknowns;       // two launches of u in, y out
-                e = launch_stencil(p, q, nullptr, n, bc_kind, false, done, s, ctx->stencil_variant);  // A p_k
-                if (ctx->profile) cudaEventRecord(ctx->prof_events[3 * it + 1], s);
-                if (e == cudaSuccess)
-                    e = launch_stencil(ps, qs, nullptr, n, bc_kind, true, done, s, ctx->stencil_variant);  // A^T p*_k
-                if (ctx->profile) cudaEventRecord(ctx->prof_events[3 * it + 2], s);
-                if (e == cudaSuccess) e = launch_bicg_sigma(ps, q, len, ctx->partials, ctx->state, s);
+                if (ee == cudaSuccess)
+                    ee = elide ? launch_cg_update(x, pc, r, q, len, ctx->partials, ctx->state, ss)
+                               : launch_bicg_update(x, pc, r, q, rs, qs, len, ctx->partials, ctx->state, ss);
+                if (ee == cudaSuccess && !dir_fused)
+                    ee = elide ? launch_cg_pupdate(p, r, len, ctx->state, ss)
+                               : launch_bicg_pupdate(p, r, ps, rs, len, ctx->state, ss);
+                ++enqueued;
             }
-            if (e == cudaSuccess)
-                e = elide ? launch_cg_update(x, pc, r, q, len, ctx->partials, ctx->state, s)
-                          : launch_bicg_update(x, pc, r, q, rs, qs, len, ctx->partials, ctx->state, s);
-            if (e == cudaSuccess && !dir_fused)
-                e = elide ? launch_cg_pupdate(p, r, len, ctx->state, s)
-                          : launch_bicg_pupdate(p, r, ps, rs, len, ctx->state, s);
-            ++enqueued;
+            return ee;
+        };
+        // From the second batch on, a full batch is the same sequence of
+        // launches every time (every kernel takes its scalars and its stop
+        // flag from the device state, and the fused schedule's buffer pairs
+        // come back after an even number of iterations): it is captured once
+        // into a CUDA graph and replayed.
+        const bool graph = ctx->graphs && !ctx->profile && enqueued >= check_every && batch == check_every &&
+                           (check_every % 2 == 0 || !dir_fused);
+        if (graph) {
+            const std::vector<uintptr_t> key{(uintptr_t)n, (uintptr_t)bc_kind, (uintptr_t)elide, (uintptr_t)fused,
+                                             (uintptr_t)dir_fused, (uintptr_t)ctx->stencil_variant,
+                                             (uintptr_t)batch, (uintptr_t)x, (uintptr_t)r, (uintptr_t)rs,
+                                             (uintptr_t)pc, (uintptr_t)psc, (uintptr_t)pn, (uintptr_t)psn,
+                                             (uintptr_t)q, (uintptr_t)qs};
+            cudaGraphExec_t exec = ctx_chunk_graph(ctx, key);
+            if (!exec) {
+                cudaStream_t cs = ctx_capture_stream(ctx);
+                if (!cs) return ctx_cuda(ctx, cudaGetLastError(), "capture stream");
+                cudaGraph_t g = nullptr;
+                const long long enq0 = enqueued;
+                double* const saved[4] = {pc, psc, pn, psn};
+                e = cudaStreamBeginCapture(cs, cudaStreamCaptureModeThreadLocal);
+                if (e == cudaSuccess) {
+                    const cudaError_t ee = enqueue(cs);
+                    e = cudaStreamEndCapture(cs, &g);
+                    if (e == cudaSuccess) e = ee;
+                }
+                if (e == cudaSuccess) e = cudaGraphInstantiate(&exec, g, 0);
+                if (g) cudaGraphDestroy(g);
+                if (e != cudaSuccess) return ctx_cuda(ctx, e, "Bi-CG graph capture");
+                ctx_store_chunk_graph(ctx, key, exec);
+                // the capture ran nothing: undo its bookkeeping
+                enqueued = enq0;
+                pc = saved[0];
+                psc = saved[1];
+                pn = saved[2];
+                psn = saved[3];
+            }
+            e = cudaGraphLaunch(exec, s);
+            enqueued += batch;   // an even batch leaves the direction pairs where they were
+        } else {
+            e = enqueue(s);
         }
         note_launches((dir_fused ? 2LL : (fused ? 3LL : 5LL)) * batch);
         if (e != cudaSuccess) return ctx_cuda(ctx, e, "Bi-CG iteration");

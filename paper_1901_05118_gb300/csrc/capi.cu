@@ -79,6 +79,26 @@ int ctx_cuda(excmg_ctx* ctx, cudaError_t err, const char* what) {
     return ctx_fail(ctx, EXCMG_ERR_CUDA, std::string(what) + ": " + cudaGetErrorString(err));
 }
 
+cudaGraphExec_t ctx_chunk_graph(excmg_ctx* ctx, const std::vector<uintptr_t>& key) {
+    auto it = ctx->chunk_graphs.find(key);
+    return it == ctx->chunk_graphs.end() ? nullptr : it->second;
+}
+
+void ctx_store_chunk_graph(excmg_ctx* ctx, const std::vector<uintptr_t>& key, cudaGraphExec_t exec) {
+    if (ctx->chunk_graphs.size() >= 64) {   // bounded: drop the old ones (buffers may have moved)
+        cudaStreamSynchronize(ctx->stream);
+        for (auto& kv : ctx->chunk_graphs) cudaGraphExecDestroy(kv.second);
+        ctx->chunk_graphs.clear();
+    }
+    ctx->chunk_graphs[key] = exec;
+}
+
+cudaStream_t ctx_capture_stream(excmg_ctx* ctx) {
+    if (!ctx->capture_stream && cudaStreamCreateWithFlags(&ctx->capture_stream, cudaStreamNonBlocking) != cudaSuccess)
+        ctx->capture_stream = nullptr;
+    return ctx->capture_stream;
+}
+
 // A named workspace buffer of at least `bytes`, grown on demand.
 double* ctx_buffer(excmg_ctx* ctx, const char* name, size_t bytes, int* status) {
     excmg_buffer& b = ctx->buffers[name];
@@ -182,6 +202,8 @@ int excmg_ctx_destroy(excmg_ctx* c) {
     if (c->host_state) cudaFreeHost(c->host_state);
     if (c->host_scalar) cudaFreeHost(c->host_scalar);
     for (cudaEvent_t e : c->prof_events) cudaEventDestroy(e);
+    for (auto& kv : c->chunk_graphs) cudaGraphExecDestroy(kv.second);
+    if (c->capture_stream) cudaStreamDestroy(c->capture_stream);
     delete c;
     return EXCMG_OK;
 }
@@ -212,6 +234,13 @@ int excmg_ctx_set_schedule(excmg_ctx* c, int schedule) {
     if (schedule != EXCMG_SCHEDULE_SEPARATE && schedule != EXCMG_SCHEDULE_FUSED)
         return ctx_fail(c, EXCMG_ERR_ARG, "unknown operator schedule");
     c->schedule = schedule;
+    return EXCMG_OK;
+}
+
+int excmg_ctx_set_graphs(excmg_ctx* c, int enable) {
+    if (!c) c = default_ctx();
+    if (!c) return EXCMG_ERR_CUDA;
+    c->graphs = enable != 0;
     return EXCMG_OK;
 }
 

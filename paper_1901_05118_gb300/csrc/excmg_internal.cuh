@@ -167,6 +167,11 @@ struct excmg_ctx {
     int stencil_variant = excmg::kStencilExact;
     int shadow_mode = EXCMG_SHADOW_FULL;
     int schedule = EXCMG_SCHEDULE_SEPARATE;
+    // CUDA graphs of full batches of launched Bi-CG iterations, keyed by the
+    // grid size, the variant flags and the buffers they use (bicg.cu)
+    bool graphs = true;
+    cudaStream_t capture_stream = nullptr;
+    std::map<std::vector<uintptr_t>, cudaGraphExec_t> chunk_graphs;
     // optional timing of the operator launches inside Bi-CG
     bool profile = false;
     std::vector<cudaEvent_t> prof_events;
@@ -191,6 +196,11 @@ int device_sms();
 // threads, smem) under a lock: function attributes and occupancy belong to
 // each device's context.
 int kernel_occupancy(const void* kernel, int threads, size_t smem);
+// Cached CUDA graph of a batch of Bi-CG iterations (null if none), storing
+// one, and the context's private capture stream (capi.cu).
+cudaGraphExec_t ctx_chunk_graph(excmg_ctx* ctx, const std::vector<uintptr_t>& key);
+void ctx_store_chunk_graph(excmg_ctx* ctx, const std::vector<uintptr_t>& key, cudaGraphExec_t exec);
+cudaStream_t ctx_capture_stream(excmg_ctx* ctx);
 // Workspace helpers (capi.cu).
 int ctx_fail(excmg_ctx* ctx, int status, const std::string& msg);
 int ctx_cuda(excmg_ctx* ctx, cudaError_t err, const char* what);

@@ -55,3 +55,25 @@ def test_elided_solve_is_bit_identical(n, bc_kind):
     (uf, sf), (ue, se) = res["full"], res["elided"]
     assert [s["iters"] for s in sf] == [s["iters"] for s in se]
     assert torch.equal(uf, ue)
+
+
+@pytest.mark.parametrize("schedule", ["separate", "fused"])
+@pytest.mark.parametrize("mode", ["full", "elided"])
+def test_graph_replay_is_bit_identical(schedule, mode):
+    """Batches of launched Bi-CG iterations replayed from CUDA graphs give the
+    same bits as the same launches made directly (80 iterations: the first
+    batch of 16 launched directly, the next four replayed from the graph)."""
+    n = 136
+    b = torch.from_numpy(P.random_field(n, 93)).to(DEV)
+    x0 = torch.from_numpy(P.random_field(n, 94) * 0.1).to(DEV)
+    out = {}
+    for graphs in (False, True):
+        c = ctx(mode, schedule)
+        c.set_graphs(graphs)
+        lvl = B.Level(n, 1, c)
+        x = x0.clone()
+        it, rel, rc = B.bicg_solve(lvl, b, x, 0.0, 80)
+        assert it == 80
+        out[graphs] = (x, rel)
+    assert out[True][1] == out[False][1]
+    assert torch.equal(out[True][0], out[False][0])
