@@ -19,6 +19,8 @@
 #include <chrono>
 #include <cmath>
 #include <cstring>
+#include <map>
+#include <thread>
 #include <vector>
 
 #include "excmg_internal.cuh"
@@ -97,7 +99,7 @@ __global__ void __launch_bounds__(S_NT)
 batch_bicg_kernel(const BatchInst<T>* __restrict__ inst, const int* __restrict__ unit_begin,
                     const int* __restrict__ chunk_begin, int ninst, int total_units, int total_chunks,
                     double* unit_part, double* chunk_part, BatchState* states, int iters, int* active,
-                    GridBarrier gb) {
+                    GridBarrier gb, int* rounds) {
     __shared__ double sh[32];
     __shared__ T shf[32];
     __shared__ bool flag;
@@ -105,7 +107,9 @@ batch_bicg_kernel(const BatchInst<T>* __restrict__ inst, const int* __restrict__
     const int tid = threadIdx.x + blockDim.x * threadIdx.y;
     const int nt = blockDim.x * blockDim.y;
     bool ok = true;
+    int rounds_done = 0;
     for (int it = 0; it < iters && ok; ++it) {
+        ++rounds_done;
         // phase A: q = A p, q* = A p*, per-tile (p*, q); the CTA finishing an
         // instance's last tile forms sigma and alpha
         for (int u = blockIdx.x; u < total_units; u += G) {
@@ -203,7 +207,10 @@ batch_bicg_kernel(const BatchInst<T>* __restrict__ inst, const int* __restrict__
         }
         if (!(ok = grid_sync(gb, G))) break;
     }
-    if (!ok && blockIdx.x == 0 && thread0()) *active = -1;   // barrier gave up
+    if (blockIdx.x == 0 && thread0()) {
+        if (!ok) *active = -1;   // barrier gave up
+        *rounds = rounds_done;
+    }
 }
 
 // r32 = r / s, e = 0, r*_0 = p_0 = p*_0 = r_0 and rho_0 = (r_0, r_0) of one
@@ -288,6 +295,10 @@ struct Instance {
     // FP32 correction solve vectors
     float *r32 = nullptr, *e = nullptr, *r = nullptr, *rs = nullptr, *p = nullptr, *ps = nullptr, *q = nullptr,
           *qs = nullptr;
+    // device state slot (fixed for the instance's life) and whether a group
+    // launch holding it is running
+    int slot = -1;
+    bool in_flight = false;
     // progress
     Phase phase = kSetup;
     int level = 0;
@@ -343,6 +354,31 @@ struct excmg_batch {
     int inner_chunk = 256;       // iterations per batched launch
     std::string last_error;
     long long launches = 0;
+    std::vector<int> free_slots;
+    // One cooperative launch per level group (instances of one precision at
+    // one grid size), each on its own stream with its own tables, partial
+    // sums, barrier and counters, harvested as soon as it completes.
+    struct Group {
+        cudaStream_t stream = nullptr;
+        cudaEvent_t start = nullptr, done = nullptr;
+        bool busy = false;
+        int prec = 0, n = 0, ctas = 0, cand = -1;
+        std::vector<Instance*> members;
+        void* d_inst = nullptr;        // BatchInst<T>[max_instances]
+        int *d_unit_begin = nullptr, *d_chunk_begin = nullptr, *d_active = nullptr, *d_rounds = nullptr;
+        int *h_active = nullptr, *h_rounds = nullptr;
+        unsigned int* d_barrier = nullptr;
+        double *d_unit_part = nullptr, *d_chunk_part = nullptr;
+        size_t unit_cap = 0, chunk_cap = 0;
+    };
+    std::vector<Group> groups;
+    cudaEvent_t host_ready = nullptr;   // the context stream's state uploads
+    // Grid-size tuner: per (precision, grid size) the CTA-milliseconds per
+    // instance iteration measured for each candidate number of CTAs per
+    // instance; the cheapest is used once every candidate has been tried.
+    // The grid size changes no result bit (every partial sum belongs to a
+    // tile or chunk, not to a CTA).
+    std::map<std::pair<int, int>, std::vector<double>> tune;
 };
 
 namespace {
@@ -363,11 +399,7 @@ int bcuda(excmg_batch* b, cudaError_t e, const char* what) {
     return bfail(b, EXCMG_ERR_CUDA, std::string(what) + ": " + cudaGetErrorString(e));
 }
 
-int slot_of(excmg_batch* b, Instance* in) {
-    for (size_t k = 0; k < b->live.size(); ++k)
-        if (b->live[k] == in) return (int)k;
-    return -1;
-}
+int slot_of(excmg_batch* /*b*/, Instance* in) { return in->slot; }
 
 void free_instance(excmg_batch* b, Instance* in) {
     if (in->block) {
@@ -476,19 +508,64 @@ BatchInst<T> geometry(Instance* in, int slot, int* units, int* chunks) {
     return t;
 }
 
-// One cooperative launch of up to `iters` Bi-CG iterations for the listed
-// instances of one value type.
+// ------------------------------------------------------------ level groups
+constexpr int kTuneCands = 6;
+constexpr int kTuneCta[kTuneCands] = {1, 2, 4, 8, 16, 32};   // CTAs per instance
+
+int capacity_of(int prec) {
+    return prec == EXCMG_PRECISION_FP64 ? batch_resident_ctas<double>() : batch_resident_ctas<float>();
+}
+
+// The group record's stream, events and fixed tables (made once).
+int group_init(excmg_batch* b, excmg_batch::Group& g) {
+    if (g.stream) return EXCMG_OK;
+    const size_t mi = (size_t)b->max_instances;
+    bool ok = cudaStreamCreateWithFlags(&g.stream, cudaStreamNonBlocking) == cudaSuccess &&
+              cudaEventCreate(&g.start) == cudaSuccess && cudaEventCreate(&g.done) == cudaSuccess &&
+              cudaMalloc(&g.d_inst, mi * sizeof(BatchInst<double>)) == cudaSuccess &&
+              cudaMalloc(&g.d_unit_begin, mi * sizeof(int)) == cudaSuccess &&
+              cudaMalloc(&g.d_chunk_begin, mi * sizeof(int)) == cudaSuccess &&
+              cudaMalloc(&g.d_active, sizeof(int)) == cudaSuccess &&
+              cudaMalloc(&g.d_rounds, sizeof(int)) == cudaSuccess &&
+              cudaMallocHost(&g.h_active, 2 * sizeof(int)) == cudaSuccess &&
+              cudaMalloc(&g.d_barrier, 4 * sizeof(unsigned int)) == cudaSuccess;
+    if (!ok) {
+        cudaGetLastError();
+        return bfail(b, EXCMG_ERR_OOM, "batch group buffers");
+    }
+    g.h_rounds = g.h_active + 1;
+    return EXCMG_OK;
+}
+
+void group_free(excmg_batch::Group& g) {
+    if (g.stream) cudaStreamSynchronize(g.stream);
+    cudaFree(g.d_inst);
+    cudaFree(g.d_unit_begin);
+    cudaFree(g.d_chunk_begin);
+    cudaFree(g.d_active);
+    cudaFree(g.d_rounds);
+    cudaFreeHost(g.h_active);
+    cudaFree(g.d_barrier);
+    cudaFree(g.d_unit_part);
+    cudaFree(g.d_chunk_part);
+    if (g.start) cudaEventDestroy(g.start);
+    if (g.done) cudaEventDestroy(g.done);
+    if (g.stream) cudaStreamDestroy(g.stream);
+    g = excmg_batch::Group{};
+}
+
+// One cooperative launch of up to b->inner_chunk Bi-CG iterations for the
+// instances `list` (one precision, one grid size) on group record g, with
+// `ctas` CTAs, after the context stream's state uploads.
 template <typename T>
-int run_batched(excmg_batch* b, const std::vector<Instance*>& list, BatchInst<T>* d_inst) {
-    excmg_ctx* ctx = b->ctx;
-    cudaStream_t s = ctx->stream;
+int launch_group(excmg_batch* b, excmg_batch::Group& g, const std::vector<Instance*>& list, int ctas, int cand) {
+    int st = group_init(b, g);
+    if (st) return st;
     std::vector<BatchInst<T>> tab;
     std::vector<int> ub, cb;
-    int units = 0, chunks = 0, active = 0;
+    int units = 0, chunks = 0;
     for (Instance* in : list) {
-        const int slot = slot_of(b, in);
-        if (b->h_states[slot].done) continue;
-        BatchInst<T> t = geometry<T>(in, slot, &units, &chunks);
+        BatchInst<T> t = geometry<T>(in, in->slot, &units, &chunks);
         if (sizeof(T) == sizeof(double)) {
             t.x = (T*)in->u[in->level];
             t.r = (T*)in->res;
@@ -509,40 +586,124 @@ int run_batched(excmg_batch* b, const std::vector<Instance*>& list, BatchInst<T>
         ub.push_back(t.unit_begin);
         cb.push_back(t.chunk_begin);
         tab.push_back(t);
-        ++active;
     }
-    if (active == 0) return EXCMG_OK;
-    if (!grow(b, &b->d_unit_part, &b->unit_cap, (size_t)units) ||
-        !grow(b, &b->d_chunk_part, &b->chunk_cap, 2 * (size_t)chunks))
+    // the tables are pageable host vectors: each cudaMemcpyAsync below has
+    // staged them by the time it returns
+    if (!grow(b, &g.d_unit_part, &g.unit_cap, (size_t)units) ||
+        !grow(b, &g.d_chunk_part, &g.chunk_cap, 2 * (size_t)chunks))
         return bfail(b, EXCMG_ERR_OOM, "batch partials");
-    const int ninst = (int)tab.size();
-    *b->h_active = active;
-    cudaError_t e = cudaMemcpyAsync(d_inst, tab.data(), tab.size() * sizeof(BatchInst<T>), cudaMemcpyHostToDevice, s);
-    if (e == cudaSuccess) e = cudaMemcpyAsync(b->d_unit_begin, ub.data(), ub.size() * sizeof(int), cudaMemcpyHostToDevice, s);
-    if (e == cudaSuccess) e = cudaMemcpyAsync(b->d_chunk_begin, cb.data(), cb.size() * sizeof(int), cudaMemcpyHostToDevice, s);
-    if (e == cudaSuccess) e = cudaMemcpyAsync(b->d_active, b->h_active, sizeof(int), cudaMemcpyHostToDevice, s);
-    if (e == cudaSuccess) e = cudaMemsetAsync(b->d_barrier, 0, 4 * sizeof(unsigned int), s);
+    cudaStream_t s = g.stream;
+    *g.h_active = (int)tab.size();
+    cudaError_t e = cudaStreamWaitEvent(s, b->host_ready, 0);
+    if (e == cudaSuccess)
+        e = cudaMemcpyAsync(g.d_inst, tab.data(), tab.size() * sizeof(BatchInst<T>), cudaMemcpyHostToDevice, s);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(g.d_unit_begin, ub.data(), ub.size() * sizeof(int), cudaMemcpyHostToDevice, s);
+    if (e == cudaSuccess)
+        e = cudaMemcpyAsync(g.d_chunk_begin, cb.data(), cb.size() * sizeof(int), cudaMemcpyHostToDevice, s);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(g.d_active, g.h_active, sizeof(int), cudaMemcpyHostToDevice, s);
+    if (e == cudaSuccess) e = cudaMemsetAsync(g.d_barrier, 0, 4 * sizeof(unsigned int), s);
     if (e != cudaSuccess) return bcuda(b, e, "batch table upload");
     int iters = b->inner_chunk;
-    const int G = batch_resident_ctas<T>();
-    const BatchInst<T>* di = d_inst;
-    const int* d_ub = b->d_unit_begin;
-    const int* d_cb = b->d_chunk_begin;
-    double* up = b->d_unit_part;
-    double* cp = b->d_chunk_part;
+    int ninst = (int)tab.size();
+    const BatchInst<T>* di = (const BatchInst<T>*)g.d_inst;
+    const int* d_ub = g.d_unit_begin;
+    const int* d_cb = g.d_chunk_begin;
+    double* up = g.d_unit_part;
+    double* cp = g.d_chunk_part;
     BatchState* sts = b->d_states;
-    int* act = b->d_active;
-    GridBarrier gb{b->d_barrier, b->d_barrier + 1, (int*)(b->d_barrier + 2), kBarrierSpinLimit};
-    void* args[] = {(void*)&di, (void*)&d_ub, (void*)&d_cb, (void*)&ninst, (void*)&units, (void*)&chunks,
-                    (void*)&up, (void*)&cp, (void*)&sts, (void*)&iters, (void*)&act, (void*)&gb};
-    e = cudaLaunchCooperativeKernel((const void*)batch_bicg_kernel<T>, dim3(G), dim3(S_TX, S_TY, 1), args, 0, s);
+    int* act = g.d_active;
+    int* rounds = g.d_rounds;
+    GridBarrier gb{g.d_barrier, g.d_barrier + 1, (int*)(g.d_barrier + 2), kBarrierSpinLimit};
+    void* args[] = {(void*)&di,    (void*)&d_ub,  (void*)&d_cb, (void*)&ninst, (void*)&units, (void*)&chunks,
+                    (void*)&up,    (void*)&cp,    (void*)&sts,  (void*)&iters, (void*)&act,   (void*)&gb,
+                    (void*)&rounds};
+    e = cudaEventRecord(g.start, s);
+    if (e == cudaSuccess)
+        e = cudaLaunchCooperativeKernel((const void*)batch_bicg_kernel<T>, dim3(ctas), dim3(S_TX, S_TY, 1), args, 0,
+                                        s);
     bnote(b, 1);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(g.h_active, g.d_active, sizeof(int), cudaMemcpyDeviceToHost, s);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(g.h_rounds, g.d_rounds, sizeof(int), cudaMemcpyDeviceToHost, s);
+    if (e == cudaSuccess) e = cudaEventRecord(g.done, s);
     if (e != cudaSuccess) return bcuda(b, e, "batched Bi-CG launch");
-    e = cudaMemcpyAsync(b->h_active, b->d_active, sizeof(int), cudaMemcpyDeviceToHost, s);
-    if (e == cudaSuccess) e = cudaStreamSynchronize(s);
-    if (e != cudaSuccess) return bcuda(b, e, "batched Bi-CG");
-    if (*b->h_active < 0) return bfail(b, EXCMG_ERR_TIMEOUT, "grid barrier of the batched Bi-CG gave up");
+    g.busy = true;
+    g.prec = sizeof(T) == sizeof(double) ? EXCMG_PRECISION_FP64 : EXCMG_PRECISION_MIXED;
+    g.n = list.empty() ? 0 : (list[0]->nc << list[0]->level);
+    g.ctas = ctas;
+    g.cand = cand;
+    g.members = list;
+    for (Instance* in : list) in->in_flight = true;
     return EXCMG_OK;
+}
+
+// A completed group launch: its members' states come back, the tuner learns
+// the launch's cost, and every member whose Bi-CG call ended goes back to the
+// true-residual test of Alg. 1 (mixed: after u += ||r|| e).
+int harvest(excmg_batch* b, excmg_batch::Group& g) {
+    excmg_ctx* ctx = b->ctx;
+    cudaError_t e = cudaSuccess;
+    for (Instance* in : g.members)
+        if (e == cudaSuccess)
+            e = cudaMemcpyAsync(b->h_states + in->slot, b->d_states + in->slot, sizeof(BatchState),
+                                cudaMemcpyDeviceToHost, g.stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(g.stream);
+    if (e != cudaSuccess) return bcuda(b, e, "batch state read");
+    g.busy = false;
+    for (Instance* in : g.members) in->in_flight = false;
+    if (*g.h_active < 0) return bfail(b, EXCMG_ERR_TIMEOUT, "grid barrier of the batched Bi-CG gave up");
+    if (g.cand >= 0 && *g.h_rounds > 0) {
+        float ms = 0.f;
+        if (cudaEventElapsedTime(&ms, g.start, g.done) == cudaSuccess) {
+            auto& costs = b->tune[{g.prec, g.n}];
+            if (costs.empty()) costs.assign(kTuneCands, -1.0);
+            const double c = (double)ms * g.ctas / ((double)*g.h_rounds * (double)g.members.size());
+            if (costs[g.cand] < 0.0 || c < costs[g.cand]) costs[g.cand] = c;
+        } else {
+            cudaGetLastError();
+        }
+    }
+    for (Instance* in : g.members) {
+        if (in->phase != kInner) continue;
+        const BatchState& hs = b->h_states[in->slot];
+        if (!hs.done) continue;   // the launch's iteration chunk ended first
+        if (hs.status == kBreakdown) {
+            in->phase = kFailed;
+            in->status = EXCMG_ERR_BREAKDOWN;
+            continue;
+        }
+        in->iters += hs.iter;
+        ++in->outer;
+        if (in->prec == EXCMG_PRECISION_MIXED) {
+            const int N = in->nc << in->level;
+            batch_correct_kernel<<<kVecBlocks, kVecThreads, 0, ctx->stream>>>(in->u[in->level], in->e, node_count(N),
+                                                                              in->scale);
+            bnote(b, 1);
+            if ((e = cudaGetLastError()) != cudaSuccess) return bcuda(b, e, "batch correction");
+        }
+        in->phase = kResidual;
+    }
+    g.members.clear();
+    return EXCMG_OK;
+}
+
+// CTAs for a group of m instances of grid size n: the tuner's next untried
+// candidate, else its cheapest; *cand the candidate index (-1: not tuning).
+int group_ctas(excmg_batch* b, int prec, int n, int m, int* cand) {
+    auto& costs = b->tune[{prec, n}];
+    if (costs.empty()) costs.assign(kTuneCands, -1.0);
+    int pick = -1;
+    for (int k = 0; k < kTuneCands; ++k)
+        if (costs[k] < 0.0) {
+            pick = k;
+            break;
+        }
+    if (pick < 0) {
+        pick = 0;
+        for (int k = 1; k < kTuneCands; ++k)
+            if (costs[k] < costs[pick]) pick = k;
+    }
+    *cand = pick;
+    return kTuneCta[pick] * m;
 }
 
 }  // namespace
@@ -576,6 +737,12 @@ int excmg_batch_create(excmg_ctx* ctx, size_t hbm_budget_bytes, int max_instance
         return EXCMG_ERR_OOM;
     }
     memset(b->h_states, 0, mi * sizeof(BatchState));
+    if (cudaEventCreateWithFlags(&b->host_ready, cudaEventDisableTiming) != cudaSuccess) {
+        cudaGetLastError();
+        excmg_batch_destroy(b);
+        return EXCMG_ERR_CUDA;
+    }
+    for (int k = max_instances - 1; k >= 0; --k) b->free_slots.push_back(k);
     *out = b;
     return EXCMG_OK;
 }
@@ -586,6 +753,8 @@ int excmg_batch_destroy(excmg_batch* b) {
         if (b->ctx->stream) cudaStreamSynchronize(b->ctx->stream);
         else cudaDeviceSynchronize();
     }
+    for (auto& g : b->groups) group_free(g);
+    if (b->host_ready) cudaEventDestroy(b->host_ready);
     for (Instance* in : b->live) {
         free_instance(b, in);
         delete in;
@@ -641,7 +810,7 @@ int excmg_batch_submit(excmg_batch* b, int n_finest, int n_coarsest, int bc_kind
     const size_t need = instance_bytes(n_finest, n_coarsest, prec);
     if (b->budget && need > b->budget)
         return bfail(b, EXCMG_ERR_TOO_LARGE, "the instance needs more device memory than the batch's whole budget");
-    if ((int)b->live.size() >= b->max_instances) return bfail(b, EXCMG_ERR_BUDGET, "all instance slots are busy");
+    if (b->free_slots.empty()) return bfail(b, EXCMG_ERR_BUDGET, "all instance slots are busy");
     if (b->budget && b->bytes + need > b->budget)
         return bfail(b, EXCMG_ERR_BUDGET, "device-memory budget of the batch is full");
     Instance* in = new (std::nothrow) Instance();
@@ -706,24 +875,35 @@ int excmg_batch_submit(excmg_batch* b, int n_finest, int n_coarsest, int bc_kind
     }
     in->stats.levels = in->nl;
     in->t_submit = now_s();
+    in->slot = b->free_slots.back();
+    b->free_slots.pop_back();
     b->live.push_back(in);
-    const int slot = (int)b->live.size() - 1;
-    b->h_states[slot] = BatchState{};
-    b->h_states[slot].done = 1;   // no Bi-CG call yet
+    b->h_states[in->slot] = BatchState{};
+    b->h_states[in->slot].done = 1;   // no Bi-CG call yet
     *id_out = in->id;
     return EXCMG_OK;
 }
 
-// Advance every live instance: all pending per-instance steps, then one
-// batched launch of Bi-CG iterations per value type for the instances in
-// that phase.  *n_live receives the number of instances still running.
+// Advance the live instances: take back every group launch that has
+// completed, run the per-instance steps of every instance not on the GPU
+// (level set-up, direct solves, FP64 true residuals and the decisions of
+// Alg. 1 they drive), start one cooperative launch per level group of
+// instances ready for Bi-CG iterations (instances of one precision at one
+// grid size, each group on its own stream), then wait for at least one
+// running group.  *n_live receives the number of instances still running.
 int excmg_batch_step(excmg_batch* b, int* n_live) {
     if (!b) return EXCMG_ERR_ARG;
     excmg_ctx* ctx = b->ctx;
     cudaStream_t s = ctx->stream;
     int st = EXCMG_OK;
+    // 0. completed group launches
+    for (auto& g : b->groups)
+        if (g.busy && cudaEventQuery(g.done) == cudaSuccess)
+            if ((st = harvest(b, g))) return st;
+    cudaGetLastError();   // cudaErrorNotReady of the queries
     // 1. setup phases (the direct-solve levels run straight through)
     for (Instance* in : b->live) {
+        if (in->in_flight) continue;
         while (in->phase == kSetup) {
             if ((st = setup_level(b, in))) {
                 in->phase = kFailed;
@@ -744,8 +924,7 @@ int excmg_batch_step(excmg_batch* b, int* n_live) {
     // 2. FP64 true residuals (Alg. 1, line 7) and the decisions they drive
     std::vector<Instance*> res;
     for (Instance* in : b->live)
-        if (in->phase == kResidual) res.push_back(in);
-    bool states_dirty = false;
+        if (!in->in_flight && in->phase == kResidual) res.push_back(in);
     if (!res.empty()) {
         std::vector<std::pair<Instance*, const double*>> need_f;
         for (Instance* in : res)
@@ -803,7 +982,7 @@ int excmg_batch_step(excmg_batch* b, int* n_live) {
                 }
                 continue;
             }
-            const int slot = slot_of(b, in);
+            const int slot = in->slot;
             int cap = in->max_total - in->iters;
             if (cap > in->max_iter) cap = in->max_iter;
             cudaError_t e = cudaSuccess;
@@ -823,7 +1002,11 @@ int excmg_batch_step(excmg_batch* b, int* n_live) {
                 hs.max_iter = cap;
                 hs.done = 0;
                 hs.status = kRunning;
-                states_dirty = true;
+                // h_states is pinned: the slot's state is not touched again
+                // before its group launch has completed
+                if (e == cudaSuccess)
+                    e = cudaMemcpyAsync(b->d_states + slot, b->h_states + slot, sizeof(BatchState),
+                                        cudaMemcpyHostToDevice, s);
             } else {
                 // FP32 correction solve on A e = r / ||r||
                 in->scale = rn;
@@ -840,55 +1023,53 @@ int excmg_batch_step(excmg_batch* b, int* n_live) {
             in->phase = kInner;
         }
     }
-    // FP64 states were prepared on the host; FP32 ones by their init kernels:
-    // upload the former, then read everything back once
-    if (states_dirty) {
-        for (Instance* in : b->live)
-            if (in->phase == kInner && in->prec == EXCMG_PRECISION_FP64 && b->h_states[slot_of(b, in)].iter == 0) {
-                const int slot = slot_of(b, in);
-                cudaError_t e = cudaMemcpyAsync(b->d_states + slot, b->h_states + slot, sizeof(BatchState),
-                                                cudaMemcpyHostToDevice, s);
-                if (e != cudaSuccess) return bcuda(b, e, "state upload");
-            }
-    }
-    std::vector<Instance*> inner32, inner64;
+    // 3. one cooperative launch per level group of instances waiting for
+    // Bi-CG iterations, largest groups first, within the device's
+    // co-resident capacity (so that concurrent groups never wait on each
+    // other's CTAs)
+    std::map<std::pair<int, int>, std::vector<Instance*>> ready;
     for (Instance* in : b->live)
-        if (in->phase == kInner) (in->prec == EXCMG_PRECISION_FP64 ? inner64 : inner32).push_back(in);
-    if (!inner32.empty() || !inner64.empty()) {
-        cudaError_t e = cudaMemcpyAsync(b->h_states, b->d_states, b->live.size() * sizeof(BatchState),
-                                        cudaMemcpyDeviceToHost, s);
-        if (e == cudaSuccess) e = cudaStreamSynchronize(s);
-        if (e != cudaSuccess) return bcuda(b, e, "batch state read");
-        // 3. one batched launch per value type
-        if ((st = run_batched<double>(b, inner64, b->d_inst64))) return st;
-        if ((st = run_batched<float>(b, inner32, b->d_inst32))) return st;
-        e = cudaMemcpyAsync(b->h_states, b->d_states, b->live.size() * sizeof(BatchState), cudaMemcpyDeviceToHost, s);
-        if (e == cudaSuccess) e = cudaStreamSynchronize(s);
-        if (e != cudaSuccess) return bcuda(b, e, "batch state read");
-        // 4. finished Bi-CG calls: FP64 goes back to the true-residual test;
-        // mixed applies u += ||r|| e in FP64 first
-        for (Instance* in : b->live) {
-            if (in->phase != kInner) continue;
-            const BatchState& hs = b->h_states[slot_of(b, in)];
-            if (!hs.done) continue;
-            if (hs.status == kBreakdown) {
-                in->phase = kFailed;
-                in->status = EXCMG_ERR_BREAKDOWN;
-                continue;
+        if (!in->in_flight && in->phase == kInner) ready[{in->prec, in->nc << in->level}].push_back(in);
+    if (!ready.empty()) {
+        cudaError_t e = cudaEventRecord(b->host_ready, s);
+        if (e != cudaSuccess) return bcuda(b, e, "batch event");
+        std::vector<std::pair<long long, std::pair<int, int>>> order;
+        for (auto& kv : ready)
+            order.push_back({-(long long)kv.second.size() * node_count(kv.first.second), kv.first});
+        std::sort(order.begin(), order.end());
+        for (auto& o : order) {
+            const auto key = o.second;
+            std::vector<Instance*>& list = ready[key];
+            int used = 0;
+            for (auto& g : b->groups)
+                if (g.busy && g.prec == key.first) used += g.ctas;
+            // groups of the other precision run another kernel: count them too
+            for (auto& g : b->groups)
+                if (g.busy && g.prec != key.first) used += g.ctas;
+            const int cap = capacity_of(key.first) - used;
+            if (cap < 1) break;
+            int cand = -1;
+            int ctas = group_ctas(b, key.first, key.second, (int)list.size(), &cand);
+            if (ctas > cap) {
+                ctas = cap;
+                cand = -1;   // not the candidate's shape: not a tuning sample
             }
-            in->iters += hs.iter;
-            ++in->outer;
-            if (in->prec == EXCMG_PRECISION_MIXED) {
-                const int N = in->nc << in->level;
-                batch_correct_kernel<<<kVecBlocks, kVecThreads, 0, s>>>(in->u[in->level], in->e, node_count(N),
-                                                                        in->scale);
-                bnote(b, 1);
-                if ((e = cudaGetLastError()) != cudaSuccess) return bcuda(b, e, "batch correction");
+            excmg_batch::Group* slot = nullptr;
+            for (auto& g : b->groups)
+                if (!g.busy) {
+                    slot = &g;
+                    break;
+                }
+            if (!slot) {
+                b->groups.emplace_back();
+                slot = &b->groups.back();
             }
-            in->phase = kResidual;
+            st = key.first == EXCMG_PRECISION_FP64 ? launch_group<double>(b, *slot, list, ctas, cand)
+                                                   : launch_group<float>(b, *slot, list, ctas, cand);
+            if (st) return st;
         }
     }
-    // 5. finals
+    // 4. finals (EXP_true)
     bool any_final = false;
     for (Instance* in : b->live)
         if (in->phase == kFinal) {
@@ -901,28 +1082,33 @@ int excmg_batch_step(excmg_batch* b, int* n_live) {
     }
     const double t = now_s();
     std::vector<Instance*> keep;
-    std::vector<BatchState> hs;
-    for (size_t k = 0; k < b->live.size(); ++k) {
-        Instance* in = b->live[k];
+    for (Instance* in : b->live) {
         if (in->phase == kFinal || in->phase == kFailed) {
             if (in->phase == kFinal) in->phase = kDone;
             in->t_done = t;
             free_instance(b, in);
+            b->free_slots.push_back(in->slot);
             b->finished.push_back(in);
         } else {
             keep.push_back(in);
-            hs.push_back(b->h_states[k]);
         }
     }
-    // slots are positions in `live`: compact the device states with them
-    if (keep.size() != b->live.size()) {
-        b->live = keep;
-        if (!hs.empty()) {
-            memcpy(b->h_states, hs.data(), hs.size() * sizeof(BatchState));
-            cudaError_t e = cudaMemcpyAsync(b->d_states, b->h_states, hs.size() * sizeof(BatchState),
-                                            cudaMemcpyHostToDevice, s);
-            if (e == cudaSuccess) e = cudaStreamSynchronize(s);
-            if (e != cudaSuccess) return bcuda(b, e, "batch state compaction");
+    b->live = keep;
+    // 5. wait for one running group (the next step takes it back) unless
+    // some instance can move on without the GPU
+    bool host_work = false;
+    for (Instance* in : b->live)
+        if (!in->in_flight && (in->phase == kSetup || in->phase == kResidual)) host_work = true;
+    bool any_busy = false;
+    for (auto& g : b->groups) any_busy = any_busy || g.busy;
+    if (any_busy && !host_work) {
+        for (;;) {
+            bool one = false;
+            for (auto& g : b->groups)
+                if (g.busy && cudaEventQuery(g.done) == cudaSuccess) one = true;
+            cudaGetLastError();
+            if (one) break;
+            std::this_thread::yield();
         }
     }
     if (n_live) *n_live = (int)b->live.size();
