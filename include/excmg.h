@@ -330,6 +330,42 @@ int excmg_batch_query(excmg_batch *batch, int id, int *done, int *status, excmg_
 /* Kernel launches made by the batch so far. */
 long long excmg_batch_launches(const excmg_batch *batch);
 
+/* ------------------------------------------------------- the 2D problem */
+
+/* The two-dimensional problem of eq. (bvp2d): Laplacian^2 u = f on (0,1)^2
+ * with first- or second-kind Dirichlet data, discretised by the 13-point
+ * scheme (the paper names it without printing it; here the one built as
+ * eq. (method1) is built: 20 u - 8 (4 axis neighbours) + (4 at distance 2)
+ * + 2 (4 diagonal neighbours) = h^4 f, the square of the five-point
+ * Laplacian) with the reflection formulas of Sec. 2 along each axis, and
+ * solved by Alg. 1 / Alg. 2 with the 2D forms of the transfer steps.
+ * Node arrays hold (N+1)^2 doubles, x fastest: idx = j*(N+1) + i; g2 holds 4
+ * edges of N+1 doubles (x=0, x=1, y=0, y=1), indexed by the other
+ * coordinate (outward du/dn for bc_kind 1, d2u/dn2 for bc_kind 2).  Device
+ * pointers owned by the caller; every call is synchronous on ctx's stream.
+ * The operator sums its integer-weighted taps exactly on one power-of-two
+ * scale per 32 x 16 tile (the tile's largest input exponent) and rounds
+ * each output once. */
+/* y = A_h u (transpose: A_h^T u, the same bits); interior entries of u read,
+ * boundary entries of y set to 0. */
+int excmg2d_stencil_apply(excmg_ctx *ctx, int n, int bc_kind, int transpose, const double *u, double *y);
+/* Alg. 2 (M = I, r*_0 = r_0) on the 2D system, as bicg_solve. */
+int excmg2d_bicg_solve(excmg_ctx *ctx, int n, int bc_kind, const double *b, double *x_inout, double tol,
+                       int max_iter, int *iters_out, double *relres_out);
+/* EXP_finite in 2D (corners eq. (secfff), edge midpoints eq. (bfsec), cell
+ * centres the mean of the two diagonal rules, bi-quadratic interpolation);
+ * g1_fine as for extrapolate_interpolate (NULL: interpolated boundary). */
+int excmg2d_extrapolate_interpolate(excmg_ctx *ctx, int n_fine, const double *u_2h, const double *u_4h,
+                                    const double *g1_fine, double *w_h);
+/* EXP_true in 2D: u_tilde = u_h + (1/3) bilinear interpolation of u_h - u_2h. */
+int excmg2d_midpoint_extrapolate(excmg_ctx *ctx, int n_fine, const double *u_h, const double *u_2h,
+                                 double *u_tilde);
+/* Alg. 1 in 2D (FP64), arguments as excmg_solve_ex; n_coarsest 4..16 (the two
+ * direct-solve grids have at most 31^2 unknowns). */
+int excmg2d_solve(excmg_ctx *ctx, int n_finest, int n_coarsest, int bc_kind, const double *f, const double *g1,
+                  const double *g2, const excmg_params *params, double *u_h_out, double *u_tilde_out,
+                  excmg_stats *stats);
+
 /* ------------------------------------------------------------- diagnostics */
 
 /* Failure-path self-test (the paper has no counterpart): makes one of the

@@ -112,6 +112,15 @@ _lib.excmg_batch_launches.argtypes = [_vp]
 _lib.excmg_batch_launches.restype = ctypes.c_longlong
 _lib.excmg_selftest_wait_timeout.argtypes = [_i, ctypes.c_longlong]
 _lib.excmg_selftest_wait_timeout.restype = _i
+_lib.excmg2d_stencil_apply.argtypes = [_vp, _i, _i, _i, _vp, _vp]
+_lib.excmg2d_bicg_solve.argtypes = [_vp, _i, _i, _vp, _vp, _d, _i, ctypes.POINTER(_i), ctypes.POINTER(_d)]
+_lib.excmg2d_extrapolate_interpolate.argtypes = [_vp, _i, _vp, _vp, _vp, _vp]
+_lib.excmg2d_midpoint_extrapolate.argtypes = [_vp, _i, _vp, _vp, _vp]
+_lib.excmg2d_solve.argtypes = [_vp, _i, _i, _i, _vp, _vp, _vp, ctypes.POINTER(Params), _vp, _vp,
+                               ctypes.POINTER(Stats)]
+for _name in ("excmg2d_stencil_apply", "excmg2d_bicg_solve", "excmg2d_extrapolate_interpolate",
+              "excmg2d_midpoint_extrapolate", "excmg2d_solve"):
+    getattr(_lib, _name).restype = _i
 
 for _name in ("excmg_batch_create", "excmg_batch_destroy", "excmg_batch_submit", "excmg_batch_step",
               "excmg_batch_query"):
@@ -469,3 +478,89 @@ class Batch:
             self.close()
         except Exception:
             pass
+
+
+# ----------------------------------------------------------- the 2D problem
+# Node arrays of shape (N+1, N+1) indexed [j, i] (x fastest); g2 of shape
+# (4, N+1): edges x=0, x=1, y=0, y=1, indexed by the other coordinate.
+def _node2(t: torch.Tensor, n: int, name: str) -> int:
+    if not isinstance(t, torch.Tensor) or not t.is_cuda:
+        raise TypeError(f"{name} must be a CUDA tensor")
+    if t.dtype != torch.float64 or not t.is_contiguous() or t.numel() != (n + 1) ** 2:
+        raise ValueError(f"{name} must be a contiguous float64 tensor with (N+1)^2 = {(n + 1) ** 2} elements")
+    return t.data_ptr()
+
+
+def _new_node2(n: int, like: torch.Tensor) -> torch.Tensor:
+    return torch.empty((n + 1, n + 1), dtype=torch.float64, device=like.device)
+
+
+def stencil_apply2d(n: int, bc_kind: int, u: torch.Tensor, y: torch.Tensor | None = None, transpose: bool = False,
+                    ctx: Context | None = None) -> torch.Tensor:
+    """y = A_h u of the 13-point scheme of the 2D problem."""
+    ctx = ctx or default_context(u.device)
+    if y is None:
+        y = _new_node2(n, u)
+    ctx.check(_lib.excmg2d_stencil_apply(ctx.handle, int(n), int(bc_kind), int(bool(transpose)),
+                                         _vp(_node2(u, n, "u")), _vp(_node2(y, n, "y"))), "excmg2d_stencil_apply")
+    return y
+
+
+def bicg_solve2d(n: int, bc_kind: int, b: torch.Tensor, x: torch.Tensor, tol: float, max_iter: int = 100000,
+                 ctx: Context | None = None):
+    """Alg. 2 on the 2D system in place; returns (iters, relres, status)."""
+    ctx = ctx or default_context(b.device)
+    it = ctypes.c_int(0)
+    rr = ctypes.c_double(0.0)
+    rc = _lib.excmg2d_bicg_solve(ctx.handle, int(n), int(bc_kind), _vp(_node2(b, n, "b")), _vp(_node2(x, n, "x")),
+                                 float(tol), int(max_iter), ctypes.byref(it), ctypes.byref(rr))
+    if rc not in (EXCMG_OK, -4):
+        ctx.check(rc, "excmg2d_bicg_solve")
+    return it.value, rr.value, rc
+
+
+def extrapolate_interpolate2d(n_fine: int, u_2h: torch.Tensor, u_4h: torch.Tensor, w_h: torch.Tensor | None = None,
+                              g1_fine: torch.Tensor | None = None, ctx: Context | None = None) -> torch.Tensor:
+    ctx = ctx or default_context(u_2h.device)
+    if w_h is None:
+        w_h = _new_node2(n_fine, u_2h)
+    pg = _vp(_node2(g1_fine, n_fine, "g1_fine")) if g1_fine is not None else _vp(0)
+    ctx.check(_lib.excmg2d_extrapolate_interpolate(ctx.handle, int(n_fine), _vp(_node2(u_2h, n_fine // 2, "u_2h")),
+                                                   _vp(_node2(u_4h, n_fine // 4, "u_4h")), pg,
+                                                   _vp(_node2(w_h, n_fine, "w_h"))), "excmg2d_extrapolate_interpolate")
+    return w_h
+
+
+def midpoint_extrapolate2d(n_fine: int, u_h: torch.Tensor, u_2h: torch.Tensor, u_tilde: torch.Tensor | None = None,
+                           ctx: Context | None = None) -> torch.Tensor:
+    ctx = ctx or default_context(u_h.device)
+    if u_tilde is None:
+        u_tilde = _new_node2(n_fine, u_h)
+    ctx.check(_lib.excmg2d_midpoint_extrapolate(ctx.handle, int(n_fine), _vp(_node2(u_h, n_fine, "u_h")),
+                                                _vp(_node2(u_2h, n_fine // 2, "u_2h")),
+                                                _vp(_node2(u_tilde, n_fine, "u_tilde"))), "excmg2d_midpoint_extrapolate")
+    return u_tilde
+
+
+def excmg_solve2d(n_finest: int, n_coarsest: int, bc_kind: int, f: torch.Tensor, g1: torch.Tensor, g2: torch.Tensor,
+                  tol: float, u_out: torch.Tensor | None = None, *, ctx: Context | None = None,
+                  tol_mode: str = "uniform", max_iter: int = 100000, max_total: int = 1000000, check_every: int = 16,
+                  u_h_out: torch.Tensor | None = None, return_stats: bool = False):
+    """Alg. 1 on the 2D problem; returns u_tilde (and per-level statistics)."""
+    ctx = ctx or default_context(f.device)
+    n = int(n_finest)
+    if u_out is None:
+        u_out = _new_node2(n, f)
+    if not isinstance(g2, torch.Tensor) or g2.dtype != torch.float64 or not g2.is_contiguous() or \
+            g2.numel() != 4 * (n + 1):
+        raise ValueError("g2 must be a contiguous float64 CUDA tensor with 4 (N+1) elements")
+    params = Params(float(tol), TOL_MODES[tol_mode], int(max_iter), int(max_total), int(check_every), 0, 1e-4)
+    stats = Stats()
+    ph = _vp(_node2(u_h_out, n, "u_h_out")) if u_h_out is not None else _vp(0)
+    rc = _lib.excmg2d_solve(ctx.handle, n, int(n_coarsest), int(bc_kind), _vp(_node2(f, n, "f")),
+                            _vp(_node2(g1, n, "g1")), _vp(g2.data_ptr()), ctypes.byref(params), ph,
+                            _vp(_node2(u_out, n, "u_out")), ctypes.byref(stats))
+    ctx.check(rc, "excmg2d_solve")
+    if return_stats:
+        return u_out, stats.as_list()
+    return u_out

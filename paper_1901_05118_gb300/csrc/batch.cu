@@ -373,12 +373,20 @@ struct excmg_batch {
     };
     std::vector<Group> groups;
     cudaEvent_t host_ready = nullptr;   // the context stream's state uploads
-    // Grid-size tuner: per (precision, grid size) the CTA-milliseconds per
-    // instance iteration measured for each candidate number of CTAs per
-    // instance; the cheapest is used once every candidate has been tried.
-    // The grid size changes no result bit (every partial sum belongs to a
-    // tile or chunk, not to a CTA).
-    std::map<std::pair<int, int>, std::vector<double>> tune;
+    // Grid-size tuner, per (precision, grid size).  Candidate c gives each
+    // instance ceil(W / kTuneItems[c]) CTAs, W being its operator tiles or
+    // vector chunks, whichever are more.  Candidates are tried from the most
+    // CTAs down, and trying stops once a round takes more than twice the
+    // best round time seen.  The choice: the fewest CTA-milliseconds per
+    // instance round among the candidates within 1.25x of the best round
+    // time.  The grid size changes no result bit (every partial sum belongs
+    // to a tile or chunk, not to a CTA).
+    struct Tune {
+        double ms[8];       // milliseconds per round, -1 untried
+        double cta_ms[8];   // CTA-milliseconds per instance round
+        bool settled = false;
+    };
+    std::map<std::pair<int, int>, Tune> tune;
 };
 
 namespace {
@@ -509,8 +517,11 @@ BatchInst<T> geometry(Instance* in, int slot, int* units, int* chunks) {
 }
 
 // ------------------------------------------------------------ level groups
-constexpr int kTuneCands = 6;
-constexpr int kTuneCta[kTuneCands] = {1, 2, 4, 8, 16, 32};   // CTAs per instance
+constexpr int kTuneCands = 5;
+constexpr int kTuneItems[kTuneCands] = {1, 2, 4, 8, 16};   // tiles or chunks per CTA
+
+// CTAs per instance of candidate c for an instance with W work items.
+int tune_cpi(int W, int c) { return (W + kTuneItems[c] - 1) / kTuneItems[c]; }
 
 int capacity_of(int prec) {
     return prec == EXCMG_PRECISION_FP64 ? batch_resident_ctas<double>() : batch_resident_ctas<float>();
@@ -636,6 +647,16 @@ int launch_group(excmg_batch* b, excmg_batch::Group& g, const std::vector<Instan
     return EXCMG_OK;
 }
 
+excmg_batch::Tune& tune_of(excmg_batch* b, int prec, int n) {
+    auto it = b->tune.find({prec, n});
+    if (it == b->tune.end()) {
+        excmg_batch::Tune t;
+        for (int k = 0; k < 8; ++k) t.ms[k] = t.cta_ms[k] = -1.0;
+        it = b->tune.emplace(std::make_pair(prec, n), t).first;
+    }
+    return it->second;
+}
+
 // A completed group launch: its members' states come back, the tuner learns
 // the launch's cost, and every member whose Bi-CG call ended goes back to the
 // true-residual test of Alg. 1 (mixed: after u += ||r|| e).
@@ -654,10 +675,20 @@ int harvest(excmg_batch* b, excmg_batch::Group& g) {
     if (g.cand >= 0 && *g.h_rounds > 0) {
         float ms = 0.f;
         if (cudaEventElapsedTime(&ms, g.start, g.done) == cudaSuccess) {
-            auto& costs = b->tune[{g.prec, g.n}];
-            if (costs.empty()) costs.assign(kTuneCands, -1.0);
-            const double c = (double)ms * g.ctas / ((double)*g.h_rounds * (double)g.members.size());
-            if (costs[g.cand] < 0.0 || c < costs[g.cand]) costs[g.cand] = c;
+            excmg_batch::Tune& t = tune_of(b, g.prec, g.n);
+            const double per_round = (double)ms / (double)*g.h_rounds;
+            const double c = per_round * g.ctas / (double)g.members.size();
+            if (t.ms[g.cand] < 0.0 || per_round < t.ms[g.cand]) {
+                t.ms[g.cand] = per_round;
+                t.cta_ms[g.cand] = c;
+            }
+            double best = -1.0;
+            bool all = true;
+            for (int k = 0; k < kTuneCands; ++k) {
+                if (t.ms[k] < 0.0) all = false;
+                else if (best < 0.0 || t.ms[k] < best) best = t.ms[k];
+            }
+            if (all || per_round > 2.0 * best) t.settled = true;
         } else {
             cudaGetLastError();
         }
@@ -686,24 +717,35 @@ int harvest(excmg_batch* b, excmg_batch::Group& g) {
     return EXCMG_OK;
 }
 
-// CTAs for a group of m instances of grid size n: the tuner's next untried
-// candidate, else its cheapest; *cand the candidate index (-1: not tuning).
-int group_ctas(excmg_batch* b, int prec, int n, int m, int* cand) {
-    auto& costs = b->tune[{prec, n}];
-    if (costs.empty()) costs.assign(kTuneCands, -1.0);
+// CTAs for a group of m instances of grid size n with W work items each:
+// the tuner's next candidate while it is still trying, else its choice; *cand
+// the candidate index.
+int group_ctas(excmg_batch* b, int prec, int n, int W, int m, int* cand) {
+    excmg_batch::Tune& t = tune_of(b, prec, n);
     int pick = -1;
-    for (int k = 0; k < kTuneCands; ++k)
-        if (costs[k] < 0.0) {
+    if (!t.settled) {
+        for (int k = 0; k < kTuneCands && pick < 0; ++k) {
+            if (t.ms[k] >= 0.0) continue;
+            if (k > 0 && t.ms[k - 1] >= 0.0 && tune_cpi(W, k) == tune_cpi(W, k - 1)) {
+                // the same grid as the candidate before: nothing new to learn
+                t.ms[k] = t.ms[k - 1];
+                t.cta_ms[k] = t.cta_ms[k - 1];
+                continue;
+            }
             pick = k;
-            break;
         }
+        if (pick < 0) t.settled = true;
+    }
     if (pick < 0) {
-        pick = 0;
-        for (int k = 1; k < kTuneCands; ++k)
-            if (costs[k] < costs[pick]) pick = k;
+        double best = -1.0;
+        for (int k = 0; k < kTuneCands; ++k)
+            if (t.ms[k] >= 0.0 && (best < 0.0 || t.ms[k] < best)) best = t.ms[k];
+        for (int k = 0; k < kTuneCands; ++k)
+            if (t.ms[k] >= 0.0 && t.ms[k] <= 1.25 * best && (pick < 0 || t.cta_ms[k] < t.cta_ms[pick])) pick = k;
+        if (pick < 0) pick = 0;
     }
     *cand = pick;
-    return kTuneCta[pick] * m;
+    return tune_cpi(W, pick) * m;
 }
 
 }  // namespace
@@ -1048,8 +1090,9 @@ int excmg_batch_step(excmg_batch* b, int* n_live) {
                 if (g.busy && g.prec != key.first) used += g.ctas;
             const int cap = capacity_of(key.first) - used;
             if (cap < 1) break;
-            int cand = -1;
-            int ctas = group_ctas(b, key.first, key.second, (int)list.size(), &cand);
+            int cand = -1, units = 0, chunks = 0;
+            geometry<double>(list[0], 0, &units, &chunks);
+            int ctas = group_ctas(b, key.first, key.second, units > chunks ? units : chunks, (int)list.size(), &cand);
             if (ctas > cap) {
                 ctas = cap;
                 cand = -1;   // not the candidate's shape: not a tuning sample

@@ -48,10 +48,15 @@ constexpr int PP_AHEAD = PP_STAGES - 1;         // planes copied ahead of the on
 
 static_assert(PP_TX == FX_TX && PP_OY == FX_OY, "same tiles as fx_march (same sigma partials)");
 
-// dynamic shared memory: copy stages (NF fields) + two fixed-point tiles
+// copy stages: four (three planes ahead), three when four arrays are copied
+// per slot (the fused direction update), so that two CTAs fit on an SM
+__host__ __device__ constexpr int pp_stages(int nf) { return nf > 2 ? 3 : PP_STAGES; }
+
+// dynamic shared memory: copy stages (NF arrays copied per slot) + two
+// fixed-point tiles
 template <int NF>
 __host__ __device__ constexpr size_t pp_smem_bytes() {
-    return (size_t)PP_STAGES * NF * PP_HALO * sizeof(double) + (size_t)2 * PP_HALO * sizeof(long long);
+    return (size_t)pp_stages(NF) * NF * PP_HALO * sizeof(double) + (size_t)2 * PP_HALO * sizeof(long long);
 }
 
 // Halo index (ly * PP_HX + lx) of slot s of thread tid: slots 0, 1 are the
@@ -151,17 +156,36 @@ __device__ __forceinline__ double fx_result_cvt(long long acc, int E, bool poiso
 // shadow-elided mode; the same sums in the same order).  kCvt: round the
 // outputs through the hardware integer-to-double conversion.  Shared memory
 // is addressed through 32-bit shared-window addresses.
-template <bool kElide, bool kCvt>
+//
+// kDir (the fused schedule): p and ps hold the previous directions p_{k-1},
+// p*_{k-1}; every loaded node first becomes p_k = r_k + beta p_{k-1} (r, rs
+// give r_k, r*_k; p*_k likewise, and the twin check asks r* = r and
+// p*_{k-1} = p_{k-1}); the nodes the CTA owns are written to pn (and psn),
+// which must not alias p, ps (neighbouring CTAs still read the old values).
+struct PairDir {
+    const double* r = nullptr;
+    const double* rs = nullptr;
+    double* pn = nullptr;
+    double* psn = nullptr;
+    double beta = 0.0;
+};
+
+template <bool kElide, bool kCvt, bool kDir = false>
 __device__ __forceinline__ bool pp_march(const double* __restrict__ p, const double* __restrict__ ps,
                                          double* __restrict__ q, double* __restrict__ qs, int n, int sigma, int bx,
-                                         int by, int kz0, int kz1, unsigned char* smem, double* dot) {
-    constexpr int NF = kElide ? 1 : 2;
+                                         int by, int kz0, int kz1, unsigned char* smem, double* dot,
+                                         const PairDir& dir = PairDir{}) {
+    // arrays copied per slot: p (or p_{k-1}) [, r] [, p* (or p*_{k-1}) [, r*]]
+    constexpr int NF = (kElide ? 1 : 2) * (kDir ? 2 : 1);
+    constexpr int kShadow = kDir ? 2 : 1;   // index of the first shadow array
+    constexpr int S = pp_stages(NF);        // copy stages
+    constexpr int AHEAD = S - 1;            // planes copied ahead of the one converted
     constexpr unsigned kField = PP_HALO * 8u;          // bytes of one field of a stage
     constexpr unsigned kStage = NF * kField;           // bytes of one stage
     constexpr unsigned kTile = PP_HALO * 8u;           // bytes of one fixed-point tile
     __shared__ int wmax[2][PP_NT / 32];
     const unsigned raw = smem_u32(smem);
-    const unsigned tiles = raw + PP_STAGES * kStage;
+    const unsigned tiles = raw + S * kStage;
     const int np = n + 1;
     const unsigned plane = (unsigned)np * (unsigned)np;
     const int tx = threadIdx.x, ty = threadIdx.y, tid = ty * PP_TX + tx;
@@ -200,7 +224,7 @@ __device__ __forceinline__ bool pp_march(const double* __restrict__ p, const dou
             const int zin = kz0 - 2 + t;
             const bool zok = zin >= 1 && zin <= n - 1;
             const unsigned zb = zok ? (unsigned)zin * plane : 0u;
-            const unsigned st = raw + (unsigned)(t & (PP_STAGES - 1)) * kStage;
+            const unsigned st = raw + ((unsigned)t % (unsigned)S) * kStage;
 #pragma unroll
             for (int s = 0; s < 3; ++s) {
                 if (s < 2 || ring) {
@@ -208,7 +232,9 @@ __device__ __forceinline__ bool pp_march(const double* __restrict__ p, const dou
                     const unsigned gidx = ld ? zb + sidx[s] : 0u;
                     const unsigned nb = ld ? 8u : 0u;
                     cp_async8_u32(st + so[s], p + gidx, nb);
-                    if (!kElide) cp_async8_u32(st + kField + so[s], ps + gidx, nb);
+                    if (kDir) cp_async8_u32(st + kField + so[s], dir.r + gidx, nb);
+                    if (!kElide) cp_async8_u32(st + kShadow * kField + so[s], ps + gidx, nb);
+                    if (!kElide && kDir) cp_async8_u32(st + (kShadow + 1) * kField + so[s], dir.rs + gidx, nb);
                 }
             }
         }
@@ -217,21 +243,32 @@ __device__ __forceinline__ bool pp_march(const double* __restrict__ p, const dou
     // read back plane t's slots (its copies complete) and their exponents,
     // publish the warp's exponent maximum; false if p* differs from p
     auto scan = [&](int t, double (&v)[3], unsigned (&ev)[3]) -> bool {
-        const unsigned st = raw + (unsigned)(t & (PP_STAGES - 1)) * kStage;
+        const unsigned st = raw + ((unsigned)t % (unsigned)S) * kStage;
         unsigned diff = 0u, emax = 0u;
 #pragma unroll
         for (int s = 0; s < 3; ++s) {
             v[s] = 0.0;
             ev[s] = 0u;
             if (s < 2 || ring) {
-                v[s] = lds_f64(st + so[s]);
+                const double po = lds_f64(st + so[s]);
+                if (!kElide) {
+                    const double w = lds_f64(st + kShadow * kField + so[s]);
+                    diff |= ((unsigned)__double2loint(po) ^ (unsigned)__double2loint(w)) |
+                            ((unsigned)__double2hiint(po) ^ (unsigned)__double2hiint(w));
+                }
+                if (kDir) {
+                    const double rv = lds_f64(st + kField + so[s]);
+                    if (!kElide) {
+                        const double w = lds_f64(st + (kShadow + 1) * kField + so[s]);
+                        diff |= ((unsigned)__double2loint(rv) ^ (unsigned)__double2loint(w)) |
+                                ((unsigned)__double2hiint(rv) ^ (unsigned)__double2hiint(w));
+                    }
+                    v[s] = rv + dir.beta * po;   // p_k = r_k + beta p_{k-1}
+                } else {
+                    v[s] = po;
+                }
                 ev[s] = ((unsigned)__double2hiint(v[s]) >> 20) & 0x7FFu;
                 emax = max(emax, ev[s]);
-                if (!kElide) {
-                    const double w = lds_f64(st + kField + so[s]);
-                    diff |= ((unsigned)__double2loint(v[s]) ^ (unsigned)__double2loint(w)) |
-                            ((unsigned)__double2hiint(v[s]) ^ (unsigned)__double2hiint(w));
-                }
             }
         }
         emax = __reduce_max_sync(0xffffffffu, emax);
@@ -241,8 +278,8 @@ __device__ __forceinline__ bool pp_march(const double* __restrict__ p, const dou
     auto plane_max = [&](int t) { return (int)__reduce_max_sync(0xffffffffu, (unsigned)wmax[t & 1][lane & 7]); };
 
 #pragma unroll
-    for (int t = 0; t < PP_AHEAD; ++t) issue(t);
-    cp_async_wait<PP_AHEAD - 1>();
+    for (int t = 0; t < AHEAD; ++t) issue(t);
+    cp_async_wait<AHEAD - 1>();
     double cur[3];
     unsigned ecur[3];
     bool same = scan(0, cur, ecur);
@@ -262,8 +299,8 @@ __device__ __forceinline__ bool pp_march(const double* __restrict__ p, const dou
     double d = 0.0;
 
     for (int t = 0; t < T; ++t) {
-        issue(t + PP_AHEAD);
-        cp_async_wait<PP_AHEAD - 1>();   // planes up to t + 1 have landed
+        issue(t + AHEAD);
+        cp_async_wait<AHEAD - 1>();   // planes up to t + 1 have landed
         double nxt[3] = {0.0, 0.0, 0.0};
         unsigned enx[3] = {0u, 0u, 0u};
         same = t + 1 < T ? scan(t + 1, nxt, enx) : true;
@@ -272,6 +309,18 @@ __device__ __forceinline__ bool pp_march(const double* __restrict__ p, const dou
 #pragma unroll
         for (int s = 0; s < 3; ++s)
             if (s < 2 || ring) sts_s64(tl + so[s], to_fixed_e(cur[s], ecur[s], E));
+        if (kDir) {   // the new directions of the nodes this CTA owns
+            const int zt = kz0 - 2 + t;
+            if (zt >= kz0 && zt < kz1) {
+                const unsigned zb = (unsigned)zt * plane;
+#pragma unroll
+                for (int s = 0; s < 2; ++s)
+                    if (s == 0 ? act0 : act1) {
+                        dir.pn[zb + sidx[s]] = cur[s];
+                        if (!kElide) dir.psn[zb + sidx[s]] = cur[s];
+                    }
+            }
+        }
         // every tile of plane t written, every exponent of plane t + 1
         // published, every read of the tile of plane t - 2 done
         if (!__syncthreads_and(same)) {

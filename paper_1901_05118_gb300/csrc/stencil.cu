@@ -195,6 +195,57 @@ stencil_pair_kernel(const double* __restrict__ p, const double* __restrict__ ps,
     }
 }
 
+// The fused schedule's operator launch: p = r + beta p_prev (and p*) formed
+// on every loaded node, the nodes the CTA owns written to (pn, psn), then
+// q = A p, q* = A^T p*, sigma and alpha, with the copy-ahead march (bit for
+// bit the results of stencil_fx_kernel<2, true, true>).  A CTA whose slab
+// holds a node where r* != r or p*_prev != p_prev runs the general march.
+__device__ __noinline__ double pair_two_field_dir(const double* r, const double* rs, const double* pp,
+                                                  const double* psp, double* pn, double* psn, double* q, double* qs,
+                                                  double beta, int n, int sigma, int kz0, int kz1) {
+    FxFields fl{{pp, psp}, {q, qs}, {r, rs}, {pn, psn}, beta, nullptr, nullptr};
+    return fx_march<2, true, true>(fl, nullptr, n, sigma, blockIdx.x, blockIdx.y, kz0, kz1);
+}
+
+template <bool kElide>
+__global__ void __launch_bounds__(PP_NT, 2)
+stencil_pair_dir_kernel(const double* __restrict__ r, const double* __restrict__ rs, const double* __restrict__ pp,
+                        const double* __restrict__ psp, double* __restrict__ pn, double* __restrict__ psn,
+                        double* __restrict__ q, double* __restrict__ qs, int n, int sigma, int kz_per_cta,
+                        double* partials, BicgState* st) {
+    extern __shared__ __align__(128) unsigned char pp_smem[];
+    if (st->done) return;
+    const int kz0 = 1 + blockIdx.z * kz_per_cta;
+    const int kz1 = min(kz0 + kz_per_cta, n);
+    const PairDir dir{r, rs, pn, psn, st->beta};
+    double dot = 0.0;
+    const bool fast = pp_march<kElide, kPairCvt, true>(pp, psp, q, qs, n, sigma, blockIdx.x, blockIdx.y, kz0, kz1,
+                                                      pp_smem, &dot, dir);
+    if constexpr (!kElide) {
+        if (!fast) {
+            __syncthreads();
+            dot = pair_two_field_dir(r, rs, pp, psp, pn, psn, q, qs, dir.beta, n, sigma, kz0, kz1);
+        }
+    }
+    __shared__ double sh[32];
+    __shared__ bool am_last;
+    const double sdot = block_sum(dot, sh);
+    if (publish_partials(&sdot, 1, partials, &st->ticket, &am_last)) {
+        const double sg = gather_partials(partials, 0, sh);
+        if (thread0()) {
+            const double rho = st->rho;
+            st->sigma = sg;
+            if (!(rho != 0.0 && isfinite(rho)) || !(sg != 0.0 && isfinite(sg))) {
+                st->status = kBreakdown;
+                st->done = 1;
+            } else {
+                st->alpha = rho / sg;
+            }
+            st->ticket = 0;
+        }
+    }
+}
+
 // A u at one interior node (i, j, k) with the integer arithmetic, without
 // shared memory: the node's own 25 taps are put on the scale of their
 // largest exponent and summed exactly.  Used where grids are so small that
@@ -611,6 +662,17 @@ StencilGrid pair_grid(int n) {
     return g;
 }
 
+// The fused schedule's launches (both modes on this grid: the same sigma
+// partial sums); the first iteration of a call (no previous directions) runs
+// stencil_pair_kernel on the same grid.
+StencilGrid pair_dir_grid(int n) {
+    const int occ = resident_per_sm(stencil_pair_dir_kernel<false>, PP_NT, pp_smem_bytes<4>());
+    StencilGrid g = stencil_grid(n, PP_TX, PP_OY, occ);
+    g.block = dim3(PP_TX, PP_TY, 1);
+    g.smem = pp_smem_bytes<4>();
+    return g;
+}
+
 StencilGrid f64_grid(int n) {
     const int occ = resident_per_sm(stencil_f64_kernel<false>, TX * TY);
     StencilGrid g = stencil_grid(n, TX, TY, occ);
@@ -628,6 +690,8 @@ int stencil_cta_count(int n) {
     }
     const StencilGrid g = pair_grid(n);
     most = max(most, g.grid.x * g.grid.y * g.grid.z);
+    const StencilGrid gd = pair_dir_grid(n);
+    most = max(most, gd.grid.x * gd.grid.y * gd.grid.z);
     return (int)most;
 }
 
@@ -730,30 +794,22 @@ cudaError_t launch_bicg_persistent(double* x, double* r, double* rs, double* p, 
 cudaError_t launch_bicg_stencil_pair_dir(const double* r, const double* rs, const double* p_prev,
                                          const double* ps_prev, double* p, double* ps, double* q, double* qs, int n,
                                          int bc_kind, double* partials, BicgState* st, cudaStream_t s) {
-    FxFields fl{{p_prev, ps_prev}, {q, qs}, {r, rs}, {p, ps}, 0.0, nullptr, nullptr};
     const int sg = bc_kind == 1 ? 1 : -1;
-    if (bulk_ok(n, {r, rs, p_prev, ps_prev})) {
-        const StencilGrid g = fx_grid(n, 5);
-        opt_in_smem(stencil_fx_kernel<2, true, true, true>, g.smem);
-        stencil_fx_kernel<2, true, true, true><<<g.grid, g.block, g.smem, s>>>(fl, nullptr, n, sg, g.kz_per_cta,
-                                                                               &st->done, partials, st);
-    } else {
-        const StencilGrid g = fx_grid(n, 3);
-        stencil_fx_kernel<2, true, true><<<g.grid, g.block, 0, s>>>(fl, nullptr, n, sg, g.kz_per_cta, &st->done,
-                                                                    partials, st);
-    }
+    const StencilGrid g = pair_dir_grid(n);
+    opt_in_smem(stencil_pair_dir_kernel<false>, g.smem);
+    stencil_pair_dir_kernel<false><<<g.grid, g.block, g.smem, s>>>(r, rs, p_prev, ps_prev, p, ps, q, qs, n, sg,
+                                                                   g.kz_per_cta, partials, st);
     return cudaGetLastError();
 }
 
 cudaError_t launch_bicg_stencil_pair(const double* p, double* q, const double* ps, double* qs, int n,
                                      int bc_kind, double* partials, BicgState* st, cudaStream_t s, bool staged) {
-    FxFields fl{{p, ps}, {q, qs}, {nullptr, nullptr}, {nullptr, nullptr}, 0.0, nullptr, nullptr};
     const int sg = bc_kind == 1 ? 1 : -1;
-    if (staged && bulk_ok(n, {p, ps})) {
-        const StencilGrid g = fx_grid(n, 4);
-        opt_in_smem(stencil_fx_kernel<2, true, false, true>, g.smem);
-        stencil_fx_kernel<2, true, false, true><<<g.grid, g.block, g.smem, s>>>(fl, nullptr, n, sg, g.kz_per_cta,
-                                                                                &st->done, partials, st);
+    if (staged) {   // the fused schedule's first iteration: its grid
+        const StencilGrid g = pair_dir_grid(n);
+        const size_t smem = pp_smem_bytes<2>();
+        opt_in_smem(stencil_pair_kernel<false>, smem);
+        stencil_pair_kernel<false><<<g.grid, g.block, smem, s>>>(p, ps, q, qs, n, sg, g.kz_per_cta, partials, st);
     } else {
         const StencilGrid g = pair_grid(n);
         opt_in_smem(stencil_pair_kernel<false>, g.smem);
@@ -764,13 +820,13 @@ cudaError_t launch_bicg_stencil_pair(const double* p, double* q, const double* p
 
 cudaError_t launch_cg_stencil(const double* p, double* q, int n, int bc_kind, double* partials, BicgState* st,
                               cudaStream_t s, bool staged) {
-    FxFields fl{{p, nullptr}, {q, nullptr}, {nullptr, nullptr}, {nullptr, nullptr}, 0.0, nullptr, nullptr};
     const int sg = bc_kind == 1 ? 1 : -1;
-    if (staged && bulk_ok(n, {p})) {
-        const StencilGrid g = fx_grid(n, 6);
-        opt_in_smem(stencil_fx_kernel<1, true, false, true>, g.smem);
-        stencil_fx_kernel<1, true, false, true><<<g.grid, g.block, g.smem, s>>>(fl, nullptr, n, sg, g.kz_per_cta,
-                                                                                &st->done, partials, st);
+    if (staged) {   // the fused schedule's first iteration: its grid
+        const StencilGrid g = pair_dir_grid(n);
+        const size_t smem = pp_smem_bytes<1>();
+        opt_in_smem(stencil_pair_kernel<true>, smem);
+        stencil_pair_kernel<true><<<g.grid, g.block, smem, s>>>(p, nullptr, q, nullptr, n, sg, g.kz_per_cta, partials,
+                                                               st);
     } else {
         const StencilGrid g = pair_grid(n);
         const size_t smem = pp_smem_bytes<1>();
@@ -783,18 +839,12 @@ cudaError_t launch_cg_stencil(const double* p, double* q, int n, int bc_kind, do
 
 cudaError_t launch_cg_stencil_dir(const double* r, const double* p_prev, double* p, double* q, int n, int bc_kind,
                                   double* partials, BicgState* st, cudaStream_t s) {
-    FxFields fl{{p_prev, nullptr}, {q, nullptr}, {r, nullptr}, {p, nullptr}, 0.0, nullptr, nullptr};
     const int sg = bc_kind == 1 ? 1 : -1;
-    if (bulk_ok(n, {r, p_prev})) {
-        const StencilGrid g = fx_grid(n, 7);
-        opt_in_smem(stencil_fx_kernel<1, true, true, true>, g.smem);
-        stencil_fx_kernel<1, true, true, true><<<g.grid, g.block, g.smem, s>>>(fl, nullptr, n, sg, g.kz_per_cta,
-                                                                               &st->done, partials, st);
-    } else {
-        const StencilGrid g = fx_grid(n, 3);
-        stencil_fx_kernel<1, true, true><<<g.grid, g.block, 0, s>>>(fl, nullptr, n, sg, g.kz_per_cta, &st->done,
-                                                                    partials, st);
-    }
+    const StencilGrid g = pair_dir_grid(n);
+    const size_t smem = pp_smem_bytes<2>();
+    opt_in_smem(stencil_pair_dir_kernel<true>, smem);
+    stencil_pair_dir_kernel<true><<<g.grid, g.block, smem, s>>>(r, nullptr, p_prev, nullptr, p, nullptr, q, nullptr,
+                                                                n, sg, g.kz_per_cta, partials, st);
     return cudaGetLastError();
 }
 

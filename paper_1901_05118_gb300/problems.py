@@ -299,3 +299,72 @@ def random_field(N: int, seed: int, lo: float = -1.0, hi: float = 1.0) -> np.nda
     """Seeded uniform random node array (for operator parity on rough inputs)."""
     rng = np.random.Generator(np.random.PCG64(seed))
     return rng.uniform(lo, hi, size=(N + 1,) * 3)
+
+
+# -------------------------------------------------------------- 2D variant
+# The two-dimensional problem (eq. (bvp2d)) on (0,1)^2.  Node arrays of shape
+# (N+1, N+1) indexed [j, i] (x fastest); g2 of shape (4, N+1): edges x=0,
+# x=1, y=0, y=1, indexed by the other coordinate.
+@dataclass(frozen=True)
+class Manufactured2D:
+    """u = sum_m A_m X_m(x) Y_m(y) with each factor given as (fn, d1, d2, d4)."""
+
+    name: str
+    terms: tuple
+
+    @staticmethod
+    def axes(N: int):
+        s = np.arange(N + 1, dtype=np.float64) / N
+        return s[None, :], s[:, None]
+
+    def _sum(self, kx: int, ky: int, x, y):
+        return sum(A * X[kx](x) * Y[ky](y) for A, X, Y in self.terms)
+
+    def exact(self, N: int) -> np.ndarray:
+        x, y = self.axes(N)
+        return np.ascontiguousarray(np.broadcast_to(self._sum(0, 0, x, y), (N + 1, N + 1)), dtype=np.float64)
+
+    def rhs(self, N: int) -> np.ndarray:
+        """f = u_xxxx + 2 u_xxyy + u_yyyy."""
+        x, y = self.axes(N)
+        f = self._sum(3, 0, x, y) + 2 * self._sum(2, 2, x, y) + self._sum(0, 3, x, y)
+        return np.ascontiguousarray(np.broadcast_to(f, (N + 1, N + 1)), dtype=np.float64)
+
+    def boundary_g2(self, N: int, bc_kind: int) -> np.ndarray:
+        s = np.arange(N + 1, dtype=np.float64) / N
+        g2 = np.empty((4, N + 1))
+        for e in range(4):
+            axis, side = divmod(e, 2)
+            c = np.ones(N + 1) if side else np.zeros(N + 1)
+            x, y = (c, s) if axis == 0 else (s, c)
+            if bc_kind == 1:
+                d = self._sum(1, 0, x, y) if axis == 0 else self._sum(0, 1, x, y)
+                g2[e] = d if side else -d                     # outward normal derivative
+            elif bc_kind == 2:
+                g2[e] = self._sum(2, 0, x, y) if axis == 0 else self._sum(0, 2, x, y)
+            else:
+                raise ValueError("bc_kind must be 1 or 2")
+        return g2
+
+    def data(self, N: int, bc_kind: int):
+        return self.rhs(N), self.exact(N), self.boundary_g2(N, bc_kind)
+
+
+def sin_pi_2d() -> Manufactured2D:
+    """u = sin(pi x) sin(pi y), f = 4 pi^4 u."""
+    return Manufactured2D("sin_pi_2d", ((1.0, sin_factor(1.0), sin_factor(1.0)),))
+
+
+def exp_sum_2d() -> Manufactured2D:
+    """u = e^(x+y), f = 4u."""
+    return Manufactured2D("exp_sum_2d", ((1.0, exp_factor(), exp_factor()),))
+
+
+def polynomial_2d(cx: Sequence[float], cy: Sequence[float]) -> Manufactured2D:
+    """u = p(x) q(y) with the given coefficient lists (lowest degree first)."""
+    return Manufactured2D("poly_2d", ((1.0, poly_factor(cx), poly_factor(cy)),))
+
+
+def random_field_2d(N: int, seed: int, lo: float = -1.0, hi: float = 1.0) -> np.ndarray:
+    rng = np.random.Generator(np.random.PCG64(seed))
+    return rng.uniform(lo, hi, size=(N + 1, N + 1))
