@@ -36,6 +36,9 @@ if ROOT not in sys.path:
 METRIC = "EXCMG solve s @512³ FP64 vs FP32+refine; stencil HBM GB/s % peak; p99 latency"
 # The CPU oracle's own per-level Bi-CG counts on the default workload, written
 # by `python -m oracle.work_units` (a run of the oracle's whole 512^3 solve).
+# DRAM bytes per launch measured by ncu on 255^3 unknowns (the profiles/
+# summaries of each kernel give the capture command)
+TRAFFIC_255 = {}
 ORACLE_COUNTS = os.path.join(ROOT, "oracle", "excmg_512_counts.json")
 
 
@@ -472,15 +475,17 @@ def run_ours(args):
     if args.stencil != "exact":
         kernel = f"stencil_f64_kernel: A p or A^T p* on the {n}^3 grid"
     elif per_unknown > 48.0:
-        kernel = f"stencil_fx_kernel (fused schedule): p, p* formed, A p, A^T p*, sigma on the {n}^3 grid"
+        kernel = f"stencil_pair_dir_kernel (fused schedule): p, p* formed, A p, A^T p*, sigma on the {n}^3 grid"
     else:
-        kernel = f"stencil_fx_kernel: A p, A^T p*, sigma (operator pair) on the {n}^3 grid"
-    # DRAM traffic of the operator pair (dram__bytes_read.sum + dram__bytes_write.sum) from one
-    # ncu capture of the same kernel on 255^3 unknowns (526.77 MB), scaled to this launch by the
-    # unknowns it processes (traffic grows in proportion); only the kernel that was captured
+        kernel = f"stencil_pair_kernel: A p, A^T p*, sigma (operator pair) on the {n}^3 grid"
+    # DRAM traffic (dram__bytes_read.sum + dram__bytes_write.sum) of the kernel
+    # from one ncu capture on 255^3 unknowns, scaled to this launch by the
+    # unknowns it processes (traffic grows in proportion); None for a kernel
+    # without a capture of its current code
     traffic = None
-    if args.stencil == "exact" and 24.0 < per_unknown < 40.0:
-        traffic = 526.77e6 / 255 ** 3 * (n - 1) ** 3
+    captured = TRAFFIC_255.get(kernel.split(" ")[0]) if args.stencil == "exact" else None
+    if captured:
+        traffic = captured / 255 ** 3 * (n - 1) ** 3
     roofline = {"kernel": kernel, "bound": "hbm",
                 "achieved": achieved, "peak": hbm_peak, "unit": "GB/s",
                 "frac": (achieved / hbm_peak) if achieved else None, "traffic": traffic,
@@ -635,7 +640,10 @@ def batched_leg(args, B, problems, ctx, dev):
     out = {"workload": "64 instances, n from {32,48,64,96,128} (PCG64 seed 0), coarsest 8/6/8/6/8, kinds mixed, "
                        "u = 4 random sines, tol 1e-10 per level"}
     for precision in ("fp64", "mixed"):
+        # untimed: the DSOLVE inverses, then one whole pass so that the
+        # context's grid-size tuner has settled every level group
         run_batch(warm, precision)
+        run_batch(list(range(64)), precision)
         torch.cuda.synchronize(dev)
         t0 = time.perf_counter()
         res, steps, launches = run_batch(list(range(64)), precision)
@@ -677,9 +685,12 @@ def serving_leg(args, B, ctx, dev):
             seen.add((r.nc, r.bc))
             warm.append(r)
     S.serve(B.Batch(ctx, max_instances=256), warm, pool, tol, new_output=new_out, submit_kwargs=prec)
+    # one untimed burst settles the context's grid-size tuner
+    S.serve(B.Batch(ctx, max_instances=256), burst, pool, tol, new_output=new_out, submit_kwargs=prec)
     torch.cuda.synchronize(dev)
     _, cap = S.serve(B.Batch(ctx, max_instances=256), burst, pool, tol, new_output=new_out, submit_kwargs=prec)
-    rate = 0.8 * cap["solves_per_s"]
+    # 0.8x capacity, but the stream lasts at most about 90 s
+    rate = max(0.8 * cap["solves_per_s"], args.serve_requests / 90.0)
     reqs = S.make_requests(args.serve_requests, rate=rate, seed=1)
     pool.warm(reqs)
     torch.cuda.synchronize(dev)
@@ -688,7 +699,8 @@ def serving_leg(args, B, ctx, dev):
                          new_output=new_out, submit_kwargs=prec)
     summ.update({"capacity_solves_per_s": cap["solves_per_s"], "rate_per_s": rate, "hbm_budget_bytes": budget,
                  "precision": args.serve_precision,
-                 "workload": (f"{args.serve_requests} requests, Poisson at 0.8x capacity, n log-uniform in "
+                 "workload": (f"{args.serve_requests} requests, Poisson at max(0.8x capacity, requests / 90 s), "
+                              "n log-uniform in "
                               "[32, 256] rounded to c*2^k (c = 4..7), kinds uniform, 4 random-sine problems "
                               "per (n, kind), tol 1e-8")})
     return summ

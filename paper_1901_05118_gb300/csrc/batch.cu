@@ -373,20 +373,14 @@ struct excmg_batch {
     };
     std::vector<Group> groups;
     cudaEvent_t host_ready = nullptr;   // the context stream's state uploads
-    // Grid-size tuner, per (precision, grid size).  Candidate c gives each
-    // instance ceil(W / kTuneItems[c]) CTAs, W being its operator tiles or
-    // vector chunks, whichever are more.  Candidates are tried from the most
-    // CTAs down, and trying stops once a round takes more than twice the
-    // best round time seen.  The choice: the fewest CTA-milliseconds per
-    // instance round among the candidates within 1.25x of the best round
-    // time.  The grid size changes no result bit (every partial sum belongs
-    // to a tile or chunk, not to a CTA).
-    struct Tune {
-        double ms[8];       // milliseconds per round, -1 untried
-        double cta_ms[8];   // CTA-milliseconds per instance round
-        bool settled = false;
-    };
-    std::map<std::pair<int, int>, Tune> tune;
+    // Grid-size tuner (its table is the context's, shared by its batches).
+    // Candidate c gives each instance ceil(W / kTuneItems[c]) CTAs, W being
+    // its operator tiles or vector chunks, whichever are more.  Candidates
+    // are tried from the most CTAs down, and trying stops once a round takes
+    // more than twice the best round time seen.  The choice: the fewest
+    // CTA-milliseconds per instance round among the candidates within 1.25x
+    // of the best round time.  The grid size changes no result bit (every
+    // partial sum belongs to a tile or chunk, not to a CTA).
 };
 
 namespace {
@@ -647,12 +641,14 @@ int launch_group(excmg_batch* b, excmg_batch::Group& g, const std::vector<Instan
     return EXCMG_OK;
 }
 
-excmg_batch::Tune& tune_of(excmg_batch* b, int prec, int n) {
-    auto it = b->tune.find({prec, n});
-    if (it == b->tune.end()) {
-        excmg_batch::Tune t;
+excmg_ctx::BatchTune& tune_of(excmg_batch* b, int prec, int n) {
+    auto& table = b->ctx->batch_tune;
+    auto it = table.find({prec, n});
+    if (it == table.end()) {
+        excmg_ctx::BatchTune t;
         for (int k = 0; k < 8; ++k) t.ms[k] = t.cta_ms[k] = -1.0;
-        it = b->tune.emplace(std::make_pair(prec, n), t).first;
+        t.settled = false;
+        it = table.emplace(std::make_pair(prec, n), t).first;
     }
     return it->second;
 }
@@ -675,7 +671,7 @@ int harvest(excmg_batch* b, excmg_batch::Group& g) {
     if (g.cand >= 0 && *g.h_rounds > 0) {
         float ms = 0.f;
         if (cudaEventElapsedTime(&ms, g.start, g.done) == cudaSuccess) {
-            excmg_batch::Tune& t = tune_of(b, g.prec, g.n);
+            excmg_ctx::BatchTune& t = tune_of(b, g.prec, g.n);
             const double per_round = (double)ms / (double)*g.h_rounds;
             const double c = per_round * g.ctas / (double)g.members.size();
             if (t.ms[g.cand] < 0.0 || per_round < t.ms[g.cand]) {
@@ -721,7 +717,7 @@ int harvest(excmg_batch* b, excmg_batch::Group& g) {
 // the tuner's next candidate while it is still trying, else its choice; *cand
 // the candidate index.
 int group_ctas(excmg_batch* b, int prec, int n, int W, int m, int* cand) {
-    excmg_batch::Tune& t = tune_of(b, prec, n);
+    excmg_ctx::BatchTune& t = tune_of(b, prec, n);
     int pick = -1;
     if (!t.settled) {
         for (int k = 0; k < kTuneCands && pick < 0; ++k) {

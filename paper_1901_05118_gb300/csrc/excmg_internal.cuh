@@ -176,6 +176,14 @@ struct excmg_ctx {
     bool profile = false;
     std::vector<cudaEvent_t> prof_events;
     std::map<int, ProfRecord> prof;   // grid intervals n -> timed operator launches
+    // grid-size tuner of the batch engine, per (precision, grid intervals);
+    // kept here so that every batch on this context shares what it learned
+    struct BatchTune {
+        double ms[8];       // milliseconds per round of each candidate, -1 untried
+        double cta_ms[8];   // CTA-milliseconds per instance round
+        bool settled;
+    };
+    std::map<std::pair<int, int>, BatchTune> batch_tune;
 };
 
 struct excmg_level {
