@@ -39,7 +39,7 @@ class Manufactured:
 
     def nodes(self, fn: Callable, N: int) -> np.ndarray:
         x, y, z = self.axes(N)
-        return np.ascontiguousarray(np.broadcast_to(fn(x, y, z), (N + 1,) * 3), dtype=np.float64)
+        return np.array(np.broadcast_to(fn(x, y, z), (N + 1,) * 3), dtype=np.float64, order="C")
 
     def exact(self, N: int) -> np.ndarray:
         return self.nodes(self.u, N)
@@ -322,13 +322,13 @@ class Manufactured2D:
 
     def exact(self, N: int) -> np.ndarray:
         x, y = self.axes(N)
-        return np.ascontiguousarray(np.broadcast_to(self._sum(0, 0, x, y), (N + 1, N + 1)), dtype=np.float64)
+        return np.array(np.broadcast_to(self._sum(0, 0, x, y), (N + 1, N + 1)), dtype=np.float64, order="C")
 
     def rhs(self, N: int) -> np.ndarray:
         """f = u_xxxx + 2 u_xxyy + u_yyyy."""
         x, y = self.axes(N)
         f = self._sum(3, 0, x, y) + 2 * self._sum(2, 2, x, y) + self._sum(0, 3, x, y)
-        return np.ascontiguousarray(np.broadcast_to(f, (N + 1, N + 1)), dtype=np.float64)
+        return np.array(np.broadcast_to(f, (N + 1, N + 1)), dtype=np.float64, order="C")
 
     def boundary_g2(self, N: int, bc_kind: int) -> np.ndarray:
         s = np.arange(N + 1, dtype=np.float64) / N
