@@ -36,9 +36,10 @@ if ROOT not in sys.path:
 METRIC = "EXCMG solve s @512³ FP64 vs FP32+refine; stencil HBM GB/s % peak; p99 latency"
 # The CPU oracle's own per-level Bi-CG counts on the default workload, written
 # by `python -m oracle.work_units` (a run of the oracle's whole 512^3 solve).
-# DRAM bytes per launch measured by ncu on 255^3 unknowns (the profiles/
-# summaries of each kernel give the capture command)
-TRAFFIC_255 = {}
+# DRAM bytes (read + write) per launch measured by ncu on 255^3 unknowns
+# (python bench.py --case bicg --n 256 --iters 4 [--schedule separate]; the
+# summaries under profiles/ give the full capture commands)
+TRAFFIC_255 = {"stencil_pair_kernel": 288.93e6 + 220.17e6, "stencil_pair_dir_kernel": 582.57e6 + 489.67e6}
 ORACLE_COUNTS = os.path.join(ROOT, "oracle", "excmg_512_counts.json")
 
 
@@ -60,8 +61,8 @@ def parse(argv=None):
     ap.add_argument("--no-serve", action="store_true", help="skip the request-stream leg")
     ap.add_argument("--serve-requests", type=int, default=120)
     ap.add_argument("--no-elided", action="store_true", help="skip the shadow-elided variant leg")
-    ap.add_argument("--schedule", choices=["separate", "fused"], default="separate",
-                    help="Bi-CG operator schedule of the timed solves")
+    ap.add_argument("--schedule", choices=["separate", "fused"], default="fused",
+                    help="Bi-CG operator schedule of the timed solves on grids above 64^3")
     ap.add_argument("--serve-precision", choices=["fp64", "mixed"], default="fp64")
     ap.add_argument("--oracle-report", action="store_true",
                     help="time the CPU oracle on the small workload and one 512^3 operator application, then exit")
@@ -627,8 +628,9 @@ def batched_leg(args, B, problems, ctx, dev):
             steps += 1
         res = {i: (batch.query(ident), u) for i, (ident, u) in outs.items()}
         launches = batch.launches
+        prof = batch.profile()
         batch.close()
-        return res, steps + 1, launches
+        return res, steps + 1, launches, prof
 
     # warm-up: one instance of every (coarsest, kind) builds the DSOLVE inverses
     seen, warm = set(), []
@@ -646,7 +648,7 @@ def batched_leg(args, B, problems, ctx, dev):
         run_batch(list(range(64)), precision)
         torch.cuda.synchronize(dev)
         t0 = time.perf_counter()
-        res, steps, launches = run_batch(list(range(64)), precision)
+        res, steps, launches, prof = run_batch(list(range(64)), precision)
         torch.cuda.synchronize(dev)
         t_batch = time.perf_counter() - t0
         t0 = time.perf_counter()
@@ -658,7 +660,8 @@ def batched_leg(args, B, problems, ctx, dev):
         t_seq = time.perf_counter() - t0
         diff = max(float((res[i][1] - seq[i]).abs().max() / seq[i].abs().max()) for i in range(64))
         out[precision] = {"batched_s": t_batch, "solves_per_s": 64 / t_batch, "engine_steps": steps,
-                          "launches": launches, "sequential_s": t_seq, "speedup_vs_sequential": t_seq / t_batch,
+                          "launches": launches, "engine_profile": prof,
+                          "sequential_s": t_seq, "speedup_vs_sequential": t_seq / t_batch,
                           "max_rel_diff_vs_sequential": diff,
                           "all_ok": all(res[i][0]["done"] and res[i][0]["status"] == 0 for i in range(64))}
     return out

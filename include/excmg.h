@@ -134,21 +134,17 @@ int excmg_ctx_set_stencil(excmg_ctx *ctx, int variant);
 enum { EXCMG_SHADOW_FULL = 0, EXCMG_SHADOW_ELIDED = 1 };
 int excmg_ctx_set_shadow_mode(excmg_ctx *ctx, int mode);
 
-/* How a Bi-CG iteration is split into kernels (integer operator); both give
- * the same iterates up to the reduction order of sigma (same bits within
- * one schedule).
- * EXCMG_SCHEDULE_SEPARATE (default): operator pair (A p, A^T p*, sigma,
- *   alpha), update (x, r, r*, rho, beta) and direction update (p, p*) as
- *   three launches on grids above 64^3 (152 bytes per unknown), a three-phase
- *   cooperative launch on smaller ones.
- * EXCMG_SCHEDULE_FUSED: the operator launch first forms p = r + beta p and
- *   p* from the previous directions (recomputed on each block's halo, input
- *   rows staged in shared memory by bulk copies), then applies A and A^T:
- *   two launches, 136 bytes per unknown.  Measured slower on GB300 (4.0 ms
- *   per fused launch against 2.8 ms for the separate operator pair and
- *   direction update at 512^3; 0.254 s against 0.203 s per 512^3 solve):
- *   the halo recomputation and the barrier stalls of the staged march cost
- *   more than the saved pass. */
+/* How a Bi-CG iteration is split into kernels on grids above 64^3 (integer
+ * operator); both give the same iterates up to the reduction order of sigma
+ * (same bits within one schedule).  Grids up to 64^3 run a three-phase
+ * cooperative launch in both.
+ * EXCMG_SCHEDULE_FUSED (default): the operator launch first forms
+ *   p = r + beta p and p* = r* + beta p* from the previous directions on
+ *   every node it loads (writing the nodes it owns into a second buffer
+ *   pair), then applies A and A^T with sigma and alpha; with the update
+ *   (x, r, r*, rho, beta) that makes two launches and 136 bytes per unknown.
+ * EXCMG_SCHEDULE_SEPARATE: operator pair (A p, A^T p*, sigma, alpha), update
+ *   and direction update (p, p*) as three launches, 152 bytes per unknown. */
 enum { EXCMG_SCHEDULE_SEPARATE = 0, EXCMG_SCHEDULE_FUSED = 1 };
 int excmg_ctx_set_schedule(excmg_ctx *ctx, int schedule);
 
@@ -291,10 +287,11 @@ int excmg_dsolve(const excmg_level *level, const double *fh, double *u);
  * one context's GPU and stream, each in FP64 (integer operator, FP64 Bi-CG)
  * or in the mixed-precision form (FP64 refinement around FP32 Bi-CG
  * correction solves, see EXCMG_PRECISION_MIXED).  Every instance keeps its
- * level hierarchy resident; the Bi-CG iterations of all instances that need
- * them run together in one cooperative launch per value type and
- * excmg_batch_step.  Instances may be submitted at
- * any time and leave when done, so the batch refills continuously. */
+ * level hierarchy resident; the Bi-CG iterations of the instances that need
+ * them run in one cooperative launch per level group (instances of one
+ * precision at one grid size), each group on its own stream and taken back
+ * as soon as it completes.  Instances may be submitted at any time and leave
+ * when done, so the batch refills continuously. */
 typedef struct excmg_batch excmg_batch;
 
 /* hbm_budget_bytes caps the device memory all live instances may hold
@@ -329,6 +326,22 @@ int excmg_batch_query(excmg_batch *batch, int id, int *done, int *status, excmg_
                       double *latency_s);
 /* Kernel launches made by the batch so far. */
 long long excmg_batch_launches(const excmg_batch *batch);
+
+/* Where a batch's time went, summed since it was created: its cooperative
+ * Bi-CG launches (one per level group and step), their rounds, rounds times
+ * members (member slots, busy or idle), member iterations actually taken,
+ * the launches' device time (CUDA events on their streams), and the wall
+ * time of excmg_batch_step outside / inside its wait for a running launch. */
+typedef struct {
+    long long group_launches;
+    long long rounds;
+    long long member_rounds;
+    long long member_iters;
+    double group_ms;
+    double host_s;
+    double wait_s;
+} excmg_batch_profile;
+int excmg_batch_get_profile(const excmg_batch *batch, excmg_batch_profile *out);
 
 /* ------------------------------------------------------- the 2D problem */
 
@@ -371,11 +384,10 @@ int excmg2d_solve(excmg_ctx *ctx, int n_finest, int n_coarsest, int bc_kind, con
 /* Failure-path self-test (the paper has no counterpart): makes one of the
  * library's bounded device-side waits run out on purpose -- without a fault,
  * trap or hang -- so that the path that reports EXCMG_ERR_TIMEOUT can be
- * tested.  which = 0: the grid barrier of the cooperative kernels; a
- * cooperative launch of 8 CTAs waits for a ninth arrival that never comes,
- * and each CTA gives up after `limit` polls (at least 32 ns each).
- * which = 1: the mbarrier wait of the staged loads; one arrival of two, and
- * the wait gives up after `limit` nanoseconds.  1 <= limit <= 10^8.
+ * tested.  which = 0 (the only wait kind): the grid barrier of the
+ * cooperative kernels; a cooperative launch of 8 CTAs waits for a ninth
+ * arrival that never comes, and each CTA gives up after `limit` polls (at
+ * least 32 ns each).  1 <= limit <= 10^8.
  * Returns EXCMG_ERR_TIMEOUT when the wait gave up as designed, EXCMG_OK if it
  * did not (the mechanism failed), EXCMG_ERR_ARG, or EXCMG_ERR_CUDA.  Uses
  * fixed device memory (allocates nothing), runs on the legacy default stream

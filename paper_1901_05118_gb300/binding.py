@@ -110,6 +110,15 @@ _lib.excmg_batch_query.argtypes = [_vp, _i, ctypes.POINTER(_i), ctypes.POINTER(_
                                    ctypes.POINTER(_d)]
 _lib.excmg_batch_launches.argtypes = [_vp]
 _lib.excmg_batch_launches.restype = ctypes.c_longlong
+
+
+class BatchProfile(ctypes.Structure):
+    _fields_ = [("group_launches", ctypes.c_longlong), ("rounds", ctypes.c_longlong),
+                ("member_rounds", ctypes.c_longlong), ("member_iters", ctypes.c_longlong),
+                ("group_ms", ctypes.c_double), ("host_s", ctypes.c_double), ("wait_s", ctypes.c_double)]
+
+
+_lib.excmg_batch_get_profile.argtypes = [_vp, ctypes.POINTER(BatchProfile)]
 _lib.excmg_selftest_wait_timeout.argtypes = [_i, ctypes.c_longlong]
 _lib.excmg_selftest_wait_timeout.restype = _i
 _lib.excmg2d_stencil_apply.argtypes = [_vp, _i, _i, _i, _vp, _vp]
@@ -146,9 +155,9 @@ def launch_count() -> int:
 
 def selftest_wait_timeout(which: str, limit: int) -> int:
     """Make a bounded device wait run out on purpose ('barrier': the grid
-    barrier, limit in polls; 'mbarrier': the staged-load wait, limit in ns).
-    Returns the library status (-7, EXCMG_ERR_TIMEOUT, when it gave up)."""
-    return int(_lib.excmg_selftest_wait_timeout({"barrier": 0, "mbarrier": 1}[which], int(limit)))
+    barrier of the cooperative kernels, limit in polls).  Returns the library
+    status (-7, EXCMG_ERR_TIMEOUT, when it gave up)."""
+    return int(_lib.excmg_selftest_wait_timeout({"barrier": 0}[which], int(limit)))
 
 
 # ----------------------------------------------------------------- checks
@@ -421,6 +430,12 @@ class Batch:
     @property
     def launches(self) -> int:
         return int(_lib.excmg_batch_launches(self.handle))
+
+    def profile(self) -> dict:
+        """Counters of the batch's cooperative Bi-CG launches and step times."""
+        pr = BatchProfile()
+        self._check(_lib.excmg_batch_get_profile(self.handle, ctypes.byref(pr)), "excmg_batch_get_profile")
+        return {k: getattr(pr, k) for k, _ in BatchProfile._fields_}
 
     def submit(self, n_finest: int, n_coarsest: int, bc_kind: int, f: torch.Tensor, g1: torch.Tensor,
                g2: torch.Tensor, tol: float, u_out: torch.Tensor | None = None, *, tol_mode: str = "uniform",

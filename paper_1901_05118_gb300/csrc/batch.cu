@@ -303,6 +303,7 @@ struct Instance {
     Phase phase = kSetup;
     int level = 0;
     int iters = 0, outer = 0, bad = 0, stag = 0;
+    int call_iter = 0;         // iterations of the current Bi-CG call taken back so far
     double fnorm = 0.0, rel = 0.0, prev = 0.0, scale = 0.0;
     int status = EXCMG_OK;
     excmg_stats stats{};
@@ -354,6 +355,7 @@ struct excmg_batch {
     int inner_chunk = 256;       // iterations per batched launch
     std::string last_error;
     long long launches = 0;
+    excmg_batch_profile prof{};
     std::vector<int> free_slots;
     // One cooperative launch per level group (instances of one precision at
     // one grid size), each on its own stream with its own tables, partial
@@ -668,9 +670,22 @@ int harvest(excmg_batch* b, excmg_batch::Group& g) {
     g.busy = false;
     for (Instance* in : g.members) in->in_flight = false;
     if (*g.h_active < 0) return bfail(b, EXCMG_ERR_TIMEOUT, "grid barrier of the batched Bi-CG gave up");
+    float ms = 0.f;
+    if (cudaEventElapsedTime(&ms, g.start, g.done) != cudaSuccess) {
+        cudaGetLastError();
+        ms = -1.f;
+    }
+    b->prof.group_launches += 1;
+    b->prof.rounds += *g.h_rounds;
+    b->prof.member_rounds += (long long)*g.h_rounds * (long long)g.members.size();
+    if (ms >= 0.f) b->prof.group_ms += ms;
+    for (Instance* in : g.members) {
+        const BatchState& hs = b->h_states[in->slot];
+        b->prof.member_iters += hs.iter - in->call_iter;
+        in->call_iter = hs.iter;
+    }
     if (g.cand >= 0 && *g.h_rounds > 0) {
-        float ms = 0.f;
-        if (cudaEventElapsedTime(&ms, g.start, g.done) == cudaSuccess) {
+        if (ms >= 0.f) {
             excmg_ctx::BatchTune& t = tune_of(b, g.prec, g.n);
             const double per_round = (double)ms / (double)*g.h_rounds;
             const double c = per_round * g.ctas / (double)g.members.size();
@@ -685,8 +700,6 @@ int harvest(excmg_batch* b, excmg_batch::Group& g) {
                 else if (best < 0.0 || t.ms[k] < best) best = t.ms[k];
             }
             if (all || per_round > 2.0 * best) t.settled = true;
-        } else {
-            cudaGetLastError();
         }
     }
     for (Instance* in : g.members) {
@@ -931,6 +944,7 @@ int excmg_batch_submit(excmg_batch* b, int n_finest, int n_coarsest, int bc_kind
 // running group.  *n_live receives the number of instances still running.
 int excmg_batch_step(excmg_batch* b, int* n_live) {
     if (!b) return EXCMG_ERR_ARG;
+    const double t_enter = now_s();
     excmg_ctx* ctx = b->ctx;
     cudaStream_t s = ctx->stream;
     int st = EXCMG_OK;
@@ -1059,6 +1073,7 @@ int excmg_batch_step(excmg_batch* b, int* n_live) {
             }
             if (e != cudaSuccess) return bcuda(b, e, "Bi-CG call setup");
             in->phase = kInner;
+            in->call_iter = 0;
         }
     }
     // 3. one cooperative launch per level group of instances waiting for
@@ -1140,6 +1155,8 @@ int excmg_batch_step(excmg_batch* b, int* n_live) {
         if (!in->in_flight && (in->phase == kSetup || in->phase == kResidual)) host_work = true;
     bool any_busy = false;
     for (auto& g : b->groups) any_busy = any_busy || g.busy;
+    const double t_wait = now_s();
+    b->prof.host_s += t_wait - t_enter;
     if (any_busy && !host_work) {
         for (;;) {
             bool one = false;
@@ -1150,6 +1167,7 @@ int excmg_batch_step(excmg_batch* b, int* n_live) {
             std::this_thread::yield();
         }
     }
+    b->prof.wait_s += now_s() - t_wait;
     if (n_live) *n_live = (int)b->live.size();
     return EXCMG_OK;
 }
@@ -1176,5 +1194,11 @@ int excmg_batch_query(excmg_batch* b, int id, int* done, int* status, excmg_stat
 }
 
 long long excmg_batch_launches(const excmg_batch* b) { return b ? b->launches : 0; }
+
+int excmg_batch_get_profile(const excmg_batch* b, excmg_batch_profile* out) {
+    if (!b || !out) return EXCMG_ERR_ARG;
+    *out = b->prof;
+    return EXCMG_OK;
+}
 
 }  // extern "C"

@@ -41,8 +41,7 @@ struct BicgState {
     int done;          // 1 once converged, capped or broken down
     int status;        // kRunning / kConverged / kCapped / kBreakdown
     unsigned int ticket;   // last-block counter of the reductions
-    int fault;         // set by a kernel whose bounded wait for a copy gave up
-    int pad1[2];
+    int pad1[3];
 };
 enum { kRunning = 0, kConverged = 1, kCapped = 2, kBreakdown = 3, kTimeout = 4 };
 
@@ -67,17 +66,13 @@ cudaError_t launch_bicg_stencil_pair_dir(const double* r, const double* rs, cons
                                          const double* ps_prev, double* p, double* ps, double* q, double* qs, int n,
                                          int bc_kind, double* partials, BicgState* st, cudaStream_t s);
 // Small grids: whole Bi-CG iterations (up to `iters`) in one cooperative
-// launch with bounded grid barriers; barrier_words: 3 device words.  Unless
-// persistent_pointwise(n), the directions alternate between (p, ps) and
-// (p2, ps2), whose boundary entries must be zero; p, ps must hold p_0 on
-// entry (iteration k reads p_{k-1} from one pair, writes p_k to the other).
+// launch with bounded grid barriers; barrier_words: 3 device words.
 constexpr int kPersistentMaxN = 64;
 bool persistent_pointwise(int n);
-// elide: the shadow-elided mode (rs, ps, ps2, qs unused, may be null).
-cudaError_t launch_bicg_persistent(double* x, double* r, double* rs, double* p, double* ps, double* p2, double* ps2,
-                                   double* q, double* qs, int n, int bc_kind, int iters, double* partials,
-                                   BicgState* st, unsigned int* barrier_words, cudaStream_t s, bool elide,
-                                   bool fuse);
+// elide: the shadow-elided mode (rs, ps, qs unused, may be null).
+cudaError_t launch_bicg_persistent(double* x, double* r, double* rs, double* p, double* ps, double* q, double* qs,
+                                   int n, int bc_kind, int iters, double* partials, BicgState* st,
+                                   unsigned int* barrier_words, cudaStream_t s, bool elide);
 // Shadow-elided mode (r* = r, p* = p, A^T p* = A p not stored): the one-field
 // operator launches with sigma = (p, A p) and alpha (the second also forms
 // p = r + beta p_prev into p), and the matching set-up and update kernels.
@@ -166,7 +161,7 @@ struct excmg_ctx {
     double* host_scalar = nullptr;            // pinned host mirror of `scalar`
     int stencil_variant = excmg::kStencilExact;
     int shadow_mode = EXCMG_SHADOW_FULL;
-    int schedule = EXCMG_SCHEDULE_SEPARATE;
+    int schedule = EXCMG_SCHEDULE_FUSED;
     // CUDA graphs of full batches of launched Bi-CG iterations, keyed by the
     // grid size, the variant flags and the buffers they use (bicg.cu)
     bool graphs = true;

@@ -93,94 +93,7 @@ struct FxFields {
     const double* dr[2];
     double* pn[2];
     double beta;
-    // staged loads: shared-memory stages (fx_stage_bytes) and a device word
-    // set to 1 when a bounded wait for a copy gave up
-    unsigned char* stage;
-    int* fault;
 };
-
-// ---------------------------------------------------------------------------
-// Staged loads (kBulk).  The CTA's input rows of the next planes are brought
-// into shared memory by the bulk-copy engine while the current plane is
-// computed, so the plane loop does not wait for DRAM.  Rows hold n + 1
-// doubles; n is even on every level of the method, so a row's byte pitch is
-// not a multiple of 16 and no tiled tensor map describes the grid.  Each
-// halo row (36 doubles from x = i0 - 2) is therefore one untiled bulk copy
-// of FX_ROW doubles starting at the 16-byte boundary at or below it; readers
-// add that row's shift (0 or 1 element).  Only rows and planes inside the
-// interior are copied (the rest reads as zero, as in the direct loads); all
-// copied bytes lie inside the grid array for n >= 16.  Each stage has one
-// mbarrier that the copies of one plane complete.
-constexpr int FX_ROW = 40;   // 320 B: 36 needed + shift, a multiple of 16 B
-template <int NL, int S>
-__host__ __device__ constexpr size_t fx_stage_bytes() {
-    return (size_t)S * NL * FX_HY * FX_ROW * sizeof(double) + 128;   // + mbarriers
-}
-__host__ __device__ constexpr int fx_stages(bool dir) { return dir ? 2 : 3; }
-
-__device__ __forceinline__ unsigned smem_u32(const void* p) {
-    return (unsigned)__cvta_generic_to_shared(p);
-}
-
-__device__ __forceinline__ void mbar_init(unsigned long long* bar, unsigned count) {
-    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(bar)), "r"(count) : "memory");
-}
-
-__device__ __forceinline__ void mbar_arrive_tx(unsigned long long* bar, unsigned tx) {
-    unsigned long long state;
-    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 %0, [%1], %2;"
-                 : "=l"(state) : "r"(smem_u32(bar)), "r"(tx) : "memory");
-    (void)state;
-}
-
-__device__ __forceinline__ void mbar_arrive(unsigned long long* bar) {
-    unsigned long long state;
-    asm volatile("mbarrier.arrive.shared::cta.b64 %0, [%1];" : "=l"(state) : "r"(smem_u32(bar)) : "memory");
-    (void)state;
-}
-
-__device__ __forceinline__ bool mbar_try_wait(unsigned long long* bar, unsigned parity) {
-    unsigned ok;
-    asm volatile(
-        "{\n\t.reg .pred p;\n\t"
-        "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
-        "selp.u32 %0, 1, 0, p;\n\t}"
-        : "=r"(ok) : "r"(smem_u32(bar)), "r"(parity) : "memory");
-    return ok != 0;
-}
-
-__device__ __forceinline__ void mbar_inval(unsigned long long* bar) {
-    asm volatile("mbarrier.inval.shared::cta.b64 [%0];" ::"r"(smem_u32(bar)) : "memory");
-}
-
-__device__ __forceinline__ unsigned long long global_ns() {
-    unsigned long long t;
-    asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
-    return t;
-}
-
-// Wait for the phase with the given parity for at most limit_ns
-// nanoseconds; false when it gave up.
-__device__ __forceinline__ bool mbar_wait(unsigned long long* bar, unsigned parity, unsigned long long limit_ns) {
-    if (mbar_try_wait(bar, parity)) return true;
-    const unsigned long long t0 = global_ns();
-    do {
-        if (mbar_try_wait(bar, parity)) return true;
-    } while (global_ns() - t0 < limit_ns);
-    return false;
-}
-constexpr unsigned long long kStageWaitNs = 50000000ull;   // 50 ms: copies take microseconds
-constexpr unsigned long long kStageDrainNs = 1000000ull;   // 1 ms once a wait has given up
-
-__device__ __forceinline__ void bulk_g2s(void* dst, const void* src, unsigned bytes, unsigned long long* bar) {
-    asm volatile(
-        "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];"
-        ::"r"(smem_u32(dst)), "l"(src), "r"(bytes), "r"(smem_u32(bar)) : "memory");
-}
-
-__device__ __forceinline__ void fence_async_smem() {
-    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
-}
 
 // Rare cases (a non-finite input, or a scale outside the normal range of the
 // fast conversion) leave the hot path through a call, so that the compiler
@@ -198,7 +111,7 @@ __device__ __forceinline__ double fx_result(long long acc, int E, bool poisoned)
 // One CTA's z-march over the output columns of tile (bx, by) and the output
 // planes [kz0, kz1).  Returns this thread's share of (field 1 in, field 0
 // out) when kDot.  Called uniformly by all threads of the CTA.
-template <int NF, bool kDot, bool kDir = false, bool kBulk = false>
+template <int NF, bool kDot, bool kDir = false>
 __device__ __forceinline__ double fx_march(const FxFields& fl, const double* __restrict__ b, int n, int sigma,
                                            int bx, int by, int kz0, int kz1) {
     __shared__ long long tile[NF][FX_HY * FX_HX];
@@ -235,69 +148,6 @@ __device__ __forceinline__ double fx_march(const FxFields& fl, const double* __r
     const int c1 = cx + (ja + 1 == 1) + (ja + 1 == n - 1);
     const int ry = ty * FX_RY + 2, rx = tx + 2;   // tile coordinates of the first output
 
-    // staged loads: arrays copied per plane (kDir: p, r, p*, r*), stages
-    constexpr int NL = kDir ? 2 * NF : NF;
-    constexpr int S = fx_stages(kDir);
-    double* raw = reinterpret_cast<double*>(fl.stage);
-    unsigned long long* bar =
-        reinterpret_cast<unsigned long long*>(fl.stage + (size_t)S * NL * FX_HY * FX_ROW * sizeof(double));
-    const double* src[NL];
-    if (kBulk) {
-#pragma unroll
-        for (int a = 0; a < NL; ++a) src[a] = kDir ? ((a & 1) ? fl.dr[a >> 1] : fl.in[a >> 1]) : fl.in[a];
-    }
-    // rows of the halo inside the interior, and this thread's row shifts
-    const int row_lo = max(0, 1 - (j0 - 2)), row_hi = min(FX_HY, n - 1 - (j0 - 2) + 1);
-    const unsigned plane_tx = kBulk ? (unsigned)(max(0, row_hi - row_lo) * NL * FX_ROW * sizeof(double)) : 0u;
-    int rpar[FX_SLOTS], rbase[FX_SLOTS];   // row parity at plane 0, staged row offset
-#pragma unroll
-    for (int r = 0; r < FX_SLOTS; ++r) {
-        rpar[r] = 0;
-        rbase[r] = 0;
-        if (kBulk && sidx[r] >= 0) {
-            const int ly = sidx[r] / FX_HX, lx = sidx[r] - ly * FX_HX;
-            const long long L = (long long)(j0 - 2 + ly) * np + (i0 - 2);
-            rpar[r] = (int)(L & 1);
-            rbase[r] = ly * FX_ROW + lx;
-        }
-    }
-    const int plane_par = (int)(plane & 1);
-    const int T = kz1 - kz0 + 4;   // planes zin = kz0 - 2 .. kz1 + 1
-    bool stalled = false;
-    // copy plane t of the march into stage t % S (warp 0)
-    auto issue = [&](int t) {
-        if (t >= T || tid >= 32) return;
-        const int zin = kz0 - 2 + t;
-        unsigned long long* bt = bar + (t % S);
-        const bool load = zin >= 1 && zin <= n - 1 && plane_tx > 0;
-        // the stage was last read through ordinary loads: order those reads
-        // before the copy engine's writes
-        fence_async_smem();
-        if (lane == 0) {
-            if (load) mbar_arrive_tx(bt, plane_tx);
-            else mbar_arrive(bt);
-        }
-        __syncwarp();
-        if (load && lane >= row_lo && lane < row_hi) {
-            const long long L = ((long long)zin * np + (j0 - 2 + lane)) * np + (i0 - 2);
-            const long long La = L & ~1ll;
-            double* dst = raw + ((size_t)(t % S) * NL * FX_HY + lane) * FX_ROW;
-#pragma unroll
-            for (int a = 0; a < NL; ++a)
-                bulk_g2s(dst + (size_t)a * FX_HY * FX_ROW, src[a] + La, FX_ROW * sizeof(double), bt);
-        }
-    };
-    if (kBulk) {
-        if (tid == 0) {
-#pragma unroll
-            for (int k = 0; k < S; ++k) mbar_init(bar + k, 1);
-            asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
-        }
-        __syncthreads();
-#pragma unroll
-        for (int t = 0; t < S - 1; ++t) issue(t);
-    }
-
     long long acc[NF][FX_RY][5];
     int E[NF];
     bool poisoned[NF];
@@ -322,26 +172,6 @@ __device__ __forceinline__ double fx_march(const FxFields& fl, const double* __r
         const size_t zbase = zok ? (size_t)zin * plane : 0;
         double v[NF][FX_SLOTS];
         bool same = true;
-        // staged input of this plane: element (array a, slot r)
-        const int t = zin - (kz0 - 2);
-        const double* stg = raw + (size_t)(t % S) * NL * FX_HY * FX_ROW;
-        const int zpar = plane_par & zin;
-        auto staged = [&](int a, int r) {
-            return stg[(size_t)a * FX_HY * FX_ROW + rbase[r] + (rpar[r] ^ zpar)];
-        };
-        if (kBulk) {
-            // the stage that plane t - 1 used is free again (every thread
-            // passed the barriers after reading it): refill it
-            issue(t + S - 1);
-            const unsigned par = (unsigned)((t / S) & 1);
-            if (!mbar_wait(bar + (t % S), par, stalled ? kStageDrainNs : kStageWaitNs)) {
-                // a copy did not arrive: flag the launch, wait once more
-                // (briefly) for the copies in flight, carry on with what is
-                // there; later waits of this CTA are short
-                stalled = true;
-                mbar_wait(bar + (t % S), par, kStageDrainNs);
-            }
-        }
         if (kDir) {
             // p = r + beta p, p* = r* + beta p* on every loaded node; where
             // r*, p* equal r, p bit for bit, p* takes p's bits
@@ -351,12 +181,12 @@ __device__ __forceinline__ double fx_march(const FxFields& fl, const double* __r
                 double pv = 0.0, psv = 0.0;
                 if (zok && soff[r] >= 0) {
                     const size_t o = zbase + soff[r];
-                    const double rv = kBulk ? staged(1, r) : fl.dr[0][o];
-                    const double po = kBulk ? staged(0, r) : fl.in[0][o];
+                    const double rv = fl.dr[0][o];
+                    const double po = fl.in[0][o];
                     pv = rv + fl.beta * po;
                     if (NF == 2) {
-                        const double rsv = kBulk ? staged(NL - 1, r) : fl.dr[NF - 1][o];
-                        const double pso = kBulk ? staged(NL - 2, r) : fl.in[NF - 1][o];
+                        const double rsv = fl.dr[NF - 1][o];
+                        const double pso = fl.in[NF - 1][o];
                         if (__double_as_longlong(rsv) == __double_as_longlong(rv) &&
                             __double_as_longlong(pso) == __double_as_longlong(po))
                             psv = pv;
@@ -376,7 +206,7 @@ __device__ __forceinline__ double fx_march(const FxFields& fl, const double* __r
             for (int f = 0; f < NF; ++f)
 #pragma unroll
                 for (int r = 0; r < FX_SLOTS; ++r)
-                    v[f][r] = (zok && soff[r] >= 0) ? (kBulk ? staged(f, r) : fl.in[f][zbase + soff[r]]) : 0.0;
+                    v[f][r] = (zok && soff[r] >= 0) ? fl.in[f][zbase + soff[r]] : 0.0;
         }
         if (NF == 2) {
 #pragma unroll
@@ -542,16 +372,6 @@ __device__ __forceinline__ double fx_march(const FxFields& fl, const double* __r
                 acc[f][q][3] = acc[f][q][4];
                 acc[f][q][4] = 0;
             }
-        }
-    }
-    if (kBulk) {
-        if (stalled) atomicExch(fl.fault, 1);
-        // every thread has passed its last wait (the plane loop ends with
-        // barriers): release the mbarriers, which a caller marching another
-        // tile in the same launch initialises again
-        if (tid == 0) {
-#pragma unroll
-            for (int k = 0; k < S; ++k) mbar_inval(bar + k);
         }
     }
     return dot;

@@ -76,6 +76,9 @@ __device__ __forceinline__ int pp_slot(int tid, int s) {
     return (2 + (k >> 2)) * PP_HX + (c < 2 ? c : PP_HX - 4 + c);
 }
 
+// 32-bit shared-memory address of a generic pointer into shared memory
+__device__ __forceinline__ unsigned smem_u32(const void* p) { return (unsigned)__cvta_generic_to_shared(p); }
+
 __device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;" ::: "memory"); }
 template <int N>
 __device__ __forceinline__ void cp_async_wait() {

@@ -1,12 +1,10 @@
 // Failure-path self-test: make one of the library's bounded device-side
 // waits run out on purpose, without a fault, trap or hang, so that the path
 // that turns a wait that gave up into EXCMG_ERR_TIMEOUT can be tested.  The
-// waits are the ones the kernels use (grid_sync of the cooperative kernels,
-// mbar_wait of the staged loads); only the arrival they wait for is one that
-// nothing makes.
+// wait is the one the cooperative kernels use (grid_sync); only the arrival
+// it waits for is one that nothing makes.
 #include "excmg_internal.cuh"
 #include "grid_sync.cuh"
-#include "march_fx.cuh"
 
 namespace excmg {
 namespace {
@@ -25,27 +23,13 @@ __global__ void barrier_timeout_kernel(GridBarrier gb) {
     if (blockIdx.x == 0 && threadIdx.x == 0) g_selftest_status = ok ? kConverged : kTimeout;
 }
 
-// One CTA: an mbarrier that expects two arrivals gets one, and thread 0
-// waits for its phase to complete for at most limit_ns nanoseconds.
-__global__ void mbarrier_timeout_kernel(unsigned long long limit_ns) {
-    __shared__ unsigned long long bar;
-    if (threadIdx.x == 0) mbar_init(&bar, 2);
-    __syncthreads();
-    if (threadIdx.x == 0) {
-        mbar_arrive(&bar);
-        const bool ok = mbar_wait(&bar, 0u, limit_ns);
-        g_selftest_status = ok ? kConverged : kTimeout;
-        mbar_inval(&bar);
-    }
-}
-
 }  // namespace
 }  // namespace excmg
 
 using namespace excmg;
 
 extern "C" int excmg_selftest_wait_timeout(int which, long long limit) {
-    if ((which != 0 && which != 1) || limit < 1 || limit > 100000000ll) return EXCMG_ERR_ARG;
+    if (which != 0 || limit < 1 || limit > 100000000ll) return EXCMG_ERR_ARG;
     void* words = nullptr;
     void* status = nullptr;
     cudaError_t e = cudaGetSymbolAddress(&words, g_selftest_barrier);
@@ -53,16 +37,11 @@ extern "C" int excmg_selftest_wait_timeout(int which, long long limit) {
     if (e == cudaSuccess) e = cudaMemsetAsync(words, 0, sizeof(g_selftest_barrier), nullptr);
     if (e == cudaSuccess) e = cudaMemsetAsync(status, 0xFF, sizeof(int), nullptr);
     if (e == cudaSuccess) {
-        if (which == 0) {
-            unsigned int* w = (unsigned int*)words;
-            GridBarrier gb{w, w + 1, (int*)(w + 2), limit};
-            void* args[] = {&gb};
-            e = cudaLaunchCooperativeKernel((const void*)barrier_timeout_kernel, dim3(kSelftestCtas), dim3(32), args,
-                                            0, nullptr);
-        } else {
-            mbarrier_timeout_kernel<<<1, 32>>>((unsigned long long)limit);
-            e = cudaGetLastError();
-        }
+        unsigned int* w = (unsigned int*)words;
+        GridBarrier gb{w, w + 1, (int*)(w + 2), limit};
+        void* args[] = {&gb};
+        e = cudaLaunchCooperativeKernel((const void*)barrier_timeout_kernel, dim3(kSelftestCtas), dim3(32), args, 0,
+                                        nullptr);
         note_launches(1);
     }
     int out = -1;

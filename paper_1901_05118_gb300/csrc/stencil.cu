@@ -98,52 +98,22 @@ stencil_f64_kernel(const double* __restrict__ u, double* __restrict__ y, const d
     }
 }
 
-// Three CTAs per SM (at most 85 registers): the march waits on each plane's
-// loads, and 24 resident warps hide more of that latency than 16 (measured
-// 1.83 ms against 2.11 ms per operator pair at 512^3, despite a few bytes of
-// spilled state).
-template <int NF, bool kDot, bool kDir = false, bool kBulk = false>
+// y = A u (or y = b - A u): the single-field march of march_fx.cuh, three
+// CTAs per SM (the march waits on each plane's loads, and 24 resident warps
+// hide more of that latency than 16).
 __global__ void __launch_bounds__(FX_NT, 3)
 stencil_fx_kernel(FxFields fl, const double* __restrict__ b, int n, int sigma, int kz_per_cta,
-                  const int* __restrict__ skip, double* partials, BicgState* st) {
-    extern __shared__ __align__(128) unsigned char fx_stage_smem[];
+                  const int* __restrict__ skip) {
     if (skip != nullptr && *skip) return;
     const int kz0 = 1 + blockIdx.z * kz_per_cta;
     const int kz1 = min(kz0 + kz_per_cta, n);
-    if (kDir) fl.beta = st->beta;
-    if (kBulk) {
-        fl.stage = fx_stage_smem;
-        fl.fault = &st->fault;
-    }
-    const double dot = fx_march<NF, kDot, kDir, kBulk>(fl, b, n, sigma, blockIdx.x, blockIdx.y, kz0, kz1);
-    if (kDot) {
-        __shared__ double sh[32];
-        __shared__ bool am_last;
-        double sdot = block_sum(dot, sh);
-        if (publish_partials(&sdot, 1, partials, &st->ticket, &am_last)) {
-            const double sg = gather_partials(partials, 0, sh);
-            if (thread0()) {
-                const double rho = st->rho;
-                st->sigma = sg;
-                if (kBulk && *(volatile int*)&st->fault) {
-                    st->status = kTimeout;
-                    st->done = 1;
-                } else if (!(rho != 0.0 && isfinite(rho)) || !(sg != 0.0 && isfinite(sg))) {
-                    st->status = kBreakdown;
-                    st->done = 1;
-                } else {
-                    st->alpha = rho / sg;
-                }
-                st->ticket = 0;
-            }
-        }
-    }
+    (void)fx_march<1, false>(fl, b, n, sigma, blockIdx.x, blockIdx.y, kz0, kz1);
 }
 
 // The operator launch of the default Bi-CG schedule on grids above 64^3:
 // q = A p, q* = A^T p*, sigma = (p*, q) and alpha = rho / sigma (Alg. 2),
 // with the copy-ahead march of march_pair.cuh (bit for bit the results of
-// stencil_fx_kernel<2, true>).  A CTA whose slab holds a node where p*
+// fx_march<2, true>).  A CTA whose slab holds a node where p*
 // differs from p (a caller-chosen r*_0) runs the general two-field march
 // instead.  kElide: the shadow-elided mode (p only, q only; the same sums).
 constexpr bool kPairCvt = true;   // outputs rounded by the hardware conversion
@@ -151,7 +121,7 @@ constexpr bool kPairCvt = true;   // outputs rounded by the hardware conversion
 // the general two-field march, kept out of line: it runs only where p* != p
 __device__ __noinline__ double pair_two_field(const double* p, const double* ps, double* q, double* qs, int n,
                                               int sigma, int bx, int by, int kz0, int kz1) {
-    const FxFields fl{{p, ps}, {q, qs}, {nullptr, nullptr}, {nullptr, nullptr}, 0.0, nullptr, nullptr};
+    const FxFields fl{{p, ps}, {q, qs}, {nullptr, nullptr}, {nullptr, nullptr}, 0.0};
     return fx_march<2, true>(fl, nullptr, n, sigma, bx, by, kz0, kz1);
 }
 
@@ -198,12 +168,12 @@ stencil_pair_kernel(const double* __restrict__ p, const double* __restrict__ ps,
 // The fused schedule's operator launch: p = r + beta p_prev (and p*) formed
 // on every loaded node, the nodes the CTA owns written to (pn, psn), then
 // q = A p, q* = A^T p*, sigma and alpha, with the copy-ahead march (bit for
-// bit the results of stencil_fx_kernel<2, true, true>).  A CTA whose slab
+// bit the results of fx_march<2, true, true>).  A CTA whose slab
 // holds a node where r* != r or p*_prev != p_prev runs the general march.
 __device__ __noinline__ double pair_two_field_dir(const double* r, const double* rs, const double* pp,
                                                   const double* psp, double* pn, double* psn, double* q, double* qs,
                                                   double beta, int n, int sigma, int kz0, int kz1) {
-    FxFields fl{{pp, psp}, {q, qs}, {r, rs}, {pn, psn}, beta, nullptr, nullptr};
+    FxFields fl{{pp, psp}, {q, qs}, {r, rs}, {pn, psn}, beta};
     return fx_march<2, true, true>(fl, nullptr, n, sigma, blockIdx.x, blockIdx.y, kz0, kz1);
 }
 
@@ -299,8 +269,6 @@ struct BicgVectors {
     double* rs;
     double* p;
     double* ps;
-    double* p2;    // second direction pair of the z-march variant (p_k lives
-    double* ps2;   // in p / ps for odd k, in p2 / ps2 for even k)
     double* q;
     double* qs;
 };
@@ -325,10 +293,9 @@ __device__ __forceinline__ double all_partials(const double* partials, int c, do
 // p*, A^T p* are not stored because they equal r, p, A p bit for bit (the
 // integer operator is symmetric and r*_0 = r_0); v.rs, v.ps, v.ps2, v.qs are
 // unused and the iterates are the same bits as with kElide = false.
-// kFuse (z-march only): the fused schedule -- p = r + beta p formed inside
-// the operator phase from staged rows, two phases per iteration; otherwise
-// three phases with a separate direction update.
-template <bool kPointwise, bool kElide, bool kFuse>
+// Three phases per iteration: operator pair with sigma; x, r, r* update
+// with (r*, r) and (r, r); direction update.
+template <bool kPointwise, bool kElide>
 __global__ void __launch_bounds__(FX_NT, 2)
 bicg_persistent_kernel(BicgVectors v, size_t len, int n, int sigma, int gx, int gy, int slabs, int kz_per,
                        int iters, double* partials, BicgState* st, GridBarrier gb) {
@@ -342,16 +309,8 @@ bicg_persistent_kernel(BicgVectors v, size_t len, int n, int sigma, int gx, int 
     int iter = st->iter, status = st->status, done = st->done;
     const int max_iter = st->max_iter;
     const double stop = st->tol * st->bnorm;
-    const FxFields fl{{v.p, v.ps}, {v.q, v.qs}, {nullptr, nullptr}, {nullptr, nullptr}, 0.0, nullptr, nullptr};
     bool ok = true;
     for (int it = 0; it < iters && !done && ok; ++it) {
-        // z-march variant: iteration k forms p_k = r_k + beta_{k-1} p_{k-1}
-        // (p*_k likewise) inside the operator phase, reading p_{k-1} from one
-        // buffer pair and writing p_k to the other; k = 0 reads the copy of
-        // r_0 made by the set-up with beta = 0, which gives r_0 exactly
-        const bool odd = iter & 1;
-        double* const pk = odd ? v.p : v.p2;
-        double* const psk = odd ? v.ps : v.ps2;
         // phase A: q = A p, qs = A^T ps, sigma = (ps, q); per node on the
         // smallest grids, by z-marching tiles otherwise
         double dot = 0.0;
@@ -371,29 +330,20 @@ bicg_persistent_kernel(BicgVectors v, size_t len, int n, int sigma, int gx, int 
                 }
             }
         } else {
-            FxFields fd{{odd ? v.p2 : v.p, odd ? v.ps2 : v.ps}, {v.q, v.qs}, {v.r, v.rs}, {pk, psk}, beta,
-                        persistent_stage_smem, &st->fault};
             for (int u = blockIdx.x; u < units; u += G) {
                 const int bx = u % gx, by = (u / gx) % gy, bz = u / (gx * gy);
                 const int kz0 = 1 + bz * kz_per;
                 const int kz1 = min(kz0 + kz_per, n);
-                if (kFuse) {
-                    if (kElide)
-                        dot += fx_march<1, true, true, true>(fd, nullptr, n, sigma, bx, by, kz0, kz1);
-                    else
-                        dot += fx_march<2, true, true, true>(fd, nullptr, n, sigma, bx, by, kz0, kz1);
-                } else {
-                    // the copy-ahead march (same sums as fx_march<2, true>);
-                    // the CTA's previous unit is done with the shared buffers
+                // the copy-ahead march (same sums as fx_march<2, true>); the
+                // CTA's previous unit is done with the shared buffers
+                __syncthreads();
+                double dd = 0.0;
+                if (pp_march<kElide, kPairCvt>(v.p, v.ps, v.q, v.qs, n, sigma, bx, by, kz0, kz1,
+                                               persistent_stage_smem, &dd)) {
+                    dot += dd;
+                } else if constexpr (!kElide) {
                     __syncthreads();
-                    double dd = 0.0;
-                    if (pp_march<kElide, kPairCvt>(v.p, v.ps, v.q, v.qs, n, sigma, bx, by, kz0, kz1,
-                                                   persistent_stage_smem, &dd)) {
-                        dot += dd;
-                    } else if constexpr (!kElide) {
-                        __syncthreads();
-                        dot += pair_two_field(v.p, v.ps, v.q, v.qs, n, sigma, bx, by, kz0, kz1);
-                    }
+                    dot += pair_two_field(v.p, v.ps, v.q, v.qs, n, sigma, bx, by, kz0, kz1);
                 }
             }
         }
@@ -411,10 +361,10 @@ bicg_persistent_kernel(BicgVectors v, size_t len, int n, int sigma, int gx, int 
         // (entries t, t + S of this thread loaded together,
         // then updated and summed in index order)
         double vr = 0.0, vrr = 0.0;
-        const double* const pcur = (kPointwise || !kFuse) ? v.p : pk;
+        const double* const pcur = v.p;
         bool twin = true;   // as in bicg_update_kernel: vr == vrr so far
         const size_t S = (size_t)G * nthreads;
-        constexpr int kB = (kPointwise || kFuse) ? 1 : 2;   // entries per thread loaded together
+        constexpr int kB = kPointwise ? 1 : 2;   // entries per thread loaded together
         for (size_t t0 = (size_t)blockIdx.x * nthreads + tid; t0 < len; t0 += kB * S) {
             double xv[kB], pv[kB], rv[kB], qv[kB], rsv[kB], qsv[kB];
 #pragma unroll
@@ -486,9 +436,8 @@ bicg_persistent_kernel(BicgVectors v, size_t len, int n, int sigma, int gx, int 
             done = 1;
             break;
         }
-        if (kPointwise || !kFuse) {
-            // phase C: p = r + beta p; p* = r* + beta p* (the fused schedule
-            // does this in the next operator phase)
+        {
+            // phase C: p = r + beta p; p* = r* + beta p*
             for (size_t t0 = (size_t)blockIdx.x * nthreads + tid; t0 < len; t0 += kB * S) {
                 double rv[kB], pv[kB], rsv[kB], psv[kB];
 #pragma unroll
@@ -515,7 +464,7 @@ bicg_persistent_kernel(BicgVectors v, size_t len, int n, int sigma, int gx, int 
         }
     }
     if (blockIdx.x == 0 && thread0()) {
-        if (!ok || *(volatile int*)&st->fault) {
+        if (!ok) {
             status = kTimeout;
             done = 1;
         }
@@ -601,53 +550,10 @@ void opt_in_smem(K kernel, size_t smem) {
     (void)kernel_occupancy((const void*)kernel, FX_NT, smem);
 }
 
-// The staged (bulk-copy) march needs n >= 16 (all copied rows then lie in
-// the array) and 16-byte aligned arrays (the copies start on 16-byte
-// boundaries of the array).
-bool bulk_ok(int n, std::initializer_list<const double*> arrays) {
-    if (n < 16) return false;
-    for (const double* a : arrays)
-        if (((uintptr_t)a & 15u) != 0) return false;
-    return true;
-}
-
-StencilGrid fx_grid(int n, int nf) {
-    if (nf == 1) {
-        const int occ1 = resident_per_sm(stencil_fx_kernel<1, false>, FX_NT);
-        StencilGrid g = stencil_grid(n, FX_TX, FX_OY, occ1);
-        g.block = dim3(FX_TX, FX_TY, 1);
-        return g;
-    }
-    if (nf == 3) {
-        const int occ3 = resident_per_sm(stencil_fx_kernel<2, true, true>, FX_NT);
-        StencilGrid g = stencil_grid(n, FX_TX, FX_OY, occ3);
-        g.block = dim3(FX_TX, FX_TY, 1);
-        return g;
-    }
-    if (nf == 6 || nf == 7) {
-        // shadow-elided operator (one field, staged loads): the grid of the
-        // pair kernel it replaces (4 / 5), so that sigma adds the same
-        // per-CTA partial sums
-        const size_t smem6 = fx_stage_bytes<1, fx_stages(false)>();
-        const size_t smem7 = fx_stage_bytes<2, fx_stages(true)>();
-        if (nf == 6) opt_in_smem(stencil_fx_kernel<1, true, false, true>, smem6);
-        if (nf == 7) opt_in_smem(stencil_fx_kernel<1, true, true, true>, smem7);
-        StencilGrid g = fx_grid(n, nf - 2);
-        g.smem = nf == 6 ? smem6 : smem7;
-        return g;
-    }
-    if (nf == 4 || nf == 5) {   // staged loads: pair (4), pair with directions (5)
-        const size_t smem4 = fx_stage_bytes<2, fx_stages(false)>();
-        const size_t smem5 = fx_stage_bytes<4, fx_stages(true)>();
-        const int occ = nf == 4 ? resident_per_sm(stencil_fx_kernel<2, true, false, true>, FX_NT, smem4)
-                                : resident_per_sm(stencil_fx_kernel<2, true, true, true>, FX_NT, smem5);
-        StencilGrid g = stencil_grid(n, FX_TX, FX_OY, occ);
-        g.block = dim3(FX_TX, FX_TY, 1);
-        g.smem = nf == 4 ? smem4 : smem5;
-        return g;
-    }
-    const int occ2 = resident_per_sm(stencil_fx_kernel<2, true>, FX_NT);
-    StencilGrid g = stencil_grid(n, FX_TX, FX_OY, occ2);
+// The single-field operator launch (A u, b - A u).
+StencilGrid fx_grid(int n) {
+    const int occ1 = resident_per_sm(stencil_fx_kernel, FX_NT);
+    StencilGrid g = stencil_grid(n, FX_TX, FX_OY, occ1);
     g.block = dim3(FX_TX, FX_TY, 1);
     return g;
 }
@@ -684,10 +590,8 @@ StencilGrid f64_grid(int n) {
 
 int stencil_cta_count(int n) {
     unsigned most = 0;
-    for (int nf = 2; nf <= 5; ++nf) {
-        const StencilGrid g = fx_grid(n, nf);
-        most = max(most, g.grid.x * g.grid.y * g.grid.z);
-    }
+    const StencilGrid g1 = fx_grid(n);
+    most = max(most, g1.grid.x * g1.grid.y * g1.grid.z);
     const StencilGrid g = pair_grid(n);
     most = max(most, g.grid.x * g.grid.y * g.grid.z);
     const StencilGrid gd = pair_dir_grid(n);
@@ -707,41 +611,31 @@ cudaError_t launch_stencil(const double* u, double* y, const double* b, int n, i
     } else {
         // A^T u == A u bit for bit in integer arithmetic (see above)
         (void)transpose;
-        const StencilGrid g = fx_grid(n, 1);
+        const StencilGrid g = fx_grid(n);
         FxFields fl{{u, nullptr}, {y, nullptr}, {nullptr, nullptr}, {nullptr, nullptr}, 0.0};
-        stencil_fx_kernel<1, false><<<g.grid, g.block, 0, s>>>(fl, b, n, bc_kind == 1 ? 1 : -1, g.kz_per_cta,
-                                                               skip, nullptr, nullptr);
+        stencil_fx_kernel<<<g.grid, g.block, 0, s>>>(fl, b, n, bc_kind == 1 ? 1 : -1, g.kz_per_cta, skip);
     }
     return cudaGetLastError();
 }
 
 constexpr int kPointwiseMaxN = 40;   // per-node operator on grids up to 40^3
 
-// dynamic shared memory of the z-march variant: the staged loads of the
-// operator phase with the direction update fused in
-size_t persistent_stage_bytes() { return fx_stage_bytes<4, fx_stages(true)>(); }
+// dynamic shared memory of the z-march variant: the copy-ahead march's
+// stages and tiles
+size_t persistent_smem(bool pointwise) { return pointwise ? 0 : pp_smem_bytes<2>(); }
 
-// dynamic shared memory of a cooperative launch: none for the per-node
-// operator, the copy stages and tiles of pp_march for the plain z-march
-size_t persistent_smem(bool pointwise, bool fuse) {
-    if (pointwise) return 0;
-    return fuse ? persistent_stage_bytes() : pp_smem_bytes<2>();
-}
-
-int persistent_grid(int n, bool fuse, int* gx, int* gy, int* slabs, int* kz_per) {
+int persistent_grid(int n, int* gx, int* gy, int* slabs, int* kz_per) {
     // at most two CTAs per SM; the elided variants run on the grids of the
     // full ones (same partial sums)
-    const int occ_pt = min(2, resident_per_sm(bicg_persistent_kernel<true, false, false>, FX_NT));
-    const int occ_mz = min(2, resident_per_sm(bicg_persistent_kernel<false, false, false>, FX_NT, pp_smem_bytes<2>()));
-    const int occ_fz = min(2, resident_per_sm(bicg_persistent_kernel<false, false, true>, FX_NT,
-                                              persistent_stage_bytes()));
+    const int occ_pt = min(2, resident_per_sm(bicg_persistent_kernel<true, false>, FX_NT));
+    const int occ_mz = min(2, resident_per_sm(bicg_persistent_kernel<false, false>, FX_NT, pp_smem_bytes<2>()));
     const int sms = device_sms();
     const int m = n - 1;
     *gx = (m + FX_TX - 1) / FX_TX;
     *gy = (m + FX_OY - 1) / FX_OY;
     *kz_per = m < 8 ? m : (n <= 64 ? 4 : 8);
     *slabs = (m + *kz_per - 1) / *kz_per;
-    if (n > kPointwiseMaxN) return sms * (fuse ? occ_fz : occ_mz);
+    if (n > kPointwiseMaxN) return sms * occ_mz;
     // one CTA per ~256 interior nodes, at most every resident slot: fewer
     // CTAs keep the grid barriers short on small grids
     const long long pts = (long long)m * m * m;
@@ -753,42 +647,28 @@ int persistent_grid(int n, bool fuse, int* gx, int* gy, int* slabs, int* kz_per)
 
 bool persistent_pointwise(int n) { return n <= kPointwiseMaxN; }
 
-cudaError_t launch_bicg_persistent(double* x, double* r, double* rs, double* p, double* ps, double* p2, double* ps2,
-                                   double* q, double* qs, int n, int bc_kind, int iters, double* partials,
-                                   BicgState* st, unsigned int* barrier_words, cudaStream_t s, bool elide,
-                                   bool fuse) {
+cudaError_t launch_bicg_persistent(double* x, double* r, double* rs, double* p, double* ps, double* q, double* qs,
+                                   int n, int bc_kind, int iters, double* partials, BicgState* st,
+                                   unsigned int* barrier_words, cudaStream_t s, bool elide) {
     const bool pw = persistent_pointwise(n);
-    fuse = fuse && !pw;
     int gx, gy, slabs, kz_per;
-    const int G = persistent_grid(n, fuse, &gx, &gy, &slabs, &kz_per);
+    const int G = persistent_grid(n, &gx, &gy, &slabs, &kz_per);
     cudaError_t e = cudaMemsetAsync(barrier_words, 0, 3 * sizeof(unsigned int), s);
     if (e != cudaSuccess) return e;
-    BicgVectors v{x, r, rs, p, ps, p2, ps2, q, qs};
+    BicgVectors v{x, r, rs, p, ps, q, qs};
     size_t len = node_count(n);
     int sigma = bc_kind == 1 ? 1 : -1;
     GridBarrier gb{barrier_words, barrier_words + 1, (int*)(barrier_words + 2), kBarrierSpinLimit};
     void* args[] = {&v, &len, &n, &sigma, &gx, &gy, &slabs, &kz_per, &iters, &partials, &st, &gb};
     const void* fn;
-    if (pw)
-        fn = elide ? (const void*)bicg_persistent_kernel<true, true, false>
-                   : (const void*)bicg_persistent_kernel<true, false, false>;
-    else if (fuse) {
-        if (elide) {
-            opt_in_smem(bicg_persistent_kernel<false, true, true>, persistent_stage_bytes());
-            fn = (const void*)bicg_persistent_kernel<false, true, true>;
-        } else {
-            opt_in_smem(bicg_persistent_kernel<false, false, true>, persistent_stage_bytes());
-            fn = (const void*)bicg_persistent_kernel<false, false, true>;
-        }
+    if (pw) {
+        fn = elide ? (const void*)bicg_persistent_kernel<true, true> : (const void*)bicg_persistent_kernel<true, false>;
+    } else {
+        opt_in_smem(bicg_persistent_kernel<false, true>, pp_smem_bytes<2>());
+        opt_in_smem(bicg_persistent_kernel<false, false>, pp_smem_bytes<2>());
+        fn = elide ? (const void*)bicg_persistent_kernel<false, true> : (const void*)bicg_persistent_kernel<false, false>;
     }
-    else
-    {
-        opt_in_smem(bicg_persistent_kernel<false, true, false>, pp_smem_bytes<2>());
-        opt_in_smem(bicg_persistent_kernel<false, false, false>, pp_smem_bytes<2>());
-        fn = elide ? (const void*)bicg_persistent_kernel<false, true, false>
-                   : (const void*)bicg_persistent_kernel<false, false, false>;
-    }
-    return cudaLaunchCooperativeKernel(fn, dim3(G), dim3(FX_TX, FX_TY, 1), args, persistent_smem(pw, fuse), s);
+    return cudaLaunchCooperativeKernel(fn, dim3(G), dim3(FX_TX, FX_TY, 1), args, persistent_smem(pw), s);
 }
 
 cudaError_t launch_bicg_stencil_pair_dir(const double* r, const double* rs, const double* p_prev,

@@ -153,4 +153,6 @@ def serve(engine, requests, pool, tol: float, clock=time.perf_counter, new_outpu
                "p50_s": float(np.percentile(lat, 50)), "p99_s": float(np.percentile(lat, 99)),
                "mean_s": float(lat.mean()), "steps": steps,
                "failed": sum(1 for rec in records if rec["status"] != 0)}
+    if hasattr(engine, "profile"):
+        summary["engine_profile"] = engine.profile()
     return records, summary

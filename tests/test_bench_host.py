@@ -17,5 +17,5 @@ def test_config_names_the_workload():
     args = bench.parse([])
     cfg = bench.config(args)
     assert cfg["n_finest"] == 512 and cfg["n_coarsest"] == 8 and cfg["levels"] == 7
-    assert cfg["schedule"] == "separate" and cfg["stencil"] == "exact"
+    assert cfg["schedule"] == "fused" and cfg["stencil"] == "exact"
     assert "512^3" in cfg["workload"]
