@@ -57,6 +57,8 @@ def parse(argv=None):
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-mixed", action="store_true", help="skip the FP32-inner / FP64-refinement leg")
     ap.add_argument("--mixed-steps", type=int, default=2)
+    ap.add_argument("--mixed-tols", default="",
+                    help="comma-separated FP64 residual tolerances for a sweep of the precision leg")
     ap.add_argument("--no-batch", action="store_true", help="skip the 64-instance batched leg")
     ap.add_argument("--no-serve", action="store_true", help="skip the request-stream leg")
     ap.add_argument("--serve-requests", type=int, default=120)
@@ -421,42 +423,71 @@ def run_ours(args):
     ms_step = max_over_ranks(ms_total / args.steps, world, dev)
     value = seconds_per_solve(ms_step, len(bcs), world)
 
-    # ---- end to end through the C ABI, host buffers
+    # ---- end to end through the C ABI, host buffers.  Every solve copies its
+    # inputs (f, g1, g2) from pinned host memory and reads u back; the copies
+    # run on their own streams into two device buffer sets, so the inputs of
+    # solve i+1 and the result of solve i-1 move while solve i computes (the
+    # solve call itself returns when its work is done).
     e2e = None
     if not args.no_e2e:
         h2d = sum(host[k].numel() * 8 for k in ("f", "g1")) + host["g2_1"].numel() * 8
         d2h = u_host.numel() * 8
+        sets = [d, {k: torch.empty_like(v) for k, v in d.items()}]
+        outs = [u_out, torch.empty_like(u_out)]
+        u_hosts = [u_host, torch.empty_like(u_host).pin_memory()]
+        s_h2d, s_d2h = torch.cuda.Stream(dev), torch.cuda.Stream(dev)
+        order = [bc for _ in range(args.steps) for bc in bcs]
+        ns = len(order)
+
+        def e2e_solve(bc, k):
+            return B.excmg_solve(n, nc, bc, sets[k]["f"], sets[k]["g1"], sets[k][f"g2_{bc}"], args.tol, outs[k],
+                                 ctx=ctx)
+
         barrier()
-        e2 = torch.cuda.Event(enable_timing=True)
-        e3 = torch.cuda.Event(enable_timing=True)
-        marks = []
+        ev = lambda: torch.cuda.Event(enable_timing=True)
+        h2d_start = [ev() for _ in range(ns)]
+        d2h_start = [ev() for _ in range(ns)]
+        inputs_ready = [ev() for _ in range(ns)]
+        result_read = [ev() for _ in range(ns)]
+        solve_done = [ev() for _ in range(ns)]
+        e2, e3 = ev(), ev()
         e2.record(stream)
-        for _ in range(args.steps):
-            for bc in bcs:
-                m = [torch.cuda.Event(enable_timing=True) for _ in range(3)]
-                d["f"].copy_(host["f"], non_blocking=True)
-                d["g1"].copy_(host["g1"], non_blocking=True)
-                d[f"g2_{bc}"].copy_(host[f"g2_{bc}"], non_blocking=True)
-                m[0].record(stream)
-                solve(bc)
-                m[1].record(stream)
-                u_host.copy_(u_out, non_blocking=True)
-                m[2].record(stream)
-                marks.append(m)
+
+        def prefetch(i):
+            k = i % 2
+            with torch.cuda.stream(s_h2d):
+                s_h2d.wait_stream(stream)          # set k's previous solve has finished
+                h2d_start[i].record(s_h2d)
+                for key in ("f", "g1", f"g2_{order[i]}"):
+                    sets[k][key].copy_(host[key], non_blocking=True)
+                inputs_ready[i].record(s_h2d)
+
+        prefetch(0)
+        for i, bc in enumerate(order):
+            k = i % 2
+            stream.wait_event(inputs_ready[i])
+            if i >= 2:
+                stream.wait_event(result_read[i - 2])   # outs[k] has been read back
+            if i + 1 < ns:
+                prefetch(i + 1)
+            e2e_solve(bc, k)
+            solve_done[i].record(stream)
+            with torch.cuda.stream(s_d2h):
+                s_d2h.wait_event(solve_done[i])
+                d2h_start[i].record(s_d2h)
+                u_hosts[k].copy_(outs[k], non_blocking=True)
+                result_read[i].record(s_d2h)
+        stream.wait_event(result_read[ns - 1])
         e3.record(stream)
         barrier()
-        prev = e2
-        h2d_ms = solve_ms = d2h_ms = 0.0
-        for m in marks:
-            h2d_ms += prev.elapsed_time(m[0])
-            solve_ms += m[0].elapsed_time(m[1])
-            d2h_ms += m[1].elapsed_time(m[2])
-            prev = m[2]
         ms_e2e = max_over_ranks(e2.elapsed_time(e3) / args.steps, world, dev)
-        ns = args.steps * len(bcs)
         e2e = {"value": seconds_per_solve(ms_e2e, len(bcs), world), "unit": "s",
                "h2d_bytes_per_step": h2d * len(bcs), "d2h_bytes_per_step": d2h * len(bcs),
-               "per_solve_ms": {"h2d": h2d_ms / ns, "solve": solve_ms / ns, "d2h": d2h_ms / ns},
+               "pipeline": "inputs of the next solve and the result of the previous one copied on two "
+                           "streams into two device buffer sets while a solve runs",
+               "per_solve_ms": {"h2d": statistics.mean(h2d_start[i].elapsed_time(inputs_ready[i]) for i in range(ns)),
+                                "solve": statistics.mean(inputs_ready[i].elapsed_time(solve_done[i]) for i in range(ns)),
+                                "d2h": statistics.mean(d2h_start[i].elapsed_time(result_read[i]) for i in range(ns))},
                "host_binding": host_binding}
 
     # ---- roofline of the operator kernel on the finest grid
@@ -562,43 +593,49 @@ def precision_leg(args, B, problems, ctx, dev, stream, barrier, world):
     refinement to the same FP64 relative residual tol on every level.
     Reports seconds per solve of each, the max error of each against the
     exact solution (the discretisation error) and their distance from each
-    other."""
+    other; with --mixed-tols, the same for every tolerance of the sweep."""
     import torch
 
     n, nc = args.n, args.nc
     prob = problems.sin2pi_plus_poly()
     f = torch.from_numpy(prob.rhs(n)).to(dev)
     ue = torch.from_numpy(prob.exact(n)).to(dev)
+    g2s = {bc: torch.from_numpy(prob.boundary_g2(n, bc)).to(dev) for bc in (1, 2)}
+
+    def one(tol):
+        res = {}
+        for prec in ("fp64", "mixed"):
+            times, errs, outs = [], [], {}
+            for bc in (1, 2):
+                u = torch.empty_like(f)
+                run = lambda: B.excmg_solve(n, nc, bc, f, ue, g2s[bc], tol, u, ctx=ctx, precision=prec,
+                                            return_stats=True, max_total=20000)
+                _, st = run()   # warm-up
+                barrier()
+                e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+                e0.record(stream)
+                for _ in range(args.mixed_steps):
+                    _, st = run()
+                e1.record(stream)
+                barrier()
+                times.append(e0.elapsed_time(e1) / args.mixed_steps / 1e3)
+                errs.append(float((u - ue).abs().max()))
+                outs[bc] = u.clone()
+                res.setdefault("levels_" + prec, {})[str(bc)] = [(s["n"], s["iters"], s["calls"]) for s in st]
+            res[prec] = (sum(times) / len(times), errs, outs)
+        t64, e64, o64 = res["fp64"]
+        tmx, emx, omx = res["mixed"]
+        return {"tol": tol, "fp64_s": max_over_ranks(t64, world, dev), "mixed_s": max_over_ranks(tmx, world, dev),
+                "speedup": t64 / tmx, "err_vs_exact_linf_fp64": e64, "err_vs_exact_linf_mixed": emx,
+                "mixed_minus_fp64_linf": [float((omx[bc] - o64[bc]).abs().max()) for bc in (1, 2)],
+                "levels_fp64": res["levels_fp64"], "levels_mixed": res["levels_mixed"]}
+
     out = {"workload": (f"{n}^3, coarsest {nc}^3, u = sin(2 pi x)sin(2 pi y)sin(2 pi z) + x^2y^2z^2, "
                         f"first- and second-kind data, FP64 residual tol {args.tol:g} per level"),
            "inner_tol": B.MIXED_INNER_TOL, "inner_cap": B.MIXED_INNER_CAP}
-    res = {}
-    for prec in ("fp64", "mixed"):
-        times, errs, outs = [], [], {}
-        for bc in (1, 2):
-            g2 = torch.from_numpy(prob.boundary_g2(n, bc)).to(dev)
-            u = torch.empty_like(f)
-            run = lambda: B.excmg_solve(n, nc, bc, f, ue, g2, args.tol, u, ctx=ctx, precision=prec,
-                                        return_stats=True, max_total=20000)
-            _, st = run()   # warm-up
-            barrier()
-            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-            e0.record(stream)
-            for _ in range(args.mixed_steps):
-                _, st = run()
-            e1.record(stream)
-            barrier()
-            times.append(e0.elapsed_time(e1) / args.mixed_steps / 1e3)
-            errs.append(float((u - ue).abs().max()))
-            outs[bc] = u.clone()
-            res.setdefault("levels_" + prec, {})[str(bc)] = [(s["n"], s["iters"], s["calls"]) for s in st]
-        res[prec] = (sum(times) / len(times), errs, outs)
-    t64, e64, o64 = res["fp64"]
-    tmx, emx, omx = res["mixed"]
-    out.update({"fp64_s": max_over_ranks(t64, world, dev), "mixed_s": max_over_ranks(tmx, world, dev),
-                "speedup": t64 / tmx, "err_vs_exact_linf_fp64": e64, "err_vs_exact_linf_mixed": emx,
-                "mixed_minus_fp64_linf": [float((omx[bc] - o64[bc]).abs().max()) for bc in (1, 2)],
-                "levels_fp64": res["levels_fp64"], "levels_mixed": res["levels_mixed"]})
+    out.update(one(args.tol))
+    if args.mixed_tols:
+        out["sweep"] = [one(float(t)) for t in args.mixed_tols.split(",") if t.strip()]
     return out
 
 

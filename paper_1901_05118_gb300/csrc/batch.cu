@@ -27,6 +27,7 @@
 #include "grid_sync.cuh"
 #include "march_f32.cuh"
 #include "march_fx.cuh"
+#include "march_pair.cuh"
 #include "reduce.cuh"
 
 namespace excmg {
@@ -46,15 +47,30 @@ struct BatchInst {     // device table entry, one per instance in the Bi-CG phas
     T *x, *r, *rs, *p, *ps, *q, *qs;
 };
 
-// One tile's operator pair (A p, A p* -- A is symmetric) and its share of
-// (p*, A p): FP32 arithmetic for the correction solves, the integer
-// evaluation for FP64 solves.
-__device__ __forceinline__ float march_pair(const BatchInst<float>& in, int bx, int by, int kz0, int kz1) {
+// One tile's operator pair (A p, A p* -- A is symmetric) and this thread's
+// share of (p*, A p): FP32 arithmetic for the correction solves; for FP64
+// solves the integer evaluation by the copy-ahead march (p* equals p bit for
+// bit: every call starts from r*_0 = p_0 = p*_0 = r_0), with the general
+// two-field march where a tile holds p* != p.  Called uniformly by the CTA.
+__device__ __forceinline__ float march_pair(const BatchInst<float>& in, int bx, int by, int kz0, int kz1,
+                                            unsigned char*) {
     return f32_march<2, true>(in.p, in.ps, in.q, in.qs, in.n, (float)in.sigma, bx, by, kz0, kz1);
 }
-__device__ __forceinline__ double march_pair(const BatchInst<double>& in, int bx, int by, int kz0, int kz1) {
+__device__ __forceinline__ double march_pair(const BatchInst<double>& in, int bx, int by, int kz0, int kz1,
+                                             unsigned char* smem) {
+    __syncthreads();   // the CTA's previous unit is done with the shared buffers
+    double d = 0.0;
+    if (pp_march<false, true>(in.p, in.ps, in.q, in.qs, in.n, in.sigma, bx, by, kz0, kz1, smem, &d)) return d;
+    __syncthreads();
     const FxFields fl{{in.p, in.ps}, {in.q, in.qs}, {nullptr, nullptr}, {nullptr, nullptr}, 0.0};
     return fx_march<2, true>(fl, nullptr, in.n, in.sigma, bx, by, kz0, kz1);
+}
+
+// dynamic shared memory of the batched kernel: the copy-ahead march's stages
+// and tiles for FP64 instances, none for the FP32 march
+template <typename T>
+constexpr size_t batch_smem() {
+    return sizeof(T) == sizeof(double) ? pp_smem_bytes<2>() : 0;
 }
 
 struct BatchState {    // device, one per slot
@@ -103,6 +119,7 @@ batch_bicg_kernel(const BatchInst<T>* __restrict__ inst, const int* __restrict__
     __shared__ double sh[32];
     __shared__ T shf[32];
     __shared__ bool flag;
+    extern __shared__ __align__(128) unsigned char batch_smem_buf[];
     const unsigned int G = gridDim.x;
     const int tid = threadIdx.x + blockDim.x * threadIdx.y;
     const int nt = blockDim.x * blockDim.y;
@@ -120,7 +137,7 @@ batch_bicg_kernel(const BatchInst<T>* __restrict__ inst, const int* __restrict__
             const int loc = u - in.unit_begin;
             const int bx = loc % in.gx, by = (loc / in.gx) % in.gy, bz = loc / (in.gx * in.gy);
             const int kz0 = 1 + bz * in.kz_per;
-            const T d = march_pair(in, bx, by, kz0, min(kz0 + in.kz_per, in.n));
+            const T d = march_pair(in, bx, by, kz0, min(kz0 + in.kz_per, in.n), batch_smem_buf);
             const double ds = (double)block_sum(d, shf);
             if (thread0()) unit_part[u] = ds;
             if (take_last(&st.ticket_a, (unsigned)in.nunits, &flag)) {
@@ -260,7 +277,7 @@ batch_correct_kernel(double* __restrict__ u, const float* __restrict__ e, size_t
 // The cooperative grid: every SM of the current device, at most two CTAs each.
 template <typename T>
 int batch_resident_ctas() {
-    const int occ = min(2, kernel_occupancy((const void*)batch_bicg_kernel<T>, S_NT, 0));
+    const int occ = min(2, kernel_occupancy((const void*)batch_bicg_kernel<T>, S_NT, batch_smem<T>()));
     return device_sms() * occ;
 }
 
@@ -626,8 +643,8 @@ int launch_group(excmg_batch* b, excmg_batch::Group& g, const std::vector<Instan
                     (void*)&rounds};
     e = cudaEventRecord(g.start, s);
     if (e == cudaSuccess)
-        e = cudaLaunchCooperativeKernel((const void*)batch_bicg_kernel<T>, dim3(ctas), dim3(S_TX, S_TY, 1), args, 0,
-                                        s);
+        e = cudaLaunchCooperativeKernel((const void*)batch_bicg_kernel<T>, dim3(ctas), dim3(S_TX, S_TY, 1), args,
+                                        batch_smem<T>(), s);
     bnote(b, 1);
     if (e == cudaSuccess) e = cudaMemcpyAsync(g.h_active, g.d_active, sizeof(int), cudaMemcpyDeviceToHost, s);
     if (e == cudaSuccess) e = cudaMemcpyAsync(g.h_rounds, g.d_rounds, sizeof(int), cudaMemcpyDeviceToHost, s);
