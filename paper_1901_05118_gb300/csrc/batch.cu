@@ -34,6 +34,7 @@ namespace excmg {
 namespace {
 
 constexpr int kChunk = 8192;          // vector entries per chunk of the batched kernel
+constexpr int kLd = 2;                // vector entries per thread loaded together
 constexpr int kBatchMaxInst = 1024;
 
 template <typename T>
@@ -111,7 +112,7 @@ __device__ __forceinline__ double sum_range(const double* v, int begin, int coun
 }
 
 template <typename T>
-__global__ void __launch_bounds__(S_NT)
+__global__ void __launch_bounds__(S_NT, 2)
 batch_bicg_kernel(const BatchInst<T>* __restrict__ inst, const int* __restrict__ unit_begin,
                     const int* __restrict__ chunk_begin, int ninst, int total_units, int total_chunks,
                     double* unit_part, double* chunk_part, BatchState* states, int iters, int* active,
@@ -168,14 +169,34 @@ batch_bicg_kernel(const BatchInst<T>* __restrict__ inst, const int* __restrict__
             const long long t0 = (long long)(c - in.chunk_begin) * kChunk;
             const long long t1 = min(t0 + kChunk, in.len);
             T vr = 0, vrr = 0;
-            for (long long t = t0 + tid; t < t1; t += nt) {
-                in.x[t] = in.x[t] + alpha * in.p[t];
-                const T rn = in.r[t] - alpha * in.q[t];
-                const T rsn = in.rs[t] - alpha * in.qs[t];
-                in.r[t] = rn;
-                in.rs[t] = rsn;
-                vr += rsn * rn;
-                vrr += rn * rn;
+            // kLd entries per thread loaded together, then updated and summed
+            // in index order
+            for (long long tb = t0 + tid; tb < t1; tb += (long long)kLd * nt) {
+                T xv[kLd], pv[kLd], rv[kLd], qv[kLd], rsv[kLd], qsv[kLd];
+#pragma unroll
+                for (int k = 0; k < kLd; ++k) {
+                    const long long t = tb + (long long)k * nt;
+                    if (t < t1) {
+                        xv[k] = in.x[t];
+                        pv[k] = in.p[t];
+                        rv[k] = in.r[t];
+                        qv[k] = in.q[t];
+                        rsv[k] = in.rs[t];
+                        qsv[k] = in.qs[t];
+                    }
+                }
+#pragma unroll
+                for (int k = 0; k < kLd; ++k) {
+                    const long long t = tb + (long long)k * nt;
+                    if (t >= t1) break;
+                    in.x[t] = xv[k] + alpha * pv[k];
+                    const T rn = rv[k] - alpha * qv[k];
+                    const T rsn = rsv[k] - alpha * qsv[k];
+                    in.r[t] = rn;
+                    in.rs[t] = rsn;
+                    vr += rsn * rn;
+                    vrr += rn * rn;
+                }
             }
             const double a = (double)block_sum(vr, shf);
             const double b = (double)block_sum(vrr, shf);
@@ -217,9 +238,25 @@ batch_bicg_kernel(const BatchInst<T>* __restrict__ inst, const int* __restrict__
             const T beta = (T)st.beta;
             const long long t0 = (long long)(c - in.chunk_begin) * kChunk;
             const long long t1 = min(t0 + kChunk, in.len);
-            for (long long t = t0 + tid; t < t1; t += nt) {
-                in.p[t] = in.r[t] + beta * in.p[t];
-                in.ps[t] = in.rs[t] + beta * in.ps[t];
+            for (long long tb = t0 + tid; tb < t1; tb += (long long)kLd * nt) {
+                T rv[kLd], pv[kLd], rsv[kLd], psv[kLd];
+#pragma unroll
+                for (int k = 0; k < kLd; ++k) {
+                    const long long t = tb + (long long)k * nt;
+                    if (t < t1) {
+                        rv[k] = in.r[t];
+                        pv[k] = in.p[t];
+                        rsv[k] = in.rs[t];
+                        psv[k] = in.ps[t];
+                    }
+                }
+#pragma unroll
+                for (int k = 0; k < kLd; ++k) {
+                    const long long t = tb + (long long)k * nt;
+                    if (t >= t1) break;
+                    in.p[t] = rv[k] + beta * pv[k];
+                    in.ps[t] = rsv[k] + beta * psv[k];
+                }
             }
         }
         if (!(ok = grid_sync(gb, G))) break;
@@ -517,7 +554,7 @@ BatchInst<T> geometry(Instance* in, int slot, int* units, int* chunks) {
     t.sigma = in->bc == 1 ? 1 : -1;
     t.gx = (m + S_TX - 1) / S_TX;
     t.gy = (m + S_OY - 1) / S_OY;
-    t.kz_per = m < 8 ? m : 8;
+    t.kz_per = m < 8 ? m : (N >= 128 ? 16 : 8);   // longer slabs: less halo per output plane
     t.nunits = t.gx * t.gy * ((m + t.kz_per - 1) / t.kz_per);
     t.unit_begin = *units;
     t.len = (long long)node_count(N);
