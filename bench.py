@@ -59,6 +59,8 @@ def parse(argv=None):
     ap.add_argument("--mixed-steps", type=int, default=2)
     ap.add_argument("--mixed-tols", default="",
                     help="comma-separated FP64 residual tolerances for a sweep of the precision leg")
+    ap.add_argument("--mixed-inner", default="",
+                    help="comma-separated inner_tol:cap pairs of the FP32 correction solves to sweep at --tol")
     ap.add_argument("--no-batch", action="store_true", help="skip the 64-instance batched leg")
     ap.add_argument("--no-serve", action="store_true", help="skip the request-stream leg")
     ap.add_argument("--serve-requests", type=int, default=120)
@@ -604,14 +606,17 @@ def precision_leg(args, B, problems, ctx, dev, stream, barrier, world):
     ue = torch.from_numpy(prob.exact(n)).to(dev)
     g2s = {bc: torch.from_numpy(prob.boundary_g2(n, bc)).to(dev) for bc in (1, 2)}
 
-    def one(tol):
+    def one(tol, inner=None):
         res = {}
-        for prec in ("fp64", "mixed"):
+        for prec in (("mixed",) if inner else ("fp64", "mixed")):
+            kw = {}
+            if inner and prec == "mixed":
+                kw = {"inner_tol": inner[0], "max_iter": inner[1]}
             times, errs, outs = [], [], {}
             for bc in (1, 2):
                 u = torch.empty_like(f)
                 run = lambda: B.excmg_solve(n, nc, bc, f, ue, g2s[bc], tol, u, ctx=ctx, precision=prec,
-                                            return_stats=True, max_total=20000)
+                                            return_stats=True, max_total=20000, **kw)
                 _, st = run()   # warm-up
                 barrier()
                 e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
@@ -625,6 +630,11 @@ def precision_leg(args, B, problems, ctx, dev, stream, barrier, world):
                 outs[bc] = u.clone()
                 res.setdefault("levels_" + prec, {})[str(bc)] = [(s["n"], s["iters"], s["calls"]) for s in st]
             res[prec] = (sum(times) / len(times), errs, outs)
+        if inner:
+            tmx, emx, _ = res["mixed"]
+            return {"tol": tol, "inner_tol": inner[0], "inner_cap": inner[1],
+                    "mixed_s": max_over_ranks(tmx, world, dev), "err_vs_exact_linf_mixed": emx,
+                    "levels_mixed": res["levels_mixed"]}
         t64, e64, o64 = res["fp64"]
         tmx, emx, omx = res["mixed"]
         return {"tol": tol, "fp64_s": max_over_ranks(t64, world, dev), "mixed_s": max_over_ranks(tmx, world, dev),
@@ -638,6 +648,9 @@ def precision_leg(args, B, problems, ctx, dev, stream, barrier, world):
     out.update(one(args.tol))
     if args.mixed_tols:
         out["sweep"] = [one(float(t)) for t in args.mixed_tols.split(",") if t.strip()]
+    if args.mixed_inner:
+        pairs = [p.split(":") for p in args.mixed_inner.split(",") if p.strip()]
+        out["inner_sweep"] = [one(args.tol, (float(a), int(b))) for a, b in pairs]
     return out
 
 

@@ -46,6 +46,7 @@ struct BatchInst {     // device table entry, one per instance in the Bi-CG phas
     int slot;          // index into the state array
     long long len;
     T *x, *r, *rs, *p, *ps, *q, *qs;
+    T *p2, *ps2;       // FP64: second direction pair (p_k in p for even k, in p2 for odd k)
 };
 
 // One tile's operator pair (A p, A p* -- A is symmetric) and this thread's
@@ -67,17 +68,41 @@ __device__ __forceinline__ double march_pair(const BatchInst<double>& in, int bx
     return fx_march<2, true>(fl, nullptr, in.n, in.sigma, bx, by, kz0, kz1);
 }
 
+// FP64, iteration k >= 1 of a Bi-CG call: p_k = r_k + beta p_{k-1} (and p*_k)
+// formed on every loaded node from the pair holding p_{k-1}, the CTA's own
+// nodes written to the other pair, then the operator pair on p_k.
+__device__ __forceinline__ double march_pair_dir(const BatchInst<double>& in, int k, double beta, int bx, int by,
+                                                 int kz0, int kz1, unsigned char* smem) {
+    const bool odd = k & 1;
+    const double* pp = odd ? in.p : in.p2;
+    const double* psp = odd ? in.ps : in.ps2;
+    double* pn = odd ? in.p2 : in.p;
+    double* psn = odd ? in.ps2 : in.ps;
+    __syncthreads();   // the CTA's previous unit is done with the shared buffers
+    double d = 0.0;
+    const PairDir dir{in.r, in.rs, pn, psn, beta};
+    if (pp_march<false, true, true>(pp, psp, in.q, in.qs, in.n, in.sigma, bx, by, kz0, kz1, smem, &d, dir))
+        return d;
+    __syncthreads();
+    const FxFields fl{{pp, psp}, {in.q, in.qs}, {in.r, in.rs}, {pn, psn}, beta};
+    return fx_march<2, true, true>(fl, nullptr, in.n, in.sigma, bx, by, kz0, kz1);
+}
+
 // dynamic shared memory of the batched kernel: the copy-ahead march's stages
 // and tiles for FP64 instances, none for the FP32 march
 template <typename T>
 constexpr size_t batch_smem() {
-    return sizeof(T) == sizeof(double) ? pp_smem_bytes<2>() : 0;
+    return sizeof(T) == sizeof(double) ? pp_smem_bytes<4>() : 0;
 }
 
 struct BatchState {    // device, one per slot
     double rho, rr, alpha, beta, sigma, tol;
     int iter, max_iter, done, status;
     unsigned int ticket_a, ticket_b;
+    // set in phase A at a breakdown: the instance leaves the launch's count
+    // of running instances in phase B, so that the count changes in phase B
+    // only and every CTA reads the same value after its barrier
+    int exit_pending, pad;
 };
 
 // Instance owning global index g, given each instance's first index.
@@ -121,6 +146,9 @@ batch_bicg_kernel(const BatchInst<T>* __restrict__ inst, const int* __restrict__
     __shared__ T shf[32];
     __shared__ bool flag;
     extern __shared__ __align__(128) unsigned char batch_smem_buf[];
+    // FP64 groups fold the direction update into the operator phase (two
+    // grid barriers per round); FP32 groups keep a separate phase C
+    constexpr bool kFused = sizeof(T) == sizeof(double);
     const unsigned int G = gridDim.x;
     const int tid = threadIdx.x + blockDim.x * threadIdx.y;
     const int nt = blockDim.x * blockDim.y;
@@ -138,7 +166,17 @@ batch_bicg_kernel(const BatchInst<T>* __restrict__ inst, const int* __restrict__
             const int loc = u - in.unit_begin;
             const int bx = loc % in.gx, by = (loc / in.gx) % in.gy, bz = loc / (in.gx * in.gy);
             const int kz0 = 1 + bz * in.kz_per;
-            const T d = march_pair(in, bx, by, kz0, min(kz0 + in.kz_per, in.n), batch_smem_buf);
+            T d;
+            if constexpr (kFused) {
+                // the state's iteration count is this call's k until phase B
+                // of this round completes
+                const int k = st.iter;
+                d = k == 0 ? march_pair(in, bx, by, kz0, min(kz0 + in.kz_per, in.n), batch_smem_buf)
+                           : march_pair_dir(in, k, st.beta, bx, by, kz0, min(kz0 + in.kz_per, in.n),
+                                            batch_smem_buf);
+            } else {
+                d = march_pair(in, bx, by, kz0, min(kz0 + in.kz_per, in.n), batch_smem_buf);
+            }
             const double ds = (double)block_sum(d, shf);
             if (thread0()) unit_part[u] = ds;
             if (take_last(&st.ticket_a, (unsigned)in.nunits, &flag)) {
@@ -148,7 +186,7 @@ batch_bicg_kernel(const BatchInst<T>* __restrict__ inst, const int* __restrict__
                     if (!(st.rho != 0.0 && isfinite(st.rho)) || !(sg != 0.0 && isfinite(sg))) {
                         st.status = kBreakdown;
                         st.done = 1;
-                        atomicSub(active, 1);
+                        st.exit_pending = 1;
                     } else {
                         st.alpha = st.rho / sg;
                     }
@@ -164,8 +202,20 @@ batch_bicg_kernel(const BatchInst<T>* __restrict__ inst, const int* __restrict__
             const int i = owner(chunk_begin, ninst, c);
             const BatchInst<T>& in = inst[i];
             BatchState& st = states[in.slot];
-            if (*(volatile int*)&st.done) continue;
+            if (*(volatile int*)&st.done) {
+                // an instance that broke down in phase A of this round: its
+                // chunks update nothing, the CTA taking the last one takes
+                // it out of the running count
+                if (*(volatile int*)&st.exit_pending && take_last(&st.ticket_b, (unsigned)in.nchunks, &flag) &&
+                    thread0()) {
+                    st.exit_pending = 0;
+                    st.ticket_b = 0;
+                    atomicSub(active, 1);
+                }
+                continue;
+            }
             const T alpha = (T)st.alpha;
+            const T* const pk = (kFused && (st.iter & 1)) ? in.p2 : in.p;   // p_k
             const long long t0 = (long long)(c - in.chunk_begin) * kChunk;
             const long long t1 = min(t0 + kChunk, in.len);
             T vr = 0, vrr = 0;
@@ -178,7 +228,7 @@ batch_bicg_kernel(const BatchInst<T>* __restrict__ inst, const int* __restrict__
                     const long long t = tb + (long long)k * nt;
                     if (t < t1) {
                         xv[k] = in.x[t];
-                        pv[k] = in.p[t];
+                        pv[k] = pk[t];
                         rv[k] = in.r[t];
                         qv[k] = in.q[t];
                         rsv[k] = in.rs[t];
@@ -226,40 +276,42 @@ batch_bicg_kernel(const BatchInst<T>* __restrict__ inst, const int* __restrict__
             }
         }
         if (!(ok = grid_sync(gb, G))) break;
-        // the counter changes only in phases A and B: between this barrier
-        // and the next every CTA reads the same value
+        // the counter changes only in phase B: between this barrier and the
+        // next phase B every CTA reads the same value
         if (*(volatile int*)active <= 0) break;
-        // phase C: p = r + beta p; p* = r* + beta p*
-        for (int c = blockIdx.x; c < total_chunks; c += G) {
-            const int i = owner(chunk_begin, ninst, c);
-            const BatchInst<T>& in = inst[i];
-            const BatchState& st = states[in.slot];
-            if (*(volatile const int*)&st.done) continue;
-            const T beta = (T)st.beta;
-            const long long t0 = (long long)(c - in.chunk_begin) * kChunk;
-            const long long t1 = min(t0 + kChunk, in.len);
-            for (long long tb = t0 + tid; tb < t1; tb += (long long)kLd * nt) {
-                T rv[kLd], pv[kLd], rsv[kLd], psv[kLd];
+        if constexpr (!kFused) {
+            // phase C: p = r + beta p; p* = r* + beta p*
+            for (int c = blockIdx.x; c < total_chunks; c += G) {
+                const int i = owner(chunk_begin, ninst, c);
+                const BatchInst<T>& in = inst[i];
+                const BatchState& st = states[in.slot];
+                if (*(volatile const int*)&st.done) continue;
+                const T beta = (T)st.beta;
+                const long long t0 = (long long)(c - in.chunk_begin) * kChunk;
+                const long long t1 = min(t0 + kChunk, in.len);
+                for (long long tb = t0 + tid; tb < t1; tb += (long long)kLd * nt) {
+                    T rv[kLd], pv[kLd], rsv[kLd], psv[kLd];
 #pragma unroll
-                for (int k = 0; k < kLd; ++k) {
-                    const long long t = tb + (long long)k * nt;
-                    if (t < t1) {
-                        rv[k] = in.r[t];
-                        pv[k] = in.p[t];
-                        rsv[k] = in.rs[t];
-                        psv[k] = in.ps[t];
+                    for (int k = 0; k < kLd; ++k) {
+                        const long long t = tb + (long long)k * nt;
+                        if (t < t1) {
+                            rv[k] = in.r[t];
+                            pv[k] = in.p[t];
+                            rsv[k] = in.rs[t];
+                            psv[k] = in.ps[t];
+                        }
+                    }
+#pragma unroll
+                    for (int k = 0; k < kLd; ++k) {
+                        const long long t = tb + (long long)k * nt;
+                        if (t >= t1) break;
+                        in.p[t] = rv[k] + beta * pv[k];
+                        in.ps[t] = rsv[k] + beta * psv[k];
                     }
                 }
-#pragma unroll
-                for (int k = 0; k < kLd; ++k) {
-                    const long long t = tb + (long long)k * nt;
-                    if (t >= t1) break;
-                    in.p[t] = rv[k] + beta * pv[k];
-                    in.ps[t] = rsv[k] + beta * psv[k];
-                }
             }
+            if (!(ok = grid_sync(gb, G))) break;
         }
-        if (!(ok = grid_sync(gb, G))) break;
     }
     if (blockIdx.x == 0 && thread0()) {
         if (!ok) *active = -1;   // barrier gave up
@@ -346,6 +398,7 @@ struct Instance {
     double *fh = nullptr, *res = nullptr, *W = nullptr;
     // FP64 Bi-CG vectors (r is `res`)
     double *rs64 = nullptr, *p64 = nullptr, *ps64 = nullptr, *q64 = nullptr, *qs64 = nullptr;
+    double *p2_64 = nullptr, *ps2_64 = nullptr;   // second direction pair
     // FP32 correction solve vectors
     float *r32 = nullptr, *e = nullptr, *r = nullptr, *rs = nullptr, *p = nullptr, *ps = nullptr, *q = nullptr,
           *qs = nullptr;
@@ -376,7 +429,7 @@ size_t instance_bytes(int n, int nc, int prec) {
     b += 2 * align256(node_count(n) * sizeof(double));                                   // fh, res
     b += align256(node_count(n / 2) * sizeof(double));                                   // W
     if (prec == EXCMG_PRECISION_FP64)
-        b += 5 * align256(node_count(n) * sizeof(double));                               // r*, p, p*, q, q*
+        b += 7 * align256(node_count(n) * sizeof(double));                   // r*, p, p*, q, q*, p2, p*2
     else
         b += 8 * align256(node_count(n) * sizeof(float));                                // r32, e, 6 vectors
     return b;
@@ -457,8 +510,6 @@ int bcuda(excmg_batch* b, cudaError_t e, const char* what) {
     return bfail(b, EXCMG_ERR_CUDA, std::string(what) + ": " + cudaGetErrorString(e));
 }
 
-int slot_of(excmg_batch* /*b*/, Instance* in) { return in->slot; }
-
 void free_instance(excmg_batch* b, Instance* in) {
     if (in->block) {
         cudaFree(in->block);
@@ -507,8 +558,11 @@ int setup_level(excmg_batch* b, Instance* in) {
     if (e == cudaSuccess && l >= 2) {
         const size_t len = node_count(N);
         if (in->prec == EXCMG_PRECISION_FP64) {
-            e = cudaMemsetAsync(in->q64, 0, len * sizeof(double), ctx->stream);
-            if (e == cudaSuccess) e = cudaMemsetAsync(in->qs64, 0, len * sizeof(double), ctx->stream);
+            // (the second direction pair as well: the operator phase writes
+            // its interior entries only)
+            double* const zero[] = {in->q64, in->qs64, in->p2_64, in->ps2_64};
+            for (double* z : zero)
+                if (e == cudaSuccess) e = cudaMemsetAsync(z, 0, len * sizeof(double), ctx->stream);
         } else {
             e = cudaMemsetAsync(in->q, 0, len * sizeof(float), ctx->stream);
             if (e == cudaSuccess) e = cudaMemsetAsync(in->qs, 0, len * sizeof(float), ctx->stream);
@@ -635,6 +689,8 @@ int launch_group(excmg_batch* b, excmg_batch::Group& g, const std::vector<Instan
             t.ps = (T*)in->ps64;
             t.q = (T*)in->q64;
             t.qs = (T*)in->qs64;
+            t.p2 = (T*)in->p2_64;
+            t.ps2 = (T*)in->ps2_64;
         } else {
             t.x = (T*)in->e;
             t.r = (T*)in->r;
@@ -968,6 +1024,8 @@ int excmg_batch_submit(excmg_batch* b, int n_finest, int n_coarsest, int bc_kind
         in->ps64 = (double*)take(n64);
         in->q64 = (double*)take(n64);
         in->qs64 = (double*)take(n64);
+        in->p2_64 = (double*)take(n64);
+        in->ps2_64 = (double*)take(n64);
     } else {
         in->r32 = (float*)take(n32);
         in->e = (float*)take(n32);
