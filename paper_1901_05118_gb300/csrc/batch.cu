@@ -399,6 +399,10 @@ struct Instance {
     // FP64 Bi-CG vectors (r is `res`)
     double *rs64 = nullptr, *p64 = nullptr, *ps64 = nullptr, *q64 = nullptr, *qs64 = nullptr;
     double *p2_64 = nullptr, *ps2_64 = nullptr;   // second direction pair
+    // launched mode (FP64 levels above 64^3): iterations of the current
+    // Bi-CG call enqueued so far, and which direction pair holds p_k
+    long long launched_k = 0;
+    bool dir_in_p2 = false;
     // FP32 correction solve vectors
     float *r32 = nullptr, *e = nullptr, *r = nullptr, *rs = nullptr, *p = nullptr, *ps = nullptr, *q = nullptr,
           *qs = nullptr;
@@ -444,25 +448,21 @@ struct excmg_batch {
     int next_id = 0;
     std::vector<Instance*> live;
     std::vector<Instance*> finished;
-    // device tables (one per value type)
-    BatchInst<float>* d_inst32 = nullptr;
-    BatchInst<double>* d_inst64 = nullptr;
-    int* d_unit_begin = nullptr;
-    int* d_chunk_begin = nullptr;
+    // per-slot Bi-CG states of the cooperative launches (device, pinned host)
     BatchState* d_states = nullptr;
     BatchState* h_states = nullptr;
-    double* d_unit_part = nullptr;
-    double* d_chunk_part = nullptr;
-    int* d_active = nullptr;
-    int* h_active = nullptr;
-    unsigned int* d_barrier = nullptr;
     double* d_norms = nullptr;   // per-slot norms
     double* h_norms = nullptr;
-    size_t unit_cap = 0, chunk_cap = 0;
-    int inner_chunk = 256;       // iterations per batched launch
+    int inner_chunk = 256;       // iterations per cooperative launch
+    int launched_rounds = 16;    // iterations per launched-mode group launch
     std::string last_error;
     long long launches = 0;
     excmg_batch_profile prof{};
+    // launched mode: a Bi-CG state and a partial-sum array per slot, and a
+    // pinned host copy of the states
+    BicgState* d_bstate = nullptr;
+    BicgState* h_bstate = nullptr;
+    double* d_bpart = nullptr;
     std::vector<int> free_slots;
     // One cooperative launch per level group (instances of one precision at
     // one grid size), each on its own stream with its own tables, partial
@@ -471,6 +471,7 @@ struct excmg_batch {
         cudaStream_t stream = nullptr;
         cudaEvent_t start = nullptr, done = nullptr;
         bool busy = false;
+        bool launched = false;   // launched mode: per-member kernels, no grid barrier
         int prec = 0, n = 0, ctas = 0, cand = -1;
         std::vector<Instance*> members;
         void* d_inst = nullptr;        // BatchInst<T>[max_instances]
@@ -753,6 +754,69 @@ int launch_group(excmg_batch* b, excmg_batch::Group& g, const std::vector<Instan
     return EXCMG_OK;
 }
 
+// FP64 levels above the cooperative kernel's range run in launched mode:
+// per member and iteration the single solver's two kernels (the operator
+// launch with the direction update folded in, then the update), with the
+// member's own state and partial sums, so that a large level moves its
+// bytes as fast as in a single solve.
+bool launched_level(const Instance* in) {
+    return in->prec == EXCMG_PRECISION_FP64 && (in->nc << in->level) > kPersistentMaxN;
+}
+
+int launch_group_launched(excmg_batch* b, excmg_batch::Group& g, const std::vector<Instance*>& list) {
+    int st = group_init(b, g);
+    if (st) return st;
+    cudaStream_t s = g.stream;
+    const int K = b->launched_rounds;
+    long long nl = 0;
+    cudaError_t e = cudaStreamWaitEvent(s, b->host_ready, 0);
+    if (e == cudaSuccess) e = cudaEventRecord(g.start, s);
+    for (int k = 0; k < K && e == cudaSuccess; ++k) {
+        for (Instance* in : list) {
+            if (e != cudaSuccess) break;
+            const int N = in->nc << in->level;
+            BicgState* bs = b->d_bstate + in->slot;
+            double* part = b->d_bpart + (size_t)in->slot * kMaxPartials;
+            double* pc = in->dir_in_p2 ? in->p2_64 : in->p64;
+            double* psc = in->dir_in_p2 ? in->ps2_64 : in->ps64;
+            if (in->launched_k == 0) {
+                // p_0 = r_0: the operator pair on the fused schedule's grid
+                e = launch_bicg_stencil_pair(pc, in->q64, psc, in->qs64, N, in->bc, part, bs, s, true);
+            } else {
+                double* pn = in->dir_in_p2 ? in->p64 : in->p2_64;
+                double* psn = in->dir_in_p2 ? in->ps64 : in->ps2_64;
+                e = launch_bicg_stencil_pair_dir(in->res, in->rs64, pc, psc, pn, psn, in->q64, in->qs64, N, in->bc,
+                                                 part, bs, s);
+                in->dir_in_p2 = !in->dir_in_p2;
+                pc = pn;
+            }
+            if (e == cudaSuccess)
+                e = launch_bicg_update(in->u[in->level], pc, in->res, in->q64, in->rs64, in->qs64, node_count(N), part,
+                                       bs, s);
+            ++in->launched_k;
+            nl += 2;
+        }
+    }
+    bnote(b, nl);
+    for (Instance* in : list)
+        if (e == cudaSuccess)
+            e = cudaMemcpyAsync(b->h_bstate + in->slot, b->d_bstate + in->slot, sizeof(BicgState),
+                                cudaMemcpyDeviceToHost, s);
+    if (e == cudaSuccess) e = cudaEventRecord(g.done, s);
+    if (e != cudaSuccess) return bcuda(b, e, "launched batch group");
+    *g.h_active = 0;
+    *g.h_rounds = K;
+    g.busy = true;
+    g.launched = true;
+    g.prec = EXCMG_PRECISION_FP64;
+    g.n = list[0]->nc << list[0]->level;
+    g.ctas = 0;
+    g.cand = -1;
+    g.members = list;
+    for (Instance* in : list) in->in_flight = true;
+    return EXCMG_OK;
+}
+
 excmg_ctx::BatchTune& tune_of(excmg_batch* b, int prec, int n) {
     auto& table = b->ctx->batch_tune;
     auto it = table.find({prec, n});
@@ -771,12 +835,26 @@ excmg_ctx::BatchTune& tune_of(excmg_batch* b, int prec, int n) {
 int harvest(excmg_batch* b, excmg_batch::Group& g) {
     excmg_ctx* ctx = b->ctx;
     cudaError_t e = cudaSuccess;
-    for (Instance* in : g.members)
-        if (e == cudaSuccess)
-            e = cudaMemcpyAsync(b->h_states + in->slot, b->d_states + in->slot, sizeof(BatchState),
-                                cudaMemcpyDeviceToHost, g.stream);
+    if (!g.launched)
+        for (Instance* in : g.members)
+            if (e == cudaSuccess)
+                e = cudaMemcpyAsync(b->h_states + in->slot, b->d_states + in->slot, sizeof(BatchState),
+                                    cudaMemcpyDeviceToHost, g.stream);
     if (e == cudaSuccess) e = cudaStreamSynchronize(g.stream);
     if (e != cudaSuccess) return bcuda(b, e, "batch state read");
+    if (g.launched) {
+        // the members' states came back in the single solver's layout
+        for (Instance* in : g.members) {
+            const BicgState& bs = b->h_bstate[in->slot];
+            BatchState& hs = b->h_states[in->slot];
+            hs.done = bs.done;
+            hs.status = bs.status;
+            hs.iter = bs.iter;
+            hs.rr = bs.rr;
+            hs.rho = bs.rho;
+        }
+        g.launched = false;
+    }
     g.busy = false;
     for (Instance* in : g.members) in->in_flight = false;
     if (*g.h_active < 0) return bfail(b, EXCMG_ERR_TIMEOUT, "grid barrier of the batched Bi-CG gave up");
@@ -880,17 +958,13 @@ int excmg_batch_create(excmg_ctx* ctx, size_t hbm_budget_bytes, int max_instance
     b->budget = hbm_budget_bytes;
     b->max_instances = max_instances;
     const size_t mi = (size_t)max_instances;
-    bool ok = cudaMalloc(&b->d_inst32, mi * sizeof(BatchInst<float>)) == cudaSuccess &&
-              cudaMalloc(&b->d_inst64, mi * sizeof(BatchInst<double>)) == cudaSuccess &&
-              cudaMalloc(&b->d_unit_begin, mi * sizeof(int)) == cudaSuccess &&
-              cudaMalloc(&b->d_chunk_begin, mi * sizeof(int)) == cudaSuccess &&
-              cudaMalloc(&b->d_states, mi * sizeof(BatchState)) == cudaSuccess &&
+    bool ok = cudaMalloc(&b->d_states, mi * sizeof(BatchState)) == cudaSuccess &&
               cudaMallocHost(&b->h_states, mi * sizeof(BatchState)) == cudaSuccess &&
-              cudaMalloc(&b->d_active, sizeof(int)) == cudaSuccess &&
-              cudaMallocHost(&b->h_active, sizeof(int)) == cudaSuccess &&
-              cudaMalloc(&b->d_barrier, 4 * sizeof(unsigned int)) == cudaSuccess &&
               cudaMalloc(&b->d_norms, mi * sizeof(double)) == cudaSuccess &&
               cudaMallocHost(&b->h_norms, mi * sizeof(double)) == cudaSuccess &&
+              cudaMalloc(&b->d_bstate, mi * sizeof(BicgState)) == cudaSuccess &&
+              cudaMallocHost(&b->h_bstate, mi * sizeof(BicgState)) == cudaSuccess &&
+              cudaMalloc(&b->d_bpart, mi * (size_t)kMaxPartials * sizeof(double)) == cudaSuccess &&
               cudaMemset(b->d_states, 0, mi * sizeof(BatchState)) == cudaSuccess;
     if (!ok) {
         cudaGetLastError();
@@ -924,19 +998,13 @@ int excmg_batch_destroy(excmg_batch* b) {
         free_instance(b, in);
         delete in;
     }
-    cudaFree(b->d_inst32);
-    cudaFree(b->d_inst64);
-    cudaFree(b->d_unit_begin);
-    cudaFree(b->d_chunk_begin);
     cudaFree(b->d_states);
     cudaFreeHost(b->h_states);
-    cudaFree(b->d_unit_part);
-    cudaFree(b->d_chunk_part);
-    cudaFree(b->d_active);
-    cudaFreeHost(b->h_active);
-    cudaFree(b->d_barrier);
     cudaFree(b->d_norms);
     cudaFreeHost(b->h_norms);
+    cudaFree(b->d_bstate);
+    cudaFreeHost(b->h_bstate);
+    cudaFree(b->d_bpart);
     delete b;
     return EXCMG_OK;
 }
@@ -1171,6 +1239,22 @@ int excmg_batch_step(excmg_batch* b, int* n_live) {
                 if (e == cudaSuccess)
                     e = cudaMemcpyAsync(b->d_states + slot, b->h_states + slot, sizeof(BatchState),
                                         cudaMemcpyHostToDevice, s);
+                if (launched_level(in)) {
+                    // the same call in the single solver's state layout
+                    BicgState& bs = b->h_bstate[slot];
+                    bs = BicgState{};
+                    bs.rho = b->h_norms[k];
+                    bs.rr = b->h_norms[k];
+                    bs.bnorm = in->fnorm;
+                    bs.tol = level_eps(in, l);
+                    bs.max_iter = cap;
+                    bs.status = kRunning;
+                    in->launched_k = 0;
+                    in->dir_in_p2 = false;
+                    if (e == cudaSuccess)
+                        e = cudaMemcpyAsync(b->d_bstate + slot, b->h_bstate + slot, sizeof(BicgState),
+                                            cudaMemcpyHostToDevice, s);
+                }
             } else {
                 // FP32 correction solve on A e = r / ||r||
                 in->scale = rn;
@@ -1205,6 +1289,16 @@ int excmg_batch_step(excmg_batch* b, int* n_live) {
         for (auto& o : order) {
             const auto key = o.second;
             std::vector<Instance*>& list = ready[key];
+            auto free_group = [&]() -> excmg_batch::Group& {
+                for (auto& g : b->groups)
+                    if (!g.busy) return g;
+                b->groups.emplace_back();
+                return b->groups.back();
+            };
+            if (launched_level(list[0])) {
+                if ((st = launch_group_launched(b, free_group(), list))) return st;
+                continue;
+            }
             int used = 0;
             for (auto& g : b->groups)
                 if (g.busy && g.prec == key.first) used += g.ctas;
@@ -1212,7 +1306,7 @@ int excmg_batch_step(excmg_batch* b, int* n_live) {
             for (auto& g : b->groups)
                 if (g.busy && g.prec != key.first) used += g.ctas;
             const int cap = capacity_of(key.first) - used;
-            if (cap < 1) break;
+            if (cap < 1) continue;
             int cand = -1, units = 0, chunks = 0;
             geometry<double>(list[0], 0, &units, &chunks);
             int ctas = group_ctas(b, key.first, key.second, units > chunks ? units : chunks, (int)list.size(), &cand);
@@ -1220,16 +1314,7 @@ int excmg_batch_step(excmg_batch* b, int* n_live) {
                 ctas = cap;
                 cand = -1;   // not the candidate's shape: not a tuning sample
             }
-            excmg_batch::Group* slot = nullptr;
-            for (auto& g : b->groups)
-                if (!g.busy) {
-                    slot = &g;
-                    break;
-                }
-            if (!slot) {
-                b->groups.emplace_back();
-                slot = &b->groups.back();
-            }
+            excmg_batch::Group* slot = &free_group();
             st = key.first == EXCMG_PRECISION_FP64 ? launch_group<double>(b, *slot, list, ctas, cand)
                                                    : launch_group<float>(b, *slot, list, ctas, cand);
             if (st) return st;
