@@ -73,13 +73,13 @@ int bicg_run(excmg_ctx* ctx, int n, int bc_kind, const double* b, double* x, dou
     const bool fused = ctx->stencil_variant == kStencilExact && stencil_cta_count(n) <= kMaxPartials;
     // small grids run whole iterations in one cooperative launch
     const bool persistent = fused && n <= kPersistentMaxN;
-    // the fused schedule (the default) folds p = r + beta p into the
-    // operator step, which reads the previous directions from one buffer
-    // pair and writes the new ones to the other (neighbouring blocks still
-    // read the old values); the per-node cooperative kernel of the smallest
-    // grids keeps a separate direction-update phase
+    // the fused schedule (the default on the launched levels) folds
+    // p = r + beta p into the operator step, which reads the previous
+    // directions from one buffer pair and writes the new ones to the other
+    // (neighbouring blocks still read the old values); the cooperative
+    // kernel of the small grids keeps a separate direction-update phase
     const bool fuse = ctx->schedule == EXCMG_SCHEDULE_FUSED;
-    const bool dir_fused = fused && fuse && !(persistent && persistent_pointwise(n));
+    const bool dir_fused = fused && fuse && !persistent;
     double* p2 = dir_fused ? ctx_buffer(ctx, "bicg_p2", bytes, &st) : nullptr;
     double* ps2 = (dir_fused && !elide && !st) ? ctx_buffer(ctx, "bicg_ps2", bytes, &st) : nullptr;
     if (st) return st;
@@ -121,8 +121,8 @@ int bicg_run(excmg_ctx* ctx, int n, int bc_kind, const double* b, double* x, dou
             int chunk = 256;
             const int left = max_iter - ctx->host_state->iter;
             if (chunk > left) chunk = left;
-            e = launch_bicg_persistent(x, r, rs, p, ps, p2, ps2, q, qs, n, bc_kind, chunk, ctx->partials, ctx->state,
-                                       ctx->barrier, s, elide, fuse);
+            e = launch_bicg_persistent(x, r, rs, p, ps, q, qs, n, bc_kind, chunk, ctx->partials, ctx->state,
+                                       ctx->barrier, s, elide);
             note_launches(1);
             if (e != cudaSuccess) return ctx_cuda(ctx, e, "cooperative Bi-CG launch");
         }

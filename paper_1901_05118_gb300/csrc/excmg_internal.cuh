@@ -66,17 +66,13 @@ cudaError_t launch_bicg_stencil_pair_dir(const double* r, const double* rs, cons
                                          const double* ps_prev, double* p, double* ps, double* q, double* qs, int n,
                                          int bc_kind, double* partials, BicgState* st, cudaStream_t s);
 // Small grids: whole Bi-CG iterations (up to `iters`) in one cooperative
-// launch with bounded grid barriers; barrier_words: 3 device words.  With
-// fuse (z-march grids only, not persistent_pointwise(n)) the directions
-// alternate between (p, ps) and (p2, ps2), whose boundary entries must be
-// zero; p, ps must hold p_0 on entry.
+// launch with bounded grid barriers; barrier_words: 3 device words.
 constexpr int kPersistentMaxN = 64;
 bool persistent_pointwise(int n);
-// elide: the shadow-elided mode (rs, ps, ps2, qs unused, may be null).
-cudaError_t launch_bicg_persistent(double* x, double* r, double* rs, double* p, double* ps, double* p2, double* ps2,
-                                   double* q, double* qs, int n, int bc_kind, int iters, double* partials,
-                                   BicgState* st, unsigned int* barrier_words, cudaStream_t s, bool elide,
-                                   bool fuse);
+// elide: the shadow-elided mode (rs, ps, qs unused, may be null).
+cudaError_t launch_bicg_persistent(double* x, double* r, double* rs, double* p, double* ps, double* q, double* qs,
+                                   int n, int bc_kind, int iters, double* partials, BicgState* st,
+                                   unsigned int* barrier_words, cudaStream_t s, bool elide);
 // Shadow-elided mode (r* = r, p* = p, A^T p* = A p not stored): the one-field
 // operator launches with sigma = (p, A p) and alpha (the second also forms
 // p = r + beta p_prev into p), and the matching set-up and update kernels.

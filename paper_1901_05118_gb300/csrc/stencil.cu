@@ -172,10 +172,9 @@ stencil_pair_kernel(const double* __restrict__ p, const double* __restrict__ ps,
 // holds a node where r* != r or p*_prev != p_prev runs the general march.
 __device__ __noinline__ double pair_two_field_dir(const double* r, const double* rs, const double* pp,
                                                   const double* psp, double* pn, double* psn, double* q, double* qs,
-                                                  double beta, int n, int sigma, int bx, int by, int kz0,
-                                                  int kz1) {
+                                                  double beta, int n, int sigma, int kz0, int kz1) {
     FxFields fl{{pp, psp}, {q, qs}, {r, rs}, {pn, psn}, beta};
-    return fx_march<2, true, true>(fl, nullptr, n, sigma, bx, by, kz0, kz1);
+    return fx_march<2, true, true>(fl, nullptr, n, sigma, blockIdx.x, blockIdx.y, kz0, kz1);
 }
 
 template <bool kElide>
@@ -195,8 +194,7 @@ stencil_pair_dir_kernel(const double* __restrict__ r, const double* __restrict__
     if constexpr (!kElide) {
         if (!fast) {
             __syncthreads();
-            dot = pair_two_field_dir(r, rs, pp, psp, pn, psn, q, qs, dir.beta, n, sigma, blockIdx.x, blockIdx.y, kz0,
-                                         kz1);
+            dot = pair_two_field_dir(r, rs, pp, psp, pn, psn, q, qs, dir.beta, n, sigma, kz0, kz1);
         }
     }
     __shared__ double sh[32];
@@ -271,8 +269,6 @@ struct BicgVectors {
     double* rs;
     double* p;
     double* ps;
-    double* p2;    // kFuse: second direction pair (p_k in p for even k, in p2
-    double* ps2;   // for odd k)
     double* q;
     double* qs;
 };
@@ -298,11 +294,8 @@ __device__ __forceinline__ double all_partials(const double* partials, int c, do
 // integer operator is symmetric and r*_0 = r_0); v.rs, v.ps, v.ps2, v.qs are
 // unused and the iterates are the same bits as with kElide = false.
 // Three phases per iteration: operator pair with sigma; x, r, r* update
-// with (r*, r) and (r, r); direction update.  kFuse (z-march only): the
-// direction update is folded into the operator phase (p_k = r_k + beta
-// p_{k-1} formed on every loaded node, written to the other direction pair),
-// two phases per iteration.
-template <bool kPointwise, bool kElide, bool kFuse>
+// with (r*, r) and (r, r); direction update.
+template <bool kPointwise, bool kElide>
 __global__ void __launch_bounds__(FX_NT, 2)
 bicg_persistent_kernel(BicgVectors v, size_t len, int n, int sigma, int gx, int gy, int slabs, int kz_per,
                        int iters, double* partials, BicgState* st, GridBarrier gb) {
@@ -345,25 +338,8 @@ bicg_persistent_kernel(BicgVectors v, size_t len, int n, int sigma, int gx, int 
                 // CTA's previous unit is done with the shared buffers
                 __syncthreads();
                 double dd = 0.0;
-                if (kFuse && iter > 0) {
-                    // iteration k = iter >= 1 of the call: p_{k-1} in one
-                    // pair, p_k to the other
-                    const bool odd = iter & 1;
-                    const double* pp = odd ? v.p : v.p2;
-                    const double* psp = odd ? v.ps : v.ps2;
-                    double* pn = odd ? v.p2 : v.p;
-                    double* psn = odd ? v.ps2 : v.ps;
-                    const PairDir dir{v.r, v.rs, pn, psn, beta};
-                    if (pp_march<kElide, kPairCvt, true>(pp, psp, v.q, v.qs, n, sigma, bx, by, kz0, kz1,
-                                                         persistent_stage_smem, &dd, dir)) {
-                        dot += dd;
-                    } else if constexpr (!kElide) {
-                        __syncthreads();
-                        dot += pair_two_field_dir(v.r, v.rs, pp, psp, pn, psn, v.q, v.qs, beta, n, sigma, bx, by,
-                                                  kz0, kz1);
-                    }
-                } else if (pp_march<kElide, kPairCvt>(v.p, v.ps, v.q, v.qs, n, sigma, bx, by, kz0, kz1,
-                                                      persistent_stage_smem, &dd)) {
+                if (pp_march<kElide, kPairCvt>(v.p, v.ps, v.q, v.qs, n, sigma, bx, by, kz0, kz1,
+                                               persistent_stage_smem, &dd)) {
                     dot += dd;
                 } else if constexpr (!kElide) {
                     __syncthreads();
@@ -385,7 +361,7 @@ bicg_persistent_kernel(BicgVectors v, size_t len, int n, int sigma, int gx, int 
         // (entries t, t + S of this thread loaded together,
         // then updated and summed in index order)
         double vr = 0.0, vrr = 0.0;
-        const double* const pcur = (kFuse && (iter & 1)) ? v.p2 : v.p;   // p_k
+        const double* const pcur = v.p;
         bool twin = true;   // as in bicg_update_kernel: vr == vrr so far
         const size_t S = (size_t)G * nthreads;
         constexpr int kB = kPointwise ? 1 : 2;   // entries per thread loaded together
@@ -460,7 +436,7 @@ bicg_persistent_kernel(BicgVectors v, size_t len, int n, int sigma, int gx, int 
             done = 1;
             break;
         }
-        if constexpr (!kFuse) {
+        {
             // phase C: p = r + beta p; p* = r* + beta p*
             for (size_t t0 = (size_t)blockIdx.x * nthreads + tid; t0 < len; t0 += kB * S) {
                 double rv[kB], pv[kB], rsv[kB], psv[kB];
@@ -644,22 +620,15 @@ cudaError_t launch_stencil(const double* u, double* y, const double* b, int n, i
 
 constexpr int kPointwiseMaxN = 40;   // per-node operator on grids up to 40^3
 
-// dynamic shared memory of the z-march variants: the copy-ahead march's
-// stages and tiles (four arrays per slot when the direction update is folded
-// in; the elided fused variant runs the full one's grid with the same size)
-size_t persistent_smem(bool pointwise, bool fuse) {
-    if (pointwise) return 0;
-    return fuse ? pp_smem_bytes<4>() : pp_smem_bytes<2>();
-}
+// dynamic shared memory of the z-march variant: the copy-ahead march's
+// stages and tiles
+size_t persistent_smem(bool pointwise) { return pointwise ? 0 : pp_smem_bytes<2>(); }
 
-int persistent_grid(int n, bool fuse, int* gx, int* gy, int* slabs, int* kz_per) {
+int persistent_grid(int n, int* gx, int* gy, int* slabs, int* kz_per) {
     // at most two CTAs per SM; the elided variants run on the grids of the
     // full ones (same partial sums)
-    const int occ_pt = min(2, resident_per_sm(bicg_persistent_kernel<true, false, false>, FX_NT));
-    const int occ_mz = fuse ? min(2, resident_per_sm(bicg_persistent_kernel<false, false, true>, FX_NT,
-                                                     persistent_smem(false, true)))
-                            : min(2, resident_per_sm(bicg_persistent_kernel<false, false, false>, FX_NT,
-                                                     persistent_smem(false, false)));
+    const int occ_pt = min(2, resident_per_sm(bicg_persistent_kernel<true, false>, FX_NT));
+    const int occ_mz = min(2, resident_per_sm(bicg_persistent_kernel<false, false>, FX_NT, pp_smem_bytes<2>()));
     const int sms = device_sms();
     const int m = n - 1;
     *gx = (m + FX_TX - 1) / FX_TX;
@@ -678,38 +647,28 @@ int persistent_grid(int n, bool fuse, int* gx, int* gy, int* slabs, int* kz_per)
 
 bool persistent_pointwise(int n) { return n <= kPointwiseMaxN; }
 
-cudaError_t launch_bicg_persistent(double* x, double* r, double* rs, double* p, double* ps, double* p2, double* ps2,
-                                   double* q, double* qs, int n, int bc_kind, int iters, double* partials,
-                                   BicgState* st, unsigned int* barrier_words, cudaStream_t s, bool elide,
-                                   bool fuse) {
+cudaError_t launch_bicg_persistent(double* x, double* r, double* rs, double* p, double* ps, double* q, double* qs,
+                                   int n, int bc_kind, int iters, double* partials, BicgState* st,
+                                   unsigned int* barrier_words, cudaStream_t s, bool elide) {
     const bool pw = persistent_pointwise(n);
-    fuse = fuse && !pw;
     int gx, gy, slabs, kz_per;
-    const int G = persistent_grid(n, fuse, &gx, &gy, &slabs, &kz_per);
+    const int G = persistent_grid(n, &gx, &gy, &slabs, &kz_per);
     cudaError_t e = cudaMemsetAsync(barrier_words, 0, 3 * sizeof(unsigned int), s);
     if (e != cudaSuccess) return e;
-    BicgVectors v{x, r, rs, p, ps, p2, ps2, q, qs};
+    BicgVectors v{x, r, rs, p, ps, q, qs};
     size_t len = node_count(n);
     int sigma = bc_kind == 1 ? 1 : -1;
     GridBarrier gb{barrier_words, barrier_words + 1, (int*)(barrier_words + 2), kBarrierSpinLimit};
     void* args[] = {&v, &len, &n, &sigma, &gx, &gy, &slabs, &kz_per, &iters, &partials, &st, &gb};
     const void* fn;
-    const size_t smem = persistent_smem(pw, fuse);
     if (pw) {
-        fn = elide ? (const void*)bicg_persistent_kernel<true, true, false>
-                   : (const void*)bicg_persistent_kernel<true, false, false>;
-    } else if (fuse) {
-        opt_in_smem(bicg_persistent_kernel<false, true, true>, smem);
-        opt_in_smem(bicg_persistent_kernel<false, false, true>, smem);
-        fn = elide ? (const void*)bicg_persistent_kernel<false, true, true>
-                   : (const void*)bicg_persistent_kernel<false, false, true>;
+        fn = elide ? (const void*)bicg_persistent_kernel<true, true> : (const void*)bicg_persistent_kernel<true, false>;
     } else {
-        opt_in_smem(bicg_persistent_kernel<false, true, false>, smem);
-        opt_in_smem(bicg_persistent_kernel<false, false, false>, smem);
-        fn = elide ? (const void*)bicg_persistent_kernel<false, true, false>
-                   : (const void*)bicg_persistent_kernel<false, false, false>;
+        opt_in_smem(bicg_persistent_kernel<false, true>, pp_smem_bytes<2>());
+        opt_in_smem(bicg_persistent_kernel<false, false>, pp_smem_bytes<2>());
+        fn = elide ? (const void*)bicg_persistent_kernel<false, true> : (const void*)bicg_persistent_kernel<false, false>;
     }
-    return cudaLaunchCooperativeKernel(fn, dim3(G), dim3(FX_TX, FX_TY, 1), args, smem, s);
+    return cudaLaunchCooperativeKernel(fn, dim3(G), dim3(FX_TX, FX_TY, 1), args, persistent_smem(pw), s);
 }
 
 cudaError_t launch_bicg_stencil_pair_dir(const double* r, const double* rs, const double* p_prev,
