@@ -288,10 +288,12 @@ int excmg_dsolve(const excmg_level *level, const double *fh, double *u);
  * or in the mixed-precision form (FP64 refinement around FP32 Bi-CG
  * correction solves, see EXCMG_PRECISION_MIXED).  Every instance keeps its
  * level hierarchy resident; the Bi-CG iterations of the instances that need
- * them run in one cooperative launch per level group (instances of one
- * precision at one grid size), each group on its own stream and taken back
- * as soon as it completes.  Instances may be submitted at any time and leave
- * when done, so the batch refills continuously. */
+ * them run per level group (instances of one precision at one grid size),
+ * each group on its own stream and taken back as soon as it completes: one
+ * cooperative launch for all members of a group on grids up to 64^3 (and
+ * for FP32 correction solves), the single solver's kernels per member on
+ * larger FP64 grids.  Instances may be submitted at any time and leave when
+ * done, so the batch refills continuously. */
 typedef struct excmg_batch excmg_batch;
 
 /* hbm_budget_bytes caps the device memory all live instances may hold

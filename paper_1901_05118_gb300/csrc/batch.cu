@@ -1,16 +1,21 @@
 // Many independent EXCMG solves on one GPU at once.
 //
-// Each instance keeps its whole level hierarchy (Alg. 1) and its FP64/FP32
-// refinement state resident on the device and moves through a small state
-// machine: direct solves of the two coarsest grids, then per Bi-CG level
-// EXP_finite + right-hand side, FP64 residual, FP32 correction solve,
-// FP64 update, until the level's tolerance (or the stagnation rule) is met,
-// and finally EXP_true.  The expensive part -- the FP32 Bi-CG iterations of
-// the correction solves (Alg. 2, M = I, r*_0 = r_0) -- runs for ALL
-// instances that are in that phase in one cooperative launch: CTAs take
-// operator tiles and vector chunks from every instance, instances advance
-// in lock step one iteration per grid-barrier round, and each instance's
-// scalars are formed by the CTA that completes its last tile / chunk.
+// Each instance keeps its whole level hierarchy (Alg. 1) and its Bi-CG (FP64)
+// or refinement (FP64 around FP32 correction solves) state resident on the
+// device and moves through a small state machine: direct solves of the two
+// coarsest grids, then per Bi-CG level EXP_finite + right-hand side, FP64
+// true residual, Bi-CG call (or FP32 correction solve and FP64 update),
+// until the level's tolerance (or the stagnation rule) is met, and finally
+// EXP_true.  The Bi-CG iterations (Alg. 2, M = I, r*_0 = r_0) of the
+// instances waiting for them run per level group -- instances of one
+// precision at one grid size -- each group on its own stream:
+//  * grids up to 64^3 and FP32 correction solves: one cooperative launch for
+//    all members; CTAs take operator tiles and vector chunks from every
+//    member, members advance in lock step one iteration per grid-barrier
+//    round, and each member's scalars are formed by the CTA that completes
+//    its last tile / chunk;
+//  * FP64 grids above 64^3 (launched mode): per member and round the single
+//    solver's fused operator and update kernels with the member's own state.
 // Instances can be submitted at any time (the engine admits them against
 // its device-memory budget) and leave as soon as they are done, so the
 // batch continuously refills: the same engine serves the fixed batch and

@@ -1,5 +1,7 @@
-"""The batch engine: many EXCMG solves resident on one GPU, their FP32
-correction solves advanced together in one cooperative launch."""
+"""The batch engine: many EXCMG solves resident on one GPU, their Bi-CG
+iterations advanced per level group (one cooperative launch for small grids
+and FP32 correction solves, the single solver's kernels per member on large
+FP64 grids)."""
 import numpy as np
 import pytest
 
