@@ -62,6 +62,8 @@ def parse(argv=None):
     ap.add_argument("--mixed-inner", default="",
                     help="comma-separated inner_tol:cap pairs of the FP32 correction solves to sweep at --tol")
     ap.add_argument("--no-batch", action="store_true", help="skip the 64-instance batched leg")
+    ap.add_argument("--batch-mixed", action="store_true",
+                    help="batched leg: also the mixed-precision form (about 90 s more)")
     ap.add_argument("--no-serve", action="store_true", help="skip the request-stream leg")
     ap.add_argument("--serve-requests", type=int, default=120)
     ap.add_argument("--no-elided", action="store_true", help="skip the shadow-elided variant leg")
@@ -172,13 +174,19 @@ class OracleSampler:
     workload and scaled to one whole solve with the oracle's own counts.
 
     A whole oracle solve of the 512^3 workload takes minutes, so one timed
-    sample is: on every Bi-CG level N = 4 nc .. n, one Bi-CG iteration of the
-    oracle (the time of a 1-iteration call minus that of a 0-iteration call
-    on the level's own right-hand side), times the oracle's iterations on that
-    level; plus, measured once, each level's fixed work of Alg. 1 (assembly
-    of f_h, EXP_finite, the true residuals of the WHILE loop).  The counts are
-    the oracle's own from a whole run (oracle/excmg_512_counts.json); without
-    that file for this workload there is no value."""
+    sample is: on every Bi-CG level N = 4 nc .. min(n, 256), one Bi-CG
+    iteration of the oracle (the time of a k-iteration call minus that of a
+    0-iteration call on the level's own right-hand side, over at least
+    0.2 s), times the oracle's iterations on that level; plus each level's
+    fixed work of Alg. 1 (assembly of f_h, EXP_finite, the true residuals of
+    the WHILE loop), timed once on min(N, 128).  Levels above the timed size
+    take the timed size's seconds scaled by their unknowns (the oracle's
+    loops are linear in them).  The counts are the oracle's own from a whole
+    run (oracle/excmg_512_counts.json); without that file for this workload
+    there is no value."""
+
+    ITER_MAX_N = 256
+    FIXED_MAX_N = 128
 
     def __init__(self, n: int, nc: int, threads: int):
         import oracle
@@ -209,10 +217,21 @@ class OracleSampler:
             self.data[key] = (self.oracle.assemble_rhs(N, bc, f, g1, g2), np.ascontiguousarray(g1))
         return self.data[key]
 
+    @staticmethod
+    def _scale(N, M):
+        """Unknowns of level N over those of level M."""
+        return ((N - 1) / (M - 1)) ** 3
+
     def iteration_s(self, N, bc):
         """Seconds per oracle Bi-CG iteration on level N: (time of a k-iteration
         call - time of a 0-iteration call) / k, k grown until the difference
-        is at least 0.2 s (at most 256 iterations)."""
+        is at least 0.2 s (at most 256 iterations); above ITER_MAX_N, that
+        size's time scaled by the unknowns."""
+        if N > self.ITER_MAX_N:
+            return self.iteration_s(self.ITER_MAX_N, bc) * self._scale(N, self.ITER_MAX_N)
+        key = ("it", N, bc)
+        if key in self.fixed:
+            return self.fixed[key]
         fh, g1 = self._level(N, bc)
         t0 = time.perf_counter()
         self.oracle.bicg(N, bc, fh, g1, 0.0, max_iter=0)
@@ -223,11 +242,21 @@ class OracleSampler:
             self.oracle.bicg(N, bc, fh, g1, 0.0, max_iter=k)
             run = time.perf_counter() - t0 - setup
             if run >= 0.2 or k >= 256:
-                return max(run / k, 1e-9)
+                self.fixed[key] = max(run / k, 1e-9)
+                return self.fixed[key]
             k *= 4
 
     def fixed_s(self, N, bc, calls):
-        """Alg. 1's work on level N besides the Bi-CG iterations (timed once)."""
+        """Alg. 1's work on level N besides the Bi-CG iterations (timed once,
+        on min(N, FIXED_MAX_N) and scaled by the unknowns)."""
+        if N > self.FIXED_MAX_N:
+            M = self.FIXED_MAX_N
+            setup, resid = self._fixed_parts(M, bc)
+            return (setup + (calls + 1) * resid) * self._scale(N, M)
+        setup, resid = self._fixed_parts(N, bc)
+        return setup + (calls + 1) * resid
+
+    def _fixed_parts(self, N, bc):
         key = (N, bc)
         if key not in self.fixed:
             o = self.oracle
@@ -241,14 +270,17 @@ class OracleSampler:
             o.residual_norm(N, bc, fh, w)
             t2 = time.perf_counter()
             self.fixed[key] = (t1 - t0, t2 - t1)
-        setup, resid = self.fixed[key]
-        return setup + (calls + 1) * resid
+        return self.fixed[key]
 
     def solve_s(self, bc):
         """Seconds of one oracle solve of the workload with kind bc, and the
         per-level breakdown; (None, None) without the oracle's counts."""
         if self.counts is None:
             return None, None
+        # iteration times are taken afresh by every call (the fixed work,
+        # timed once, is kept)
+        for key in [k for k in self.fixed if k[0] == "it"]:
+            del self.fixed[key]
         lv = {L["n"]: L for L in self.counts[bc]["levels"]}
         total, parts = 0.0, []
         for N in self.levels:
@@ -260,10 +292,11 @@ class OracleSampler:
 
     def describe(self):
         return (f"oracle (plain C, FP64) on {self.threads} host threads: per Bi-CG level N = "
-                f"{self.levels[0]}..{self.levels[-1]}, timed Bi-CG iterations (at least 0.2 s of them) x the oracle's own iterations "
+                f"{self.levels[0]}..{self.levels[-1]}, timed Bi-CG iterations (at least 0.2 s of them; levels above "
+                f"{self.ITER_MAX_N}^3 scaled by their unknowns from {self.ITER_MAX_N}^3) x the oracle's own iterations "
                 f"on that level (oracle/excmg_512_counts.json, from a whole oracle solve), plus each level's "
-                f"assembly, EXP_finite and true residuals timed once; the direct solves of the two coarsest "
-                f"grids are not counted")
+                f"assembly, EXP_finite and true residuals timed once on min(N, {self.FIXED_MAX_N})^3 and scaled by the "
+                f"unknowns; the direct solves of the two coarsest grids are not counted")
 
 
 def run_reference(args):
@@ -456,13 +489,22 @@ def run_ours(args):
         e2, e3 = ev(), ev()
         e2.record(stream)
 
+        def sliced_copy(dst, src):
+            # 64 MB slices: the solve's own small state reads share the copy
+            # engines and slip in between slices instead of waiting a whole
+            # gigabyte copy out
+            dv, sv = dst.view(-1), src.view(-1)
+            step = 1 << 23
+            for a in range(0, dv.numel(), step):
+                dv[a:a + step].copy_(sv[a:a + step], non_blocking=True)
+
         def prefetch(i):
             k = i % 2
             with torch.cuda.stream(s_h2d):
                 s_h2d.wait_stream(stream)          # set k's previous solve has finished
                 h2d_start[i].record(s_h2d)
                 for key in ("f", "g1", f"g2_{order[i]}"):
-                    sets[k][key].copy_(host[key], non_blocking=True)
+                    sliced_copy(sets[k][key], host[key])
                 inputs_ready[i].record(s_h2d)
 
         prefetch(0)
@@ -479,7 +521,7 @@ def run_ours(args):
             with torch.cuda.stream(s_d2h):
                 s_d2h.wait_event(solve_done[i])
                 d2h_start[i].record(s_d2h)
-                u_hosts[k].copy_(outs[k], non_blocking=True)
+                sliced_copy(u_hosts[k], outs[k])
                 result_read[i].record(s_d2h)
         stream.wait_event(result_read[ns - 1])
         e3.record(stream)
@@ -656,9 +698,10 @@ def precision_leg(args, B, problems, ctx, dev, stream, barrier, world):
 
 def batched_leg(args, B, problems, ctx, dev):
     """64 independent solves, finest grids drawn (seeded) from 32..128 with
-    coarsest 8/6/8/6/8, mixed kinds of boundary data, u = four random sines;
-    FP32 correction solves in FP64 refinement, tol 1e-10.  All submitted at
-    once to the batch engine; compared with the same 64 solved one by one."""
+    coarsest 8/6/8/6/8, mixed kinds of boundary data, u = four random sines,
+    tol 1e-10, in FP64 (and with --batch-mixed also with FP32 correction
+    solves in FP64 refinement).  All submitted at once to the batch engine;
+    compared with the same 64 solved one by one."""
     import torch
 
     rng = np.random.Generator(np.random.PCG64(0))
@@ -693,7 +736,7 @@ def batched_leg(args, B, problems, ctx, dev):
             warm.append(i)
     out = {"workload": "64 instances, n from {32,48,64,96,128} (PCG64 seed 0), coarsest 8/6/8/6/8, kinds mixed, "
                        "u = 4 random sines, tol 1e-10 per level"}
-    for precision in ("fp64", "mixed"):
+    for precision in (("fp64", "mixed") if args.batch_mixed else ("fp64",)):
         # untimed: the DSOLVE inverses, then one whole pass so that the
         # context's grid-size tuner has settled every level group
         run_batch(warm, precision)

@@ -15,7 +15,7 @@ int interior_norm(excmg_ctx* ctx, int n, const double* a, double* out) {
     cudaError_t e = launch_dot(a, a, len, ctx->partials, ctx->ticket, ctx->scalar, ctx->stream);
     note_launches(1);
     if (e == cudaSuccess)
-        e = cudaMemcpyAsync(ctx->host_scalar, ctx->scalar, sizeof(double), cudaMemcpyDeviceToHost, ctx->stream);
+        e = ctx_read_back(ctx, ctx->host_scalar, ctx->scalar, sizeof(double));
     if (e == cudaSuccess) e = cudaStreamSynchronize(ctx->stream);
     if (e != cudaSuccess) return ctx_cuda(ctx, e, "norm");
     *out = sqrt(*ctx->host_scalar);
@@ -28,7 +28,7 @@ int unknowns_norm(excmg_ctx* ctx, int n, const double* a, double* out) {
     cudaError_t e = launch_interior_dot(a, n, ctx->partials, ctx->ticket, ctx->scalar, ctx->stream);
     note_launches(1);
     if (e == cudaSuccess)
-        e = cudaMemcpyAsync(ctx->host_scalar, ctx->scalar, sizeof(double), cudaMemcpyDeviceToHost, ctx->stream);
+        e = ctx_read_back(ctx, ctx->host_scalar, ctx->scalar, sizeof(double));
     if (e == cudaSuccess) e = cudaStreamSynchronize(ctx->stream);
     if (e != cudaSuccess) return ctx_cuda(ctx, e, "norm");
     *out = sqrt(*ctx->host_scalar);
@@ -114,7 +114,7 @@ int bicg_run(excmg_ctx* ctx, int n, int bc_kind, const double* b, double* x, dou
     const int* done = &ctx->state->done;
     if (persistent) {
         for (;;) {
-            e = cudaMemcpyAsync(ctx->host_state, ctx->state, sizeof(BicgState), cudaMemcpyDeviceToHost, s);
+            e = ctx_read_back(ctx, ctx->host_state, ctx->state, sizeof(BicgState));
             if (e == cudaSuccess) e = cudaStreamSynchronize(s);
             if (e != cudaSuccess) return ctx_cuda(ctx, e, "Bi-CG state read");
             if (ctx->host_state->done) break;
@@ -140,7 +140,7 @@ int bicg_run(excmg_ctx* ctx, int n, int bc_kind, const double* b, double* x, dou
     double* pn = p2;           // buffer pair the next directions go to
     double* psn = ps2;
     for (; !persistent;) {
-        e = cudaMemcpyAsync(ctx->host_state, ctx->state, sizeof(BicgState), cudaMemcpyDeviceToHost, s);
+        e = ctx_read_back(ctx, ctx->host_state, ctx->state, sizeof(BicgState));
         if (e == cudaSuccess) e = cudaStreamSynchronize(s);
         if (e != cudaSuccess) return ctx_cuda(ctx, e, "Bi-CG state read");
         if (ctx->profile && batch > 0) {

@@ -100,6 +100,26 @@ cudaStream_t ctx_capture_stream(excmg_ctx* ctx) {
 }
 
 // A named workspace buffer of at least `bytes`, grown on demand.
+namespace {
+// One warp copies `words` 8-byte words from device memory into mapped host
+// memory (stores over the host link, visible to the host once the stream
+// has been synchronised).
+__global__ void read_back_kernel(const unsigned long long* __restrict__ src, unsigned long long* dst, int words) {
+    for (int i = threadIdx.x; i < words; i += blockDim.x) dst[i] = src[i];
+}
+}  // namespace
+
+cudaError_t ctx_read_back(excmg_ctx* ctx, void* host_mirror, const void* dev_src, size_t bytes) {
+    void* dst = nullptr;
+    if (host_mirror == ctx->host_state) dst = ctx->host_state_dev;
+    else if (host_mirror == ctx->host_scalar) dst = ctx->host_scalar_dev;
+    if (!dst || bytes % 8 != 0) return cudaErrorInvalidValue;
+    read_back_kernel<<<1, 32, 0, ctx->stream>>>((const unsigned long long*)dev_src, (unsigned long long*)dst,
+                                                (int)(bytes / 8));
+    note_launches(1);
+    return cudaGetLastError();
+}
+
 double* ctx_buffer(excmg_ctx* ctx, const char* name, size_t bytes, int* status) {
     excmg_buffer& b = ctx->buffers[name];
     if (b.bytes >= bytes && b.ptr) return (double*)b.ptr;
@@ -173,8 +193,10 @@ int excmg_ctx_create(void* cuda_stream, size_t hbm_budget_bytes, excmg_ctx** out
               cudaMalloc(&c->state, sizeof(BicgState)) == cudaSuccess &&
               cudaMalloc(&c->barrier, 4 * sizeof(unsigned int)) == cudaSuccess &&
               cudaMemset(c->barrier, 0, 4 * sizeof(unsigned int)) == cudaSuccess &&
-              cudaMallocHost(&c->host_state, sizeof(BicgState)) == cudaSuccess &&
-              cudaMallocHost(&c->host_scalar, 8 * sizeof(double)) == cudaSuccess &&
+              cudaHostAlloc(&c->host_state, sizeof(BicgState), cudaHostAllocMapped) == cudaSuccess &&
+              cudaHostAlloc(&c->host_scalar, 8 * sizeof(double), cudaHostAllocMapped) == cudaSuccess &&
+              cudaHostGetDevicePointer((void**)&c->host_state_dev, c->host_state, 0) == cudaSuccess &&
+              cudaHostGetDevicePointer((void**)&c->host_scalar_dev, c->host_scalar, 0) == cudaSuccess &&
               cudaMemset(c->ticket, 0, sizeof(unsigned int)) == cudaSuccess &&
               cudaMemset(c->state, 0, sizeof(BicgState)) == cudaSuccess;
     if (!ok) {

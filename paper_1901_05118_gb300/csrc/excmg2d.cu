@@ -384,7 +384,7 @@ double host_norm(excmg_ctx* ctx, const double* a, size_t len, int* st) {
     cudaError_t e = launch_dot(a, a, len, ctx->partials, ctx->ticket, ctx->scalar, ctx->stream);
     note_launches(1);
     if (e == cudaSuccess)
-        e = cudaMemcpyAsync(ctx->host_scalar, ctx->scalar, sizeof(double), cudaMemcpyDeviceToHost, ctx->stream);
+        e = ctx_read_back(ctx, ctx->host_scalar, ctx->scalar, sizeof(double));
     if (e == cudaSuccess) e = cudaStreamSynchronize(ctx->stream);
     if (e != cudaSuccess) {
         *st = ctx_cuda(ctx, e, "2D norm");
@@ -439,7 +439,7 @@ int bicg2d_run(excmg_ctx* ctx, int n, int bc_kind, const double* b, double* x, d
     const int sg = bc_kind == 1 ? 1 : -1;
     if (check_every < 1) check_every = 1;
     for (;;) {
-        e = cudaMemcpyAsync(ctx->host_state, ctx->state, sizeof(BicgState), cudaMemcpyDeviceToHost, s);
+        e = ctx_read_back(ctx, ctx->host_state, ctx->state, sizeof(BicgState));
         if (e == cudaSuccess) e = cudaStreamSynchronize(s);
         if (e != cudaSuccess) return ctx_cuda(ctx, e, "2D Bi-CG state read");
         if (ctx->host_state->done) break;

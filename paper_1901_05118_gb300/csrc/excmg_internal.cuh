@@ -43,6 +43,7 @@ struct BicgState {
     unsigned int ticket;   // last-block counter of the reductions
     int pad1[3];
 };
+static_assert(sizeof(BicgState) % 8 == 0, "read back in 8-byte words");
 enum { kRunning = 0, kConverged = 1, kCapped = 2, kBreakdown = 3, kTimeout = 4 };
 
 // ------------------------------------------------------------- kernels
@@ -157,8 +158,14 @@ struct excmg_ctx {
     double* scalar = nullptr;                 // one-off reduction results (8 doubles)
     excmg::BicgState* state = nullptr;        // device
     unsigned int* barrier = nullptr;          // device words of the cooperative solver's grid barrier
-    excmg::BicgState* host_state = nullptr;   // pinned host mirror
-    double* host_scalar = nullptr;            // pinned host mirror of `scalar`
+    // pinned, mapped host mirrors of `state` and `scalar` and their device
+    // addresses: a one-CTA kernel writes them (ctx_read_back), so reading the
+    // state back uses no copy engine and never queues behind a caller's large
+    // copies
+    excmg::BicgState* host_state = nullptr;
+    double* host_scalar = nullptr;
+    excmg::BicgState* host_state_dev = nullptr;
+    double* host_scalar_dev = nullptr;
     int stencil_variant = excmg::kStencilExact;
     int shadow_mode = EXCMG_SHADOW_FULL;
     int schedule = EXCMG_SCHEDULE_FUSED;
@@ -207,6 +214,10 @@ cudaStream_t ctx_capture_stream(excmg_ctx* ctx);
 // Workspace helpers (capi.cu).
 int ctx_fail(excmg_ctx* ctx, int status, const std::string& msg);
 int ctx_cuda(excmg_ctx* ctx, cudaError_t err, const char* what);
+// Enqueue on ctx's stream a copy of `bytes` (a multiple of 8) from device
+// memory to one of the context's mapped host mirrors (host_state or
+// host_scalar), written by a kernel; the caller synchronises the stream.
+cudaError_t ctx_read_back(excmg_ctx* ctx, void* host_mirror, const void* dev_src, size_t bytes);
 double* ctx_buffer(excmg_ctx* ctx, const char* name, size_t bytes, int* status);
 // Bi-CG driver (bicg.cu): iterates on the context's stream.
 int bicg_run(excmg_ctx* ctx, int n, int bc_kind, const double* b, double* x, double tol,

@@ -219,7 +219,7 @@ static int bicg32_run(excmg_ctx* ctx, int n, int bc_kind, const float* b32, floa
     if (err != cudaSuccess) return ctx_cuda(ctx, err, "FP32 Bi-CG setup");
     if (check_every < 1) check_every = 1;
     for (;;) {
-        err = cudaMemcpyAsync(ctx->host_state, ctx->state, sizeof(BicgState), cudaMemcpyDeviceToHost, s);
+        err = ctx_read_back(ctx, ctx->host_state, ctx->state, sizeof(BicgState));
         if (err == cudaSuccess) err = cudaStreamSynchronize(s);
         if (err != cudaSuccess) return ctx_cuda(ctx, err, "FP32 Bi-CG state read");
         if (ctx->host_state->done) break;
