@@ -33,9 +33,10 @@ namespace excmg {
 namespace {
 
 constexpr int kCC = 16;        // CTAs per cluster
-constexpr int kCT = 512;       // threads per CTA
+constexpr int kCT = 512;      // threads per CTA
 constexpr int kCMaxM = 31;     // largest N - 1
 constexpr int kCVec = 7;       // x, r, r*, p, p*, q, q*
+constexpr int kCMaxPlanes = (kCMaxM + kCC - 1) / kCC;   // planes per CTA
 enum { VX = 0, VR, VRS, VP, VPS, VQ, VQS };
 
 __device__ __forceinline__ unsigned cl_rank() {
@@ -51,9 +52,11 @@ __device__ __forceinline__ unsigned cl_map(unsigned addr, unsigned rank) {
     return d;
 }
 
+// (volatile: never merged with or moved across another load of the same
+// address; the cluster barriers order it against the writes)
 __device__ __forceinline__ double cl_ld(unsigned addr) {
     double v;
-    asm volatile("ld.shared::cluster.f64 %0, [%1];" : "=d"(v) : "r"(addr) : "memory");
+    asm volatile("ld.shared::cluster.f64 %0, [%1];" : "=d"(v) : "r"(addr));
     return v;
 }
 
@@ -72,19 +75,25 @@ struct ClusterGeom {
     }
 };
 
-// y at (i, j, k) = A u (u = vector v, held by the cluster), the per-node
-// integer evaluation: the same taps, scale and integer sums as fx_point.
-__device__ __forceinline__ double cl_point(const ClusterGeom& g, int v, int sigma, int i, int j, int k) {
+// Cluster addresses of node (1, 1) of planes k0 - 2 .. k0 + P + 1 of vector
+// v (0 outside the interior), the planes a CTA owning k0 .. k0 + P - 1 reads.
+__device__ __forceinline__ unsigned cl_plane_base(const ClusterGeom& g, int v, int kk) {
+    if (kk < 1 || kk > g.m) return 0u;
+    const int owner = (kk - 1) / g.P, pl = (kk - 1) - owner * g.P;
+    return cl_map(g.base + g.off(v, pl, 1, 1), (unsigned)owner);
+}
+
+// y at (i, j, k) = A u (u held by the cluster; pbase: the cluster addresses
+// of planes k - 2 .. k + 2), the per-node integer evaluation: the same taps,
+// scale and integer sums as fx_point.
+__device__ __forceinline__ double cl_point(const ClusterGeom& g, const unsigned* pbase, int sigma, int i, int j, int k) {
     const int m = g.m;
     unsigned pb[5];
     bool pz[5];
 #pragma unroll
     for (int d = 0; d < 5; ++d) {
-        const int kk = k + d - 2;
-        pz[d] = kk >= 1 && kk <= m;
-        const int owner = pz[d] ? (kk - 1) / g.P : 0;
-        const int pl = pz[d] ? (kk - 1) - owner * g.P : 0;
-        pb[d] = pz[d] ? cl_map(g.base + g.off(v, pl, 1, 1), (unsigned)owner) : 0u;
+        pb[d] = pbase[d];
+        pz[d] = pb[d] != 0u;
     }
     auto val = [&](int a, int b, int d) -> double {
         if (a < 1 || a > m || b < 1 || b > m || !pz[d]) return 0.0;
@@ -149,6 +158,7 @@ bicg_cluster_kernel(double* __restrict__ x, double* __restrict__ r, double* __re
     extern __shared__ __align__(16) double csm[];
     __shared__ double sh[32];
     __shared__ double bc[4];
+    __shared__ unsigned pbase[2][kCMaxPlanes + 4];   // p and p* planes k0 - 2 .. k0 + P + 1
     const int m = n - 1, P = (m + kCC - 1) / kCC, mm = m * m;
     const int rank = (int)cl_rank();
     const int k0 = 1 + rank * P;
@@ -185,6 +195,10 @@ bicg_cluster_kernel(double* __restrict__ x, double* __restrict__ r, double* __re
                 diff = 1.0;
         }
     }
+    if (tid < P + 4) {
+        pbase[0][tid] = cl_plane_base(g, VP, k0 - 2 + tid);
+        pbase[1][tid] = cl_plane_base(g, VPS, k0 - 2 + tid);
+    }
     double tw[4] = {diff, 0.0, 0.0, 0.0};
     cl_reduce(tw, 1, 1, red, sh, bc);   // also: every CTA's vectors are loaded
     const bool twin = elide || tw[0] == 0.0;
@@ -195,12 +209,12 @@ bicg_cluster_kernel(double* __restrict__ x, double* __restrict__ r, double* __re
         for (int t = tid; t < nown; t += kCT) {
             const int pl = t / mm, rem = t - pl * mm;
             const int j = rem / m + 1, i = rem - (j - 1) * m + 1, k = k0 + pl;
-            const double qv = cl_point(g, VP, sigma, i, j, k);
+            const double qv = cl_point(g, &pbase[0][pl], sigma, i, j, k);
             sm(VQ, t) = qv;
             if (twin) {
                 a[0] += sm(VP, t) * qv;
             } else {
-                sm(VQS, t) = cl_point(g, VPS, sigma, i, j, k);
+                sm(VQS, t) = cl_point(g, &pbase[1][pl], sigma, i, j, k);
                 a[0] += sm(VPS, t) * qv;
             }
         }
