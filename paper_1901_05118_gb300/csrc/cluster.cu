@@ -83,46 +83,49 @@ __device__ __forceinline__ unsigned cl_plane_base(const ClusterGeom& g, int v, i
     return cl_map(g.base + g.off(v, pl, 1, 1), (unsigned)owner);
 }
 
-// y at (i, j, k) = A u (u held by the cluster; pbase: the cluster addresses
-// of planes k - 2 .. k + 2), the per-node integer evaluation: the same taps,
-// scale and integer sums as fx_point.
-__device__ __forceinline__ double cl_point(const ClusterGeom& g, const unsigned* pbase, int sigma, int i, int j, int k) {
-    const int m = g.m;
-    unsigned pb[5];
-    bool pz[5];
-#pragma unroll
-    for (int d = 0; d < 5; ++d) {
-        pb[d] = pbase[d];
-        pz[d] = pb[d] != 0u;
+// The CTA's operator tile: planes k0 - 2 .. k0 + P + 1 of a vector (pbase:
+// their cluster addresses, 0 outside the interior) as 64-bit integers on one
+// power-of-two scale -- the largest exponent among them -- with a two-node
+// zero border in x and y.  Returns the scale exponent (0x7FF: a value is
+// not finite).  Border entries are zeroed by the caller once per launch.
+__device__ __forceinline__ int cl_fill_tile(const unsigned* pbase, int P, int m, long long* tile, int* wred) {
+    const int mm = m * m, tot = (P + 4) * mm, tid = threadIdx.x, tw = m + 4;
+    int e = 0;
+    for (int t = tid; t < tot; t += kCT) {
+        const int d = t / mm, rem = t - d * mm;
+        const unsigned b = pbase[d];
+        e = max(e, b ? exponent_of(cl_ld(b + 8u * (unsigned)rem)) : 0);
     }
-    auto val = [&](int a, int b, int d) -> double {
-        if (a < 1 || a > m || b < 1 || b > m || !pz[d]) return 0.0;
-        return cl_ld(pb[d] + 8u * (unsigned)((b - 1) * m + (a - 1)));
-    };
-    const double ctr = val(i, j, 2);
-    double ax[6], far[6], dg[12];
-    ax[0] = val(i - 1, j, 2); ax[1] = val(i + 1, j, 2); ax[2] = val(i, j - 1, 2);
-    ax[3] = val(i, j + 1, 2); ax[4] = val(i, j, 1); ax[5] = val(i, j, 3);
-    far[0] = val(i - 2, j, 2); far[1] = val(i + 2, j, 2); far[2] = val(i, j - 2, 2);
-    far[3] = val(i, j + 2, 2); far[4] = val(i, j, 0); far[5] = val(i, j, 4);
-    dg[0] = val(i - 1, j - 1, 2); dg[1] = val(i - 1, j + 1, 2); dg[2] = val(i + 1, j - 1, 2); dg[3] = val(i + 1, j + 1, 2);
-    dg[4] = val(i - 1, j, 1); dg[5] = val(i + 1, j, 1); dg[6] = val(i, j - 1, 1); dg[7] = val(i, j + 1, 1);
-    dg[8] = val(i - 1, j, 3); dg[9] = val(i + 1, j, 3); dg[10] = val(i, j - 1, 3); dg[11] = val(i, j + 1, 3);
-    int E = max(1, exponent_of(ctr));
-#pragma unroll
-    for (int t = 0; t < 6; ++t) E = max(E, max(exponent_of(ax[t]), exponent_of(far[t])));
-#pragma unroll
-    for (int t = 0; t < 12; ++t) E = max(E, exponent_of(dg[t]));
-    long long s_ax = 0, s_far = 0, s_dg = 0;
-#pragma unroll
-    for (int t = 0; t < 6; ++t) {
-        s_ax += to_fixed(ax[t], E);
-        s_far += to_fixed(far[t], E);
+    e = (int)__reduce_max_sync(0xffffffffu, (unsigned)e);
+    if ((tid & 31) == 0) wred[tid >> 5] = e;
+    __syncthreads();
+    const int E = max(1, (int)__reduce_max_sync(0xffffffffu, (unsigned)wred[tid & (kCT / 32 - 1)]));
+    for (int t = tid; t < tot; t += kCT) {
+        const int d = t / mm, rem = t - d * mm;
+        const int jj = rem / m, ii = rem - jj * m;
+        const unsigned b = pbase[d];
+        tile[(d * tw + jj + 2) * tw + ii + 2] = b ? to_fixed(cl_ld(b + 8u * (unsigned)rem), E) : 0ll;
     }
-#pragma unroll
-    for (int t = 0; t < 12; ++t) s_dg += to_fixed(dg[t], E);
+    __syncthreads();
+    return E;
+}
+
+// y at own node (i, j) of local plane pl = A u from the CTA's tile of u on
+// scale E: the 25 taps of eq. (method1) summed exactly, rounded once.
+__device__ __forceinline__ double cl_apply(const long long* tile, int m, int E, int sigma, int pl, int i, int j,
+                                           int k) {
+    const int tw = m + 4;
+    auto at = [&](int d, int a, int b) { return tile[((pl + 2 + d) * tw + b + 1) * tw + a + 1]; };
+    const long long c0 = at(0, i, j);
+    const long long s_ax = at(0, i - 1, j) + at(0, i + 1, j) + at(0, i, j - 1) + at(0, i, j + 1) + at(-1, i, j) +
+                           at(1, i, j);
+    const long long s_far = at(0, i - 2, j) + at(0, i + 2, j) + at(0, i, j - 2) + at(0, i, j + 2) + at(-2, i, j) +
+                            at(2, i, j);
+    const long long s_dg = at(0, i - 1, j - 1) + at(0, i - 1, j + 1) + at(0, i + 1, j - 1) + at(0, i + 1, j + 1) +
+                           at(-1, i - 1, j) + at(-1, i + 1, j) + at(-1, i, j - 1) + at(-1, i, j + 1) +
+                           at(1, i - 1, j) + at(1, i + 1, j) + at(1, i, j - 1) + at(1, i, j + 1);
     const int c = (i == 1) + (i == m) + (j == 1) + (j == m) + (k == 1) + (k == m);
-    const long long acc = (long long)(42 + sigma * c) * to_fixed(ctr, E) - 12 * s_ax + s_far + 2 * s_dg;
+    const long long acc = (long long)(42 + sigma * c) * c0 - 12 * s_ax + s_far + 2 * s_dg;
     return fx_result(acc, E, E == 0x7FF);
 }
 
@@ -167,6 +170,8 @@ bicg_cluster_kernel(double* __restrict__ x, double* __restrict__ r, double* __re
     const int np = n + 1;
     ClusterGeom g{m, P, (unsigned)__cvta_generic_to_shared(csm)};
     double* red = csm + kCVec * P * mm;
+    long long* tile = reinterpret_cast<long long*>(red + 8);   // (P + 4) x (m + 4)^2
+    __shared__ int wred[kCT / 32];
     const bool elide = rs == nullptr;
     auto sm = [&](int v, int t) -> double& { return csm[v * P * mm + t]; };
     auto gidx = [&](int t) {
@@ -199,6 +204,7 @@ bicg_cluster_kernel(double* __restrict__ x, double* __restrict__ r, double* __re
         pbase[0][tid] = cl_plane_base(g, VP, k0 - 2 + tid);
         pbase[1][tid] = cl_plane_base(g, VPS, k0 - 2 + tid);
     }
+    for (int t = tid; t < (P + 4) * (m + 4) * (m + 4); t += kCT) tile[t] = 0ll;   // the zero border
     double tw[4] = {diff, 0.0, 0.0, 0.0};
     cl_reduce(tw, 1, 1, red, sh, bc);   // also: every CTA's vectors are loaded
     const bool twin = elide || tw[0] == 0.0;
@@ -206,18 +212,22 @@ bicg_cluster_kernel(double* __restrict__ x, double* __restrict__ r, double* __re
     for (int it = 0; it < iters && !done; ++it) {
         // phase A: q = A p, q* = A^T p* (= A p* here), sigma = (p*, q)
         double a[4] = {0.0, 0.0, 0.0, 0.0};
+        const int Ep = cl_fill_tile(pbase[0], P, m, tile, wred);
         for (int t = tid; t < nown; t += kCT) {
             const int pl = t / mm, rem = t - pl * mm;
-            const int j = rem / m + 1, i = rem - (j - 1) * m + 1, k = k0 + pl;
-            const double qv = cl_point(g, &pbase[0][pl], sigma, i, j, k);
-            sm(VQ, t) = qv;
-            if (twin) {
-                a[0] += sm(VP, t) * qv;
-            } else {
-                sm(VQS, t) = cl_point(g, &pbase[1][pl], sigma, i, j, k);
-                a[0] += sm(VPS, t) * qv;
+            const int j = rem / m + 1, i = rem - (j - 1) * m + 1;
+            sm(VQ, t) = cl_apply(tile, m, Ep, sigma, pl, i, j, k0 + pl);
+        }
+        if (!twin) {
+            __syncthreads();   // every read of p's tile is done
+            const int Es = cl_fill_tile(pbase[1], P, m, tile, wred);
+            for (int t = tid; t < nown; t += kCT) {
+                const int pl = t / mm, rem = t - pl * mm;
+                const int j = rem / m + 1, i = rem - (j - 1) * m + 1;
+                sm(VQS, t) = cl_apply(tile, m, Es, sigma, pl, i, j, k0 + pl);
             }
         }
+        for (int t = tid; t < nown; t += kCT) a[0] += sm(twin ? VP : VPS, t) * sm(VQ, t);
         cl_reduce(a, 1, 0, red, sh, bc);
         sigma_s = a[0];
         if (!(rho != 0.0 && isfinite(rho)) || !(sigma_s != 0.0 && isfinite(sigma_s))) {
@@ -290,7 +300,7 @@ bicg_cluster_kernel(double* __restrict__ x, double* __restrict__ r, double* __re
 
 size_t cluster_smem(int n) {
     const int m = n - 1, P = (m + kCC - 1) / kCC;
-    return (size_t)(kCVec * P * m * m + 8) * sizeof(double);
+    return (size_t)(kCVec * P * m * m + 8 + (P + 4) * (m + 4) * (m + 4)) * sizeof(double);
 }
 
 std::mutex g_cluster_mu;
