@@ -121,11 +121,8 @@ int bicg_run(excmg_ctx* ctx, int n, int bc_kind, const double* b, double* x, dou
             int chunk = 256;
             const int left = max_iter - ctx->host_state->iter;
             if (chunk > left) chunk = left;
-            e = cluster_bicg_usable(n)
-                    ? launch_bicg_cluster(x, r, elide ? nullptr : rs, p, elide ? nullptr : ps, n, bc_kind, chunk,
-                                          ctx->state, s)
-                    : launch_bicg_persistent(x, r, rs, p, ps, q, qs, n, bc_kind, chunk, ctx->partials, ctx->state,
-                                             ctx->barrier, s, elide);
+            e = launch_bicg_persistent(x, r, rs, p, ps, q, qs, n, bc_kind, chunk, ctx->partials, ctx->state,
+                                       ctx->barrier, s, elide);
             note_launches(1);
             if (e != cudaSuccess) return ctx_cuda(ctx, e, "cooperative Bi-CG launch");
         }

@@ -69,12 +69,6 @@ cudaError_t launch_bicg_stencil_pair_dir(const double* r, const double* rs, cons
 // Small grids: whole Bi-CG iterations (up to `iters`) in one cooperative
 // launch with bounded grid barriers; barrier_words: 3 device words.
 constexpr int kPersistentMaxN = 64;
-// Grids up to 32^3: the iterations in one 16-CTA thread-block cluster with
-// every vector in shared memory (cluster.cu), where the device can hold one
-// such cluster.  rs, ps null: the shadow-elided mode.
-bool cluster_bicg_usable(int n);
-cudaError_t launch_bicg_cluster(double* x, double* r, double* rs, double* p, double* ps, int n, int bc_kind, int iters,
-                                BicgState* st, cudaStream_t s);
 bool persistent_pointwise(int n);
 // elide: the shadow-elided mode (rs, ps, qs unused, may be null).
 cudaError_t launch_bicg_persistent(double* x, double* r, double* rs, double* p, double* ps, double* q, double* qs,
