@@ -66,6 +66,8 @@ def parse(argv=None):
                     help="batched leg: also the mixed-precision form (about 90 s more)")
     ap.add_argument("--no-serve", action="store_true", help="skip the request-stream leg")
     ap.add_argument("--serve-requests", type=int, default=120)
+    ap.add_argument("--serve-max-s", type=float, default=90.0,
+                    help="request stream: arrivals spread over at most this many seconds (0: 0.8x capacity only)")
     ap.add_argument("--no-elided", action="store_true", help="skip the shadow-elided variant leg")
     ap.add_argument("--schedule", choices=["separate", "fused"], default="fused",
                     help="Bi-CG operator schedule of the timed solves on grids above 64^3")
@@ -787,18 +789,22 @@ def serving_leg(args, B, ctx, dev):
     S.serve(B.Batch(ctx, max_instances=256), burst, pool, tol, new_output=new_out, submit_kwargs=prec)
     torch.cuda.synchronize(dev)
     _, cap = S.serve(B.Batch(ctx, max_instances=256), burst, pool, tol, new_output=new_out, submit_kwargs=prec)
-    # 0.8x capacity, but the stream lasts at most about 90 s
-    rate = max(0.8 * cap["solves_per_s"], args.serve_requests / 90.0)
+    # 0.8x capacity, but the stream lasts at most about --serve-max-s seconds
+    rate = 0.8 * cap["solves_per_s"]
+    if args.serve_max_s > 0:
+        rate = max(rate, args.serve_requests / args.serve_max_s)
     reqs = S.make_requests(args.serve_requests, rate=rate, seed=1)
     pool.warm(reqs)
     torch.cuda.synchronize(dev)
     budget = 64 * (1 << 30)
     recs, summ = S.serve(B.Batch(ctx, hbm_budget_bytes=budget, max_instances=256), reqs, pool, tol,
-                         new_output=new_out, submit_kwargs=prec)
+                         new_output=new_out, submit_kwargs=prec, keep_outputs=False)
     summ.update({"capacity_solves_per_s": cap["solves_per_s"], "rate_per_s": rate, "hbm_budget_bytes": budget,
                  "precision": args.serve_precision,
-                 "workload": (f"{args.serve_requests} requests, Poisson at max(0.8x capacity, requests / 90 s), "
-                              "n log-uniform in "
+                 "workload": (f"{args.serve_requests} requests, Poisson at "
+                              + (f"max(0.8x capacity, requests / {args.serve_max_s:g} s), " if args.serve_max_s > 0
+                                 else "0.8x capacity, ")
+                              + "n log-uniform in "
                               "[32, 256] rounded to c*2^k (c = 4..7), kinds uniform, 4 random-sine problems "
                               "per (n, kind), tol 1e-8")})
     return summ

@@ -97,10 +97,11 @@ class InputPool:
 
 
 def serve(engine, requests, pool, tol: float, clock=time.perf_counter, new_output=None, sleep=time.sleep,
-          submit_kwargs=None):
+          submit_kwargs=None, keep_outputs: bool = True):
     """Run the request stream through `engine` (a binding.Batch or anything
     with submit/step/query; submit_kwargs go to every submit).  Returns
-    per-request records and a summary."""
+    per-request records (with each result when keep_outputs) and a
+    summary."""
     submit_kwargs = submit_kwargs or {}
     pending = collections.deque(sorted(requests))
     queued = collections.deque()
@@ -142,7 +143,7 @@ def serve(engine, requests, pool, tol: float, clock=time.perf_counter, new_outpu
                     r, u = live.pop(ident)
                     records.append({"rid": r.rid, "n": r.n, "bc": r.bc, "status": q["status"],
                                     "latency_s": t_now - r.t_arrival, "arrival_s": r.t_arrival,
-                                    "engine_latency_s": q.get("latency_s"), "output": u})
+                                    "engine_latency_s": q.get("latency_s"), "output": u if keep_outputs else None})
         elif pending:
             sleep(max(0.0, min(0.01, pending[0].t_arrival - (clock() - t0))))
     wall = clock() - t0
