@@ -111,6 +111,9 @@ def test_batch_launched_levels_match_single_solves():
         ident, u = batch.submit(n, nc, bc, f, g1, g2, tol, precision="fp64")
         subs.append((ident, u, n, nc, bc, f, g1, g2))
     batch.run()
+    prof = batch.profile()
+    assert prof["group_launches"] > 0 and prof["rounds"] > 0
+    assert 0 < prof["member_iters"] <= prof["member_rounds"]
     for ident, u, n, nc, bc, f, g1, g2 in subs:
         q = batch.query(ident)
         assert q["done"] and q["status"] == 0
