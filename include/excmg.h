@@ -65,7 +65,7 @@ typedef struct excmg_ctx excmg_ctx;      /* device, stream, workspace, DSOLVE fa
 typedef struct excmg_level excmg_level;  /* one grid: (context, N, bc_kind)                */
 
 /* Tolerance schedule of Alg. 1: EXCMG_TOL_PAPER uses eps_i = tol * 10^(i-L)
- * (Alg. 1, line 5); EXCMG_TOL_UNIFORM uses eps_i = tol on every level. */
+ * (Alg. 1's tolerance schedule); EXCMG_TOL_UNIFORM uses eps_i = tol on every level. */
 enum { EXCMG_TOL_PAPER = 0, EXCMG_TOL_UNIFORM = 1 };
 
 /* Arithmetic of the Bi-CG levels.  EXCMG_PRECISION_FP64: Alg. 2 in FP64.
@@ -202,13 +202,13 @@ int stencil_apply(const excmg_level *level, int transpose, const double *u, doub
 int bicg_solve(const excmg_level *level, const double *b, double *x_inout, double tol,
                int max_iter, int *iters_out, double *relres_out);
 
-/* bicg_solve with a caller-chosen shadow residual r*_0 (Alg. 2, line 2 leaves
+/* bicg_solve with a caller-chosen shadow residual r*_0 (Alg. 2 leaves
  * x*_0 and b* free): shadow_r0 is a node array whose interior entries give
  * r*_0 ((r_0, r*_0) must not vanish); NULL means r*_0 = r_0. */
 int bicg_solve_ex(const excmg_level *level, const double *b, double *x_inout, const double *shadow_r0,
                   double tol, int max_iter, int *iters_out, double *relres_out);
 
-/* EXP_finite (Sec. 4.2.2-4.2.3, Steps 1-5; Alg. 1 line 6): third-order
+/* EXP_finite (Sec. 4.2.2-4.2.3, Steps 1-5; Alg. 1's initial guess): third-order
  * approximation w_h on the grid with n_fine intervals (n_fine divisible by
  * 4, >= 8) of the FD solution, from the FD solutions u_2h (n_fine/2
  * intervals) and u_4h (n_fine/4 intervals), all node arrays.  Steps 1-5 give
@@ -238,7 +238,7 @@ int extrapolate_interpolate(int n_fine, const double *u_2h, const double *u_4h, 
  * threads, other streams) race and must be serialised by the caller. */
 int extrapolate_interpolate_noalloc(int n_fine, const double *u_2h, const double *u_4h, double *w_h);
 
-/* EXP_true (Sec. 4.2.1, eqs. (t1), (chenlin); Alg. 1 line 11): extrapolated
+/* EXP_true (Sec. 4.2.1, eqs. (t1), (chenlin); Alg. 1's final extrapolation): extrapolated
  * solution u_tilde = u_h + (1/3) * multilinear interpolation of (u_h - u_2h)
  * on the grid with n_fine intervals (even, >= 4).  Every node is written. */
 int midpoint_extrapolate(int n_fine, const double *u_h, const double *u_2h, double *u_tilde);
@@ -275,7 +275,7 @@ int midpoint_extrapolate_ex(excmg_ctx *ctx, int n_fine, const double *u_h, const
 int excmg_assemble_rhs(const excmg_level *level, int n_src, const double *f, const double *g1,
                        const double *g2, double *fh);
 
-/* DSOLVE (Alg. 1, lines 1-2): u = A_h^{-1} fh on the level's interior nodes
+/* DSOLVE (Alg. 1's direct solves): u = A_h^{-1} fh on the level's interior nodes
  * (u's boundary entries left unchanged).  The first call on a (N, bc_kind)
  * factorises A_h (dense Gauss-Jordan inverse, kept in the context); 4 <= N <= 16
  * (at most 15^3 = 3375 unknowns, a 91 MB inverse), else EXCMG_ERR_ARG. */

@@ -342,7 +342,7 @@ int orc_assemble_dense(int N, int bc_kind, double *A) {
 }
 
 /* ------------------------------------------------------------------------
- * DSOLVE (Alg. 1, lines 1-2): a direct solve of A_h u_h = f_h.  Gaussian
+ * DSOLVE (Alg. 1's direct solves): a direct solve of A_h u_h = f_h.  Gaussian
  * elimination without pivoting in band storage; in lexicographic order the
  * half bandwidth is 2 (N-1)^2 (the z +-2 taps).  Writes the interior of u;
  * boundary entries of u are left as they are.
@@ -413,7 +413,7 @@ static double idot(int N, const double *a, const double *b) {
     return s;
 }
 
-/* ||f_h - A_h u||_2 over the unknowns (the test of Alg. 1, line 7). */
+/* ||f_h - A_h u||_2 over the unknowns (the true-residual test of Alg. 1). */
 double orc_residual_norm(int N, int bc_kind, const double *fh, const double *u) {
     size_t total = (size_t)(N + 1) * (size_t)(N + 1) * (size_t)(N + 1), p;
     double *au = (double *)malloc(total * sizeof(double)), s;
@@ -621,7 +621,7 @@ int orc_exp_finite(int Nf, const double *u1, const double *u0, double *w) {
 }
 
 /* ------------------------------------------------------------------------
- * EXP_true (Sec. 4.2.1, Alg. 1 line 11): extrapolated solution on the
+ * EXP_true (Sec. 4.2.1, Alg. 1's final extrapolation): extrapolated solution on the
  * finest grid from u_h (Nf intervals) and u_2h (Nf/2 intervals).
  * At nodes shared with the coarse grid, eq. (t1): (4 u_h - u_2h) / 3.
  * Elsewhere the paper prints the 1D midpoint rule, eq. (chenlin):
@@ -666,13 +666,13 @@ int orc_exp_true(int Nf, const double *uh, const double *u2h, double *ut) {
  * n_finest.  f, g1 are node arrays and g2 the faces on the finest grid;
  * every coarser level takes every stride-th value (the grids are nested).
  *
- * Each Bi-CG level runs the WHILE loop of Alg. 1, lines 7-9:
+ * Each Bi-CG level runs the WHILE loop of Alg. 1:
  *   while ||A u - f_h||_2 > eps_i ||f_h||_2:  u <- Bi-CG(A, u, f_h)
  * where one Bi-CG call iterates until its recursively updated residual
  * meets eps_i (or max_iter).  The loop also ends when two calls in a row
  * fail to halve the true residual ("stagnated": the floating-point floor),
  * or when the level has used max_total iterations.
- * tol_mode 0: eps_i = tol * 10^(i-L) (Alg. 1, line 5); 1: eps_i = tol.
+ * tol_mode 0: eps_i = tol * 10^(i-L) (Alg. 1's tolerance schedule); 1: eps_i = tol.
  *
  * stats (may be NULL), per level l = 0 .. L+1, 4 doubles each:
  *   [iterations, final true relative residual, Bi-CG calls, stagnated flag]
@@ -719,14 +719,14 @@ int orc_excmg(int n_finest, int n_coarsest, int bc_kind, const double *f, const 
         orc_assemble_rhs(N, bc_kind, fl, g1l, g2l, fh);
         fnorm = orc_interior_norm2(N, fh);
         if (l <= 1) {
-            /* Alg. 1, lines 1-2: DSOLVE on the two coarsest grids */
+            /* Alg. 1's direct solves: DSOLVE on the two coarsest grids */
             memcpy(u[l], g1l, tot * sizeof(double));
             status = orc_dsolve(N, bc_kind, fh, u[l]);
             rel = fnorm > 0.0 ? orc_residual_norm(N, bc_kind, fh, u[l]) / fnorm : 0.0;
         } else {
             int i = l - 1;  /* Alg. 1 loop counter, 1..L */
             eps_i = tol_mode == 0 ? tol * pow(10.0, (double)(i - L)) : tol;
-            /* Alg. 1, line 6: w_h = EXP_finite(u_2h, u_4h) */
+            /* Alg. 1's initial guess: w_h = EXP_finite(u_2h, u_4h) */
             status = orc_exp_finite(N, u[l - 1], u[l - 2], u[l]);
             /* the FD solution carries the Dirichlet data g1 on the boundary
              * (Sec. 2); the interior of w_h is the initial guess */
@@ -767,7 +767,7 @@ int orc_excmg(int n_finest, int n_coarsest, int bc_kind, const double *f, const 
         int Nf = n_finest;
         size_t tot = (size_t)(Nf + 1) * (size_t)(Nf + 1) * (size_t)(Nf + 1);
         if (u_h_out) memcpy(u_h_out, u[nl - 1], tot * sizeof(double));
-        /* Alg. 1, line 11 */
+        /* Alg. 1's final extrapolation */
         if (u_tilde_out) status = orc_exp_true(Nf, u[nl - 1], u[nl - 2], u_tilde_out);
     }
 out:

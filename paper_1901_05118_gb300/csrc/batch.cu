@@ -524,7 +524,7 @@ void free_instance(excmg_batch* b, Instance* in) {
     }
 }
 
-// Level l's eps (Alg. 1, line 5).
+// Level l's eps (Alg. 1's tolerance schedule).
 double level_eps(const Instance* in, int l) {
     const int i = l - 1;
     return in->tol_mode == EXCMG_TOL_PAPER ? in->tol * std::pow(10.0, (double)(i - in->L)) : in->tol;
@@ -1158,7 +1158,7 @@ int excmg_batch_step(excmg_batch* b, int* n_live) {
             in->fnorm = -1.0;   // formed with the first residual
         }
     }
-    // 2. FP64 true residuals (Alg. 1, line 7) and the decisions they drive
+    // 2. FP64 true residuals (Alg. 1's true-residual test) and the decisions they drive
     std::vector<Instance*> res;
     for (Instance* in : b->live)
         if (!in->in_flight && in->phase == kResidual) res.push_back(in);

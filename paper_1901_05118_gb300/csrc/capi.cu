@@ -468,7 +468,7 @@ int excmg_solve_ex(excmg_ctx* ctx, int n_finest, int n_coarsest, int bc_kind, co
             break;
         }
         if (l <= 1) {
-            // Alg. 1, lines 1-2
+            // Alg. 1's direct solves
             if ((result = dsolve_run(ctx, N, bc_kind, fh, u))) break;
             if ((result = true_residual_norm(ctx, N, bc_kind, fh, u, &rn))) break;
             rel = fnorm > 0.0 ? rn / fnorm : 0.0;
@@ -492,7 +492,7 @@ int excmg_solve_ex(excmg_ctx* ctx, int n_finest, int n_coarsest, int bc_kind, co
                 result = ctx_fail(ctx, EXCMG_ERR_NAN, "residual of the initial guess is not finite");
                 break;
             }
-            // Alg. 1, lines 7-9
+            // Alg. 1's WHILE loop
             while (rel > eps && iters < params->max_total) {
                 int it = 0;
                 double rr = 0.0;
@@ -531,7 +531,7 @@ int excmg_solve_ex(excmg_ctx* ctx, int n_finest, int n_coarsest, int bc_kind, co
         const size_t bytes = node_count(n_finest) * sizeof(double);
         cudaError_t e = cudaSuccess;
         if (u_h_out) e = cudaMemcpyAsync(u_h_out, lvl[nl - 1], bytes, cudaMemcpyDeviceToDevice, s);
-        // Alg. 1, line 11
+        // Alg. 1's final extrapolation
         if (e == cudaSuccess && u_tilde_out) {
             e = launch_exp_true(u_tilde_out, lvl[nl - 1], lvl[nl - 2], n_finest, s);
             note_launches(1);

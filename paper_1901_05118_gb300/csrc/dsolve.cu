@@ -1,4 +1,4 @@
-// DSOLVE of Alg. 1, lines 1-2: the two coarsest grids are solved directly.
+// DSOLVE of Alg. 1: the two coarsest grids are solved directly.
 //
 // A_h (the 25-point rows with reflections folded in) is assembled densely in
 // lexicographic order of the unknowns (x fastest), inverted once per

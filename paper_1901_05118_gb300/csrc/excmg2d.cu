@@ -605,7 +605,7 @@ int excmg2d_solve(excmg_ctx* ctx, int n_finest, int n_coarsest, int bc_kind, con
         const double fnorm = host_norm(ctx, fh, len, &st);
         if (st) return st;
         if (!std::isfinite(fnorm)) return ctx_fail(ctx, EXCMG_ERR_NAN, "2D right-hand side is not finite");
-        if (l <= 1) {   // Alg. 1, lines 1-2
+        if (l <= 1) {   // Alg. 1's direct solves
             if ((st = dsolve2d(ctx, N, bc_kind, fh, u))) return st;
             const double rn = residual2d(ctx, N, bc_kind, fh, u, &st);
             if (st) return st;
@@ -618,7 +618,7 @@ int excmg2d_solve(excmg_ctx* ctx, int n_finest, int n_coarsest, int bc_kind, con
             if (st) return st;
             rel = fnorm > 0.0 ? rn / fnorm : 0.0;
             if (!std::isfinite(rel)) return ctx_fail(ctx, EXCMG_ERR_NAN, "2D residual is not finite");
-            while (rel > eps && iters < params->max_total) {   // Alg. 1, lines 7-9
+            while (rel > eps && iters < params->max_total) {   // Alg. 1's WHILE loop
                 int it = 0;
                 double rr = 0.0;
                 const double prev = rel;
@@ -652,7 +652,7 @@ int excmg2d_solve(excmg_ctx* ctx, int n_finest, int n_coarsest, int bc_kind, con
     }
     cudaError_t e = cudaSuccess;
     if (u_h_out) e = cudaMemcpyAsync(u_h_out, lvl[nl - 1], lenf * sizeof(double), cudaMemcpyDeviceToDevice, s);
-    if (e == cudaSuccess && u_tilde_out) {   // Alg. 1, line 11
+    if (e == cudaSuccess && u_tilde_out) {   // Alg. 1's final extrapolation
         exp_true2d_kernel<<<blocks_for(lenf), 256, 0, s>>>(u_tilde_out, lvl[nl - 1], lvl[nl - 2], n_finest);
         e = cudaGetLastError();
         note_launches(1);

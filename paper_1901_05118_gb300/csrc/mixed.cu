@@ -5,7 +5,7 @@
 // the correction equation A e = r / ||r|| approximately with Bi-CG (Alg. 2,
 // M = I, r*_0 = r_0) entirely in FP32 -- FP32 vectors, FP32 operator, FP32
 // accumulation inside threads and CTAs -- and updates u += ||r|| e in FP64.
-// The loop ends on the FP64 true residual test of Alg. 1 (line 7), with the
+// The loop ends on the FP64 true residual test of Alg. 1, with the
 // same stagnation rule as the FP64 solver.  The FP32 operator applies A^T
 // with the same code as A: A_h is symmetric, so the two are one operator.
 //

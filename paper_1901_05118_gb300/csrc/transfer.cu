@@ -13,7 +13,7 @@
 // coordinate 0, 1/4, 1/2, 3/4, 1 has weights (1,0,0), (3/8,3/4,-1/8),
 // (0,1,0), (-1/8,3/4,3/8), (0,0,1) on the cell's three middle-grid nodes.
 //
-// EXP_true (Sec. 4.2.1, eqs. (t1), (chenlin); Alg. 1 line 11):
+// EXP_true (Sec. 4.2.1, eqs. (t1), (chenlin); Alg. 1's final extrapolation):
 //     u~ = u_h + (1/3) * (mean of u_h - u_2h over the 2^m coarse nodes
 //                         around the node),
 // which is (4 u_h - u_2h)/3 at coarse nodes and (chenlin) at 1D midpoints.

@@ -303,7 +303,7 @@ def test_excmg_solve_128_matches_oracle(bc_kind, case, schedule):
     the cooperative kernels and the 128^3 level the launched operator /
     update / direction-update kernels (in both operator schedules), inside
     the WHILE loop with its restarts, stagnation rule and EXP_finite
-    hand-offs, under both tolerance schedules of Alg. 1 line 5.  Every level
+    hand-offs, under both tolerance schedules (Alg. 1 and uniform).  Every level
     takes the oracle's Bi-CG iterations and calls and ends the same way; u_h
     and u~ match the oracle's entry by entry."""
     tol_mode, tol, max_iter, max_total = case

@@ -402,7 +402,7 @@ def test_paper_tables_at_32(name):
 
 def test_orders_second_and_extrapolated():
     """u_h is second order (Tables 1-5: order ~2); the extrapolated solution
-    of Alg. 1 line 11 is markedly more accurate."""
+    of Alg. 1's final extrapolation is markedly more accurate."""
     prob = P.sin_pi()
     errs, terrs = [], []
     for nf in (16, 32):
@@ -469,7 +469,7 @@ def test_bicg_with_chosen_shadow_matches_direct_solve(bc_kind):
     np.testing.assert_allclose(interior(x), interior(xd), rtol=0, atol=1e-9 * np.abs(xd).max())
 
 
-# -------------------------------------------- Alg. 1 line 5: the tolerances
+# ------------------------------------- the tolerance schedule of Alg. 1
 @pytest.mark.parametrize("bc_kind", [1, 2])
 def test_excmg_paper_tolerance_schedule(bc_kind):
     """eps_i = eps * 10^(i - L): level i of L (i = L the finest) stops at a
