@@ -618,7 +618,7 @@ cudaError_t launch_stencil(const double* u, double* y, const double* b, int n, i
     return cudaGetLastError();
 }
 
-constexpr int kPointwiseMaxN = 40;   // per-node operator on grids up to 40^3
+constexpr int kPointwiseMaxN = 32;   // per-node operator on grids up to 32^3
 
 // dynamic shared memory of the z-march variant: the copy-ahead march's
 // stages and tiles
