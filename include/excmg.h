@@ -311,7 +311,9 @@ size_t excmg_batch_instance_bytes(int n_finest, int n_coarsest, int precision);
  * u_out receives u_tilde.  Returns EXCMG_ERR_BUDGET (nothing admitted) when
  * the budget or the slot count is full right now -- submit again after a
  * step -- and EXCMG_ERR_TOO_LARGE when the instance alone needs more than
- * the whole budget, so that it can never be admitted. */
+ * the whole budget, so that it can never be admitted.  n_finest is limited to
+ * grids whose operator launch has at most 8192 CTAs (2048 intervals);
+ * larger ones return EXCMG_ERR_ARG. */
 int excmg_batch_submit(excmg_batch *batch, int n_finest, int n_coarsest, int bc_kind, const double *f,
                        const double *g1, const double *g2, const excmg_params *params, double *u_out,
                        int *id_out);

@@ -1035,6 +1035,9 @@ int excmg_batch_submit(excmg_batch* b, int n_finest, int n_coarsest, int bc_kind
         ++steps;
     }
     if (n != n_finest || steps < 2) return bfail(b, EXCMG_ERR_ARG, "n_finest must be n_coarsest * 2^(L+1), L >= 1");
+    // the per-slot partial sums hold one value per CTA of an operator launch
+    if (stencil_cta_count(n_finest) > kMaxPartials)
+        return bfail(b, EXCMG_ERR_ARG, "n_finest too large for the batch engine's per-instance partial sums");
     if (params->precision != EXCMG_PRECISION_FP64 && params->precision != EXCMG_PRECISION_MIXED)
         return bfail(b, EXCMG_ERR_ARG, "unknown precision");
     if (!(params->tol > 0.0) || params->max_iter < 1 || params->max_total < 1 ||
