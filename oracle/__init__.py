@@ -4,9 +4,11 @@ TEST INFRASTRUCTURE ONLY.  Only ``tests/``, ``__graft_entry__.smoke()`` and the
 CPU-baseline leg of ``bench.py`` may import this package.  The product path
 (the CUDA library and its Python binding) never touches it.
 
-The arithmetic lives in ``excmg_oracle.c`` (plain C, compiled with
-``-ffp-contract=off``); this module only builds it and marshals numpy arrays
-through ctypes.  Array conventions: node arrays of shape (N+1, N+1, N+1) in
+The arithmetic lives in ``excmg_oracle.c`` and, for the 2D problem of eq.
+(bvp2d), ``excmg2d_oracle.c`` (plain C, compiled with ``-ffp-contract=off``,
+OpenMP over loops with independent iterations); this module only builds them
+and marshals numpy arrays through ctypes (2D node arrays of shape (N+1, N+1)
+in (y, x) order, 2D g2 of shape (4, N+1) with edges x=0, x=1, y=0, y=1).  Array conventions: node arrays of shape (N+1, N+1, N+1) in
 (z, y, x) order, i.e. x fastest in memory; g2 as shape (6, N+1, N+1) with faces
 x=0, x=1, y=0, y=1, z=0, z=1 and the two in-face axes (a, b) in x<y<z order
 stored as [face, b, a].
