@@ -80,6 +80,7 @@ def parse(argv=None):
     ap.add_argument("--iters", type=int, default=4, help="--case bicg: Bi-CG iterations")
     ap.add_argument("--reps", type=int, default=3, help="--case stencil: operator applications")
     ap.add_argument("--shadow", choices=["full", "elided"], default="full", help="--case bicg: shadow mode")
+    ap.add_argument("--precision", choices=["fp64", "mixed"], default="fp64", help="--case solve: precision")
     return ap.parse_args(argv)
 
 
@@ -863,7 +864,7 @@ def profile_case(args):
         B.bicg_solve(lvl, b, x, 0.0, args.iters)
     else:
         f, g1, g2 = (torch.from_numpy(v).to(dev) for v in problems.exp_sum().data(n, args.bc))
-        B.excmg_solve(n, args.nc, args.bc, f, g1, g2, args.tol, ctx=ctx)
+        B.excmg_solve(n, args.nc, args.bc, f, g1, g2, args.tol, ctx=ctx, precision=args.precision)
     torch.cuda.synchronize()
     print(json.dumps({"case": args.case, "n": n, "ok": True}), flush=True)
 
