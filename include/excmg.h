@@ -362,7 +362,13 @@ int excmg_batch_get_profile(const excmg_batch *batch, excmg_batch_profile *out);
  * pointers owned by the caller; every call is synchronous on ctx's stream.
  * The operator sums its integer-weighted taps exactly on one power-of-two
  * scale per 32 x 16 tile (the tile's largest input exponent) and rounds
- * each output once. */
+ * each output once.  Errors: EXCMG_ERR_ARG for a null pointer, bc_kind not
+ * 1 or 2, N < 4 (EXP_finite: n_fine < 8 or not a multiple of 4; EXP_true:
+ * n_fine odd), N > 2049 in the Bi-CG and solve calls (one partial sum per
+ * 32 x 16 tile, at most 8192), u == y in excmg2d_stencil_apply; the other
+ * statuses as for the 3D calls (EXCMG_ERR_NOCONV from excmg2d_bicg_solve at
+ * its iteration cap, EXCMG_ERR_BREAKDOWN, EXCMG_ERR_NAN, EXCMG_ERR_OOM,
+ * EXCMG_ERR_BUDGET, EXCMG_ERR_CUDA). */
 /* y = A_h u (transpose: A_h^T u, the same bits); interior entries of u read,
  * boundary entries of y set to 0. */
 int excmg2d_stencil_apply(excmg_ctx *ctx, int n, int bc_kind, int transpose, const double *u, double *y);
