@@ -74,7 +74,7 @@ def parse(argv=None):
     ap.add_argument("--serve-precision", choices=["fp64", "mixed"], default="fp64")
     ap.add_argument("--oracle-report", action="store_true",
                     help="time the CPU oracle on the small workload and one 512^3 operator application, then exit")
-    ap.add_argument("--case", choices=["stencil", "bicg", "solve"],
+    ap.add_argument("--case", choices=["stencil", "bicg", "solve", "batch"],
                     help="run one small fixed case for a profiler capture (sizes from --n / --nc) and exit")
     ap.add_argument("--bc", type=int, default=1, help="--case: kind of boundary data")
     ap.add_argument("--iters", type=int, default=4, help="--case bicg: Bi-CG iterations")
@@ -835,7 +835,8 @@ def oracle_report():
 def profile_case(args):
     """A small, fixed GPU case for profiling single kernels: `stencil` (reps
     operator applications), `bicg` (iters Bi-CG iterations from x = 0 on a
-    random right-hand side) or `solve` (one EXCMG solve of u = e^(x+y+z)).
+    random right-hand side), `solve` (one EXCMG solve of u = e^(x+y+z)) or
+    `batch` (16 solves of one size in the batch engine).
     At n = 256 the inputs are still larger than L2 and a capture of a few
     launches ends quickly."""
     import torch
@@ -862,6 +863,14 @@ def profile_case(args):
         x = torch.zeros_like(b)
         lvl = B.Level(n, args.bc, ctx)
         B.bicg_solve(lvl, b, x, 0.0, args.iters)
+    elif args.case == "batch":
+        # 16 instances of one size (random sines, alternating kinds) in the batch engine
+        batch = B.Batch(ctx, max_instances=16)
+        for i in range(16):
+            f, g1, g2 = problems.random_sines_torch(5000 + i, n, 1 + i % 2, dev)
+            batch.submit(n, args.nc, 1 + i % 2, f, g1, g2, args.tol, precision=args.precision)
+        batch.run()
+        batch.close()
     else:
         f, g1, g2 = (torch.from_numpy(v).to(dev) for v in problems.exp_sum().data(n, args.bc))
         B.excmg_solve(n, args.nc, args.bc, f, g1, g2, args.tol, ctx=ctx, precision=args.precision)
